@@ -1,0 +1,429 @@
+#!/usr/bin/env python
+"""Benchmark of the RCM-relabelled hybrid BFS on one GB300.
+
+Workload (default): Kronecker SCALE 26, edgefactor 16 (2^26 vertices, 2^30
+generated tuples, initiator 0.57/0.19/0.19/0.05), seeded synthetic input,
+CSR built and RCM-relabelled on the GPU, 64 roots drawn uniformly among the
+non-isolated vertices. One step = one BFS from each of the 64 roots.
+
+Metric: harmonic-mean GTEPS over the roots, TEPS_r = m_r / t_r with m_r the
+generated tuples whose first endpoint the search reaches (duplicates and
+self-loops counted, as Graph500 counts generated edges) and t_r the device
+time of the g3_bfs call (CUDA events on the launching stream). Preprocessing
+(CSR build, RCM) is timed once and reported beside the metric, as the paper
+reports RCM time separately (Table 5).
+
+Arms:
+  --impl gb300 (default)  the CUDA library through its C ABI
+  --impl reference        the CPU oracle (serial C) on the host cores, one root
+                          per step -- the paper's method has no runnable
+                          reference implementation
+Multi-GPU: a single-root BFS does not shard; N ranks run N independent
+replicas (weak scaling) and the value is the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--scale", type=int, default=26)
+    ap.add_argument("--edgefactor", type=int, default=16)
+    ap.add_argument("--roots", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--root-seed", type=int, default=2)
+    ap.add_argument("--controller", choices=["heuristic", "learned", "topdown", "bottomup"],
+                    default="heuristic")
+    ap.add_argument("--mlp", default=os.path.join(ROOT, "paper_2012_10026_gb300",
+                                                  "mlp_params.json"))
+    ap.add_argument("--cpu-baseline", type=int, default=1, help="run the oracle leg (rank 0)")
+    ap.add_argument("--cpu-roots", type=int, default=1, help="roots in the oracle sample")
+    ap.add_argument("--cpu-timeout", type=float, default=600.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--stats-out", default="")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def start_clock_sampler(path):
+    try:
+        return subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+
+
+def stop_clock_sampler(proc, path, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+    except FileNotFoundError:
+        return None
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+            "reasons": sorted(reasons)}
+
+
+def level_bytes(st, nb):
+    """Algorithmic bytes of one level's expansion kernels:
+    bottom-up: visited word read, two row bounds per unvisited vertex (8 B
+    streamed), col entry + frontier-bitmap word per examined edge, parent and
+    level per new vertex, next-frontier and visited word writes;
+    top-down: queue entry and two row bounds per frontier vertex, col entry +
+    visited probe per edge, parent, level, queue append and visited write per
+    new vertex."""
+    words = (nb + 31) // 32
+    if st["dir"] == 1:
+        return 4 * words + 8 * st["n_u"] + 8 * st["examined"] + 8 * st["n_next"] + 8 * words
+    return 4 * st["n_f"] + 16 * st["n_f"] + 8 * st["m_f"] + 16 * st["n_next"]
+
+
+def harmonic_gteps(m, t_ms):
+    return len(m) / sum((t / 1e3) / mm for mm, t in zip(m, t_ms)) / 1e9
+
+
+# --------------------------------------------------------- CPU oracle leg
+def _oracle_worker(scale, ef, seed, root_seed, nroots, k, q):
+    """Spawned process: host generation, oracle CSR, oracle BFS on k roots."""
+    try:
+        import numpy as np
+        import graphgen
+        import oracle
+        n = 1 << scale
+        t0 = time.time()
+        src, dst = graphgen.kronecker_edges(scale, ef, seed=seed)
+        roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), nroots, root_seed)
+        t1 = time.time()
+        off, col = oracle.build_csr(src, dst, n)
+        t2 = time.time()
+        res = []
+        for r in roots[:k].tolist():
+            s = time.perf_counter()
+            _, level = oracle.bfs(off, col, r)
+            dt = time.perf_counter() - s
+            m_r = int(np.count_nonzero(level[src] >= 0))
+            res.append((r, m_r, dt))
+        q.put({"ok": True, "gen_s": t1 - t0, "csr_s": t2 - t1, "runs": res})
+    except Exception as e:  # reported, never fatal for the GPU arm
+        q.put({"ok": False, "error": repr(e)})
+
+
+def start_oracle_leg(args, k):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_worker, args=(args.scale, args.edgefactor, args.seed,
+                                                  args.root_seed, args.roots, k, q), daemon=True)
+    p.start()
+    return p, q
+
+
+def finish_oracle_leg(p, q, timeout):
+    try:
+        d = q.get(timeout=timeout)
+    except Exception:
+        p.kill()
+        return None
+    p.join(timeout=10)
+    return d
+
+
+# ------------------------------------------------------------ reference arm
+def reference_arm(args, rank, world):
+    """CPU oracle timed on the host cores, one root per step."""
+    if rank != 0:
+        return
+    import numpy as np
+    import graphgen
+    import oracle
+    n = 1 << args.scale
+    t0 = time.time()
+    src, dst = graphgen.kronecker_edges(args.scale, args.edgefactor, seed=args.seed)
+    roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), args.roots,
+                                args.root_seed)
+    off, col = oracle.build_csr(src, dst, n)
+    setup_s = time.time() - t0
+    ms, tms = [], []
+    for i in range(args.warmup + args.steps):
+        r = int(roots[i % len(roots)])
+        s = time.perf_counter()
+        _, level = oracle.bfs(off, col, r)
+        dt = time.perf_counter() - s
+        if i >= args.warmup:
+            ms.append(int(np.count_nonzero(level[src] >= 0)))
+            tms.append(dt * 1e3)
+    v = harmonic_gteps(ms, tms)
+    line = {
+        "impl": "reference", "metric": "harmonic-mean GTEPS over 64 roots, Kronecker SCALE 26",
+        "value": v, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(tms) / len(tms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"one root per step (roots in draw order), serial oracle "
+                                   f"BFS on the oracle's CSR; setup {setup_s:.1f} s untimed"},
+        "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"kronecker_scale{args.scale}_ef{args.edgefactor}_rcm_{args.roots}roots",
+            "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
+            "initiator": [0.57, 0.19, 0.19, 0.05], "gen_seed": args.seed,
+            "root_seed": args.root_seed, "controller": args.controller,
+            "l2": "256 MB write between roots (L2 flush); CSR larger than L2",
+            "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def gpu_arm(args, rank, world):
+    import numpy as np
+    import torch
+    import graphgen
+    import paper_2012_10026_gb300 as g3
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    oracle_proc = None
+    if rank == 0 and args.cpu_baseline:
+        oracle_proc = start_oracle_leg(args, args.cpu_roots)
+
+    L = g3.lib()
+    n = 1 << args.scale
+    src, dst = graphgen.kronecker_edges_dev(args.scale, args.edgefactor, seed=args.seed)
+    flags = graphgen.nonisolated_flags_dev(src, dst, n).cpu().numpy()
+    roots = graphgen.pick_roots(flags, args.roots, args.root_seed).tolist()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = g3.g3_build_csr(src, dst, n)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g3.g3_rcm_relabel(g)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    info = g.info
+    ctrl = {"heuristic": g3.G3_CTRL_HEURISTIC, "learned": g3.G3_CTRL_LEARNED,
+            "topdown": g3.G3_CTRL_TOPDOWN, "bottomup": g3.G3_CTRL_BOTTOMUP}[args.controller]
+    kw = dict(controller=ctrl, timing=1)
+    mlp_t = None
+    if ctrl == g3.G3_CTRL_LEARNED:
+        with open(args.mlp) as f:
+            mlp_t = torch.tensor(json.load(f)["params"], dtype=torch.float32, device="cuda")
+        kw["mlp_params"] = mlp_t
+    opts = g3.opts(**kw)
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # m_r per root (bookkeeping, outside any timed region)
+    m_r = {}
+    for r in roots:
+        g3.g3_bfs(g, r, parent, level, opts)
+        m_r[r] = int((level[src.long()] >= 0).sum().item()) if n <= (1 << 22) else \
+            int(sum(int((level[src[i:i + (1 << 27)].long()] >= 0).sum().item())
+                    for i in range(0, src.numel(), 1 << 27)))
+    del src, dst
+    torch.cuda.empty_cache()
+
+    ev_s = torch.cuda.Event(enable_timing=True)
+    ev_e = torch.cuda.Event(enable_timing=True)
+
+    def one_step(record):
+        times, stats = [], []
+        for r in roots:
+            flush.fill_(1)
+            ev_s.record()
+            st = g3.g3_bfs(g, r, parent, level, opts, max_stats=256)
+            ev_e.record()
+            ev_e.synchronize()
+            times.append(ev_s.elapsed_time(ev_e))
+            if record:
+                stats.append(st)
+        return times, stats
+
+    for _ in range(args.warmup):
+        one_step(False)
+    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") \
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/g3_clocks_{rank}.csv"
+    sampler = start_clock_sampler(clk_path)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = L.g3_kernel_launches()
+    w0 = time.perf_counter()
+    all_t, all_st = [], []
+    for _ in range(args.steps):
+        t, st = one_step(True)
+        all_t += t
+        all_st += st
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    launches = L.g3_kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    clocks = stop_clock_sampler(sampler, clk_path, local)
+    ms = [m_r[r] for _ in range(args.steps) for r in roots]
+    hm = harmonic_gteps(ms, all_t)
+    # whole-job value: replicas run the same work; take the slowest rank
+    norm = sum((t / 1e3) / mm for mm, t in zip(ms, all_t))
+    if dist:
+        tt = torch.tensor([norm], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        norm = float(tt.item())
+    value = world * len(ms) / norm / 1e9
+
+    # roofline of the dominant kernel
+    nb = info["n_bfs"]
+    agg = {0: [0, 0.0, 0], 1: [0, 0.0, 0]}
+    for st in all_st:
+        for s in st:
+            a = agg[s["dir"]]
+            a[0] += level_bytes(s, nb)
+            a[1] += s["ms_expand"]
+            a[2] += 1
+    dom = 1 if agg[1][1] >= agg[0][1] else 0
+    peak, peak_kind = load_peaks()
+    bytes_, tms, launches_dom = agg[dom]
+    achieved = bytes_ / (tms / 1e3) / 1e9 if tms > 0 else 0.0
+
+    # end to end through the C ABI with pinned host outputs
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.empty(n, dtype=torch.int32).pin_memory()
+        hl = torch.empty(n, dtype=torch.int32).pin_memory()
+        plain = g3.opts(**{k: v for k, v in kw.items() if k != "timing"})
+        et = []
+        for i in range(args.warmup + args.steps):
+            for r in roots:
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                s = time.perf_counter()
+                g3.g3_bfs(g, r, hp, hl, plain)
+                dt = time.perf_counter() - s
+                if i >= args.warmup:
+                    et.append(dt * 1e3)
+        e2e = {"value": harmonic_gteps(ms, et), "unit": "GTEPS", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": len(roots) * 2 * n * 4,
+               "note": "root passed by value; parent[] and level[] copied to pinned host memory"}
+
+    cpu = None
+    if oracle_proc is not None:
+        d = finish_oracle_leg(*oracle_proc, timeout=args.cpu_timeout)
+        if d and d.get("ok"):
+            runs = d["runs"]
+            cpu = {"value": harmonic_gteps([x[1] for x in runs], [x[2] * 1e3 for x in runs]),
+                   "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "sample": f"{len(runs)} of the {len(roots)} roots ({[x[0] for x in runs]}), "
+                             f"serial oracle BFS on the oracle's own CSR of the same graph "
+                             f"(host generation {d['gen_s']:.1f} s and oracle CSR "
+                             f"{d['csr_s']:.1f} s untimed)",
+                   "seconds": [x[2] for x in runs]}
+        else:
+            cpu = {"value": None, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "sample": "oracle leg did not finish: " + (d or {}).get("error", "timeout")}
+
+    if rank == 0:
+        levels = [len(st) for st in all_st]
+        line = {
+            "metric": "harmonic-mean GTEPS over 64 roots, Kronecker SCALE 26; learned vs plain BFS",
+            "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(all_t) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": workload_config(args),
+            "roofline": {"bound": "hbm", "kernel": "bu_pull" if dom == 1 else "td_expand",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind, "launches": launches_dom,
+                         "avg_launch_ms": tms / max(launches_dom, 1),
+                         "bytes_per_launch": bytes_ / max(launches_dom, 1)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks,
+            "wall_s_timed": wall,
+            "graph": {"n": info["n"], "n_plus": info["n_plus"], "nnz": info["nnz"],
+                      "max_degree": info["max_degree"]},
+            "preprocess_s": {"csr_build": t1 - t0, "rcm_relabel": t2 - t1},
+            "per_root_ms": {"min": min(all_t), "median": statistics.median(all_t),
+                            "max": max(all_t)},
+            "levels": {"min": min(levels), "max": max(levels)},
+            "hm_this_rank": hm,
+        }
+        print(json.dumps(line), flush=True)
+        if args.stats_out:
+            with open(args.stats_out, "w") as f:
+                json.dump({"roots": roots, "m_r": [m_r[r] for r in roots], "times_ms": all_t,
+                           "stats": all_st}, f)
+    g.free()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+    else:
+        gpu_arm(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * g3bfs -- C ABI of the GB300 (sm_103a) library for breadth-first search on
+ * RCM-relabelled graphs (Jiang et al., "Fast and Efficient Parallel
+ * Breadth-First Search with Power-law Graph Transformation", PPoPP'21).
+ *
+ * Problem statement (Sec. 2.1): given an undirected, unweighted graph
+ * G = (V, E) and a source s, produce the predecessor map pi with pi(s) = s,
+ * pi(v) = -1 when v is unreachable, and every level-k vertex discovered before
+ * any level-(k+1) vertex. The library also returns level[] (hop distance).
+ *
+ * Pipeline: g3_build_csr (Sec. 3.1) -> g3_rcm_relabel (Algorithm 3, Sec. 3.2)
+ * -> g3_bfs (Algorithm 2 with per-level direction choice; top-down as
+ * Algorithms 1/4, bottom-up as Algorithm 5) -> parent[] / level[] in original
+ * vertex IDs.
+ *
+ * Conventions for every call:
+ *   - Vertex IDs are int32 in [0, n). Edge counts and CSR offsets are int64.
+ *   - "device pointer" = memory the current CUDA device can address (e.g. a
+ *     torch CUDA tensor's data_ptr()); "host pointer" = ordinary host memory.
+ *     Where a call accepts either, it says so and finds out which it got.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Work is stream-ordered. Calls that must read a device-side
+ *     count to size an allocation or to steer a loop synchronise the stream
+ *     before returning; each call states whether it does.
+ *   - Every call returns a g3_status. Calls never abort, trap or print;
+ *     g3_status_str() gives a message, g3_last_error_detail() the detail of
+ *     the last failure on the calling thread.
+ *   - Outputs are caller-owned unless stated. The library owns a g3_graph and
+ *     all device memory behind it until g3_graph_free().
+ *   - A g3_graph is not thread-safe: run one call on it at a time.
+ */
+#ifndef G3BFS_H
+#define G3BFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  G3_OK = 0,
+  G3_EINVAL = 1,   /* bad argument: null pointer, size or ID out of range */
+  G3_ENOMEM = 2,   /* a device or pinned-host allocation failed */
+  G3_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+  G3_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+  G3_ERANGE = 5,   /* a result does not fit the requested output type */
+  G3_ESTATE = 6    /* call not valid in the graph's current state */
+} g3_status;
+
+const char* g3_status_str(g3_status s);
+/* Text of the last failure seen by a g3_* call on this thread ("" if none). */
+const char* g3_last_error_detail(void);
+/* Library version, e.g. "g3bfs 0.1 sm_103a". */
+const char* g3_version(void);
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all devices); for instrumentation. */
+uint64_t g3_kernel_launches(void);
+
+typedef struct g3_graph g3_graph;
+
+typedef struct {
+  int32_t n;          /* vertices of the input (original IDs 0..n-1) */
+  int32_t n_bfs;      /* vertices the BFS graph has: n_plus if relabelled, else n */
+  int32_t n_plus;     /* |V+|, non-isolated vertices (Sec. 3.2) */
+  int32_t relabelled; /* 1 after g3_rcm_relabel */
+  int64_t nnz;        /* directed CSR entries (each undirected edge twice) */
+  int64_t max_degree;
+} g3_graph_info;
+
+/* Builds the cleaned CSR of the undirected graph given by m generated tuples
+ * (src[i], dst[i]) (Sec. 3.1, Eq. 2; both directions stored, Sec. 3.1).
+ * Self-loops and duplicate tuples are removed (the Graph500 generator emits
+ * both, Sec. 4.2); degree(v) is then the row length. Rows are ascending.
+ *   src, dst : device pointers, m int32 entries each, values in [0, n);
+ *              read only; the caller keeps ownership.
+ *   m        : number of tuples, >= 0.   n : vertices, 1 <= n < 2^31.
+ *   out      : receives a new graph owned by the caller (g3_graph_free).
+ * Synchronises `stream` (the entry count sizes an allocation).
+ * Errors: G3_EINVAL (null pointer, n or m out of range, an endpoint outside
+ * [0, n)), G3_ENOMEM, G3_ECUDA. On error *out is NULL. */
+g3_status g3_build_csr(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
+                       void* stream, g3_graph** out);
+
+/* Relabels the graph by Reverse Cuthill-McKee, Algorithm 3 (Sec. 3.2), in
+ * place: V+ in increasing degree, neighbours visited in increasing degree,
+ * each component started from its first unvisited vertex of V+ (the minimal
+ * degree, Sec. 3.2), the Cuthill-McKee order reversed, isolated vertices
+ * appended in ascending original ID and dropped from the BFS graph.
+ * Ties in degree are broken by ascending original ID. The result equals the
+ * serial algorithm exactly; on the GPU it is computed level-synchronously
+ * (level k+1 of a component ordered by the position of its earliest-placed
+ * neighbour in level k, then degree, then ID).
+ * After the call the graph's CSR is the relabelled one over n_plus vertices
+ * (rows ascending) and the permutation is kept for g3_bfs and g3_get_perm.
+ * Synchronises `stream`. Errors: G3_ESTATE (already relabelled), G3_ENOMEM,
+ * G3_ECUDA. */
+g3_status g3_rcm_relabel(g3_graph* g, void* stream);
+
+g3_status g3_graph_info_get(const g3_graph* g, g3_graph_info* info);
+
+/* Copies the permutation (device pointers, n entries each; either may be
+ * NULL): old_of_new[new label] = original ID, new_of_old[original ID] = new
+ * label. Labels [0, n_plus) are V+ in RCM order, [n_plus, n) the isolated
+ * vertices. G3_ESTATE when the graph is not relabelled. Asynchronous. */
+g3_status g3_get_perm(const g3_graph* g, int32_t* old_of_new, int32_t* new_of_old,
+                      void* stream);
+
+/* Copies the current CSR (device pointers): off has n_bfs+1 int64 entries,
+ * col nnz int32 entries. Either may be NULL. Asynchronous. */
+g3_status g3_get_csr(const g3_graph* g, int64_t* off, int32_t* col, void* stream);
+
+/* Frees the graph and every device buffer it owns (synchronises nothing;
+ * the caller must not have work on the graph in flight). NULL is a no-op. */
+void g3_graph_free(g3_graph* g);
+
+/* ---------------------------------------------------------------- BFS */
+
+enum {
+  G3_CTRL_HEURISTIC = 0, /* alpha/beta rule (Sec. 2.1, Beamer), on the device */
+  G3_CTRL_LEARNED = 1,   /* 12-32-4 MLP on the device; paper has no counterpart */
+  G3_CTRL_TOPDOWN = 2,   /* every level top-down (Algorithm 1/4) */
+  G3_CTRL_BOTTOMUP = 3   /* every level after the first bottom-up (Algorithm 5) */
+};
+
+enum { G3_DIR_TD = 0, G3_DIR_BU = 1 };
+
+typedef struct {
+  int32_t controller;       /* G3_CTRL_* */
+  int32_t alpha, beta;      /* heuristic: TD->BU when m_f*alpha > m_u; BU->TD when
+                               the frontier shrank and n_f*beta < n_bfs (14, 24) */
+  int32_t t1, t2, t3;       /* top-down degree bins: thread < t1 <= warp < t2 <=
+                               CTA < t3 <= whole grid (32, 1024, 32768) */
+  int32_t bu_reverse;       /* bottom-up scans each row from its end (highest
+                               label first), the degree-aware order of
+                               Algorithm 6 approximated under RCM */
+  int32_t timing;           /* record per-level CUDA-event times in stats */
+  const float* mlp_params;  /* device pointer, G3_MLP_NPARAMS floats, for
+                               G3_CTRL_LEARNED */
+  int32_t record_both;      /* training-data mode: every level is run both
+                               top-down and bottom-up from the same state and
+                               both are timed (stats t_td_ms, t_bu_ms) */
+  int32_t reserved[7];
+} g3_bfs_opts;
+
+/* Fills the defaults listed above. */
+void g3_bfs_opts_default(g3_bfs_opts* o);
+
+/* Statistics of one level: the frontier F_L expanded at that level. */
+typedef struct {
+  int32_t level;      /* L */
+  int32_t dir;        /* G3_DIR_* used to expand F_L */
+  int64_t n_f;        /* |F_L| */
+  int64_t m_f;        /* sum of degrees over F_L */
+  int64_t n_u;        /* vertices not in levels <= L */
+  int64_t m_u;        /* sum of their degrees */
+  int64_t examined;   /* bottom-up: edges examined (per unvisited vertex, up to
+                         and including the first frontier neighbour); top-down:
+                         m_f */
+  int64_t n_next;     /* |F_{L+1}| */
+  int32_t id_min, id_max; /* smallest / largest BFS-graph label in F_L */
+  int64_t hist[4];    /* F_L vertices with degree in [0,32), [32,1024),
+                         [1024,32768), [32768,inf) */
+  int32_t t1, t2, t3; /* bin thresholds used (top-down levels) */
+  float ms;           /* level time: format conversion, expansion and
+                         controller kernels (opts.timing) */
+  float ms_expand;    /* expansion kernels only: td_front..td_stats for a
+                         top-down level, bu_pull for a bottom-up one */
+  float t_td_ms, t_bu_ms; /* record_both: time of each direction */
+  float mlp_out[4];   /* learned controller outputs for this level */
+} g3_level_stats;
+
+/* Breadth-first search from `root` (original ID) on the graph's current CSR
+ * (Algorithm 2): each level expanded top-down from a frontier queue
+ * (degree-binned thread / warp / CTA / grid work, Algorithms 1 and 4) or
+ * bottom-up over the unvisited vertices with bitmaps and an early exit on
+ * the first parent found (Algorithm 5), as the controller decides.
+ *   parent, level : n int32 entries each (original IDs); device OR host
+ *                   pointers (a host buffer is filled through a device
+ *                   staging copy; pinned memory is fastest).
+ *                   parent[root] = root, level[root] = 0; unreachable and
+ *                   isolated vertices get -1 in both. An isolated root is
+ *                   valid: only the root is reached.
+ *   opts          : NULL = defaults.
+ *   stats         : host array of max_stats entries or NULL; receives one
+ *                   record per level while room remains. *n_levels (may be
+ *                   NULL) receives the number of non-empty frontiers.
+ * The first call on a graph allocates its BFS workspace (about 20 bytes per
+ * vertex); later calls allocate nothing. Synchronises `stream` once per level
+ * (the controller's decision is read back) and before returning.
+ * Errors: G3_EINVAL (root outside [0, n), null parent/level, learned
+ * controller without parameters), G3_ENOMEM, G3_ECUDA. */
+g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, int32_t* parent,
+                 int32_t* level, g3_level_stats* stats, int32_t max_stats,
+                 int32_t* n_levels, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* G3BFS_H */

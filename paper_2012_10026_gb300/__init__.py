@@ -1,0 +1,234 @@
+"""Python binding of libg3bfs (the C ABI declared in include/g3bfs.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels. Tensors are passed as raw pointers (``tensor.data_ptr()``) together
+with the current CUDA stream; PyTorch only provides device memory and
+streams. There is no CPU fallback: if the shared library cannot be loaded the
+import of ``lib()`` raises.
+
+The module-level functions carry the C names (``g3_build_csr``,
+``g3_rcm_relabel``, ``g3_bfs`` ...). ``Graph`` is a small owner object around
+a ``g3_graph*``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libg3bfs.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "g3bfs.h")
+
+G3_OK, G3_EINVAL, G3_ENOMEM, G3_ECUDA, G3_ETIMEOUT, G3_ERANGE, G3_ESTATE = range(7)
+G3_CTRL_HEURISTIC, G3_CTRL_LEARNED, G3_CTRL_TOPDOWN, G3_CTRL_BOTTOMUP = range(4)
+G3_DIR_TD, G3_DIR_BU = 0, 1
+MLP_NPARAMS = 32 * 12 + 32 + 4 * 32 + 4
+
+
+class G3Error(RuntimeError):
+    def __init__(self, status, where, detail):
+        super().__init__(f"{where}: {detail} (status {status})")
+        self.status = status
+
+
+class g3_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_bfs", ctypes.c_int32), ("n_plus", ctypes.c_int32),
+                ("relabelled", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("max_degree", ctypes.c_int64)]
+
+
+class g3_bfs_opts(ctypes.Structure):
+    _fields_ = [("controller", ctypes.c_int32), ("alpha", ctypes.c_int32),
+                ("beta", ctypes.c_int32), ("t1", ctypes.c_int32), ("t2", ctypes.c_int32),
+                ("t3", ctypes.c_int32), ("bu_reverse", ctypes.c_int32),
+                ("timing", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
+                ("record_both", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class g3_level_stats(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("dir", ctypes.c_int32), ("n_f", ctypes.c_int64),
+                ("m_f", ctypes.c_int64), ("n_u", ctypes.c_int64), ("m_u", ctypes.c_int64),
+                ("examined", ctypes.c_int64), ("n_next", ctypes.c_int64),
+                ("id_min", ctypes.c_int32), ("id_max", ctypes.c_int32),
+                ("hist", ctypes.c_int64 * 4), ("t1", ctypes.c_int32), ("t2", ctypes.c_int32),
+                ("t3", ctypes.c_int32), ("ms", ctypes.c_float), ("ms_expand", ctypes.c_float),
+                ("t_td_ms", ctypes.c_float), ("t_bu_ms", ctypes.c_float),
+                ("mlp_out", ctypes.c_float * 4)]
+
+    def to_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["hist"] = list(self.hist)
+        d["mlp_out"] = list(self.mlp_out)
+        return d
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "g3_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "g3_last_error_detail": (ctypes.c_char_p, []),
+    "g3_version": (ctypes.c_char_p, []),
+    "g3_kernel_launches": (ctypes.c_uint64, []),
+    "g3_build_csr": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp,
+                                    ctypes.POINTER(_vp)]),
+    "g3_rcm_relabel": (ctypes.c_int, [_vp, _vp]),
+    "g3_graph_info_get": (ctypes.c_int, [_vp, ctypes.POINTER(g3_graph_info)]),
+    "g3_get_perm": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "g3_get_csr": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "g3_graph_free": (None, [_vp]),
+    "g3_bfs_opts_default": (None, [ctypes.POINTER(g3_bfs_opts)]),
+    "g3_bfs": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(g3_bfs_opts), _vp, _vp,
+                              ctypes.POINTER(g3_level_stats), ctypes.c_int32,
+                              ctypes.POINTER(ctypes.c_int32), _vp]),
+}
+
+
+def lib():
+    """Loads the in-tree libg3bfs.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"libg3bfs.so not built ({LIB_PATH}); run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Function names declared in include/g3bfs.h."""
+    import re
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(g3_[a-z0-9_]+)\s*\(", txt)) - {"g3_graph"})
+
+
+def _check(st, where):
+    if st != G3_OK:
+        L = lib()
+        raise G3Error(st, where, L.g3_last_error_detail().decode() or
+                      L.g3_status_str(st).decode())
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def opts(**kw) -> g3_bfs_opts:
+    o = g3_bfs_opts()
+    lib().g3_bfs_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "mlp_params":
+            v = ctypes.c_void_p(v.data_ptr() if hasattr(v, "data_ptr") else v)
+        setattr(o, k, v)
+    return o
+
+
+# ------------------------------------------------------------- C-named calls
+def g3_build_csr(src, dst, n: int, stream=None) -> "Graph":
+    """Cleaned CSR of the undirected graph of int32 device tuples (src, dst)."""
+    assert src.is_cuda and dst.is_cuda and src.numel() == dst.numel()
+    g = ctypes.c_void_p()
+    _check(lib().g3_build_csr(_ptr(src), _ptr(dst), src.numel(), int(n), _stream(stream),
+                              ctypes.byref(g)), "g3_build_csr")
+    return Graph(g)
+
+
+def g3_rcm_relabel(graph: "Graph", stream=None):
+    _check(lib().g3_rcm_relabel(graph.handle, _stream(stream)), "g3_rcm_relabel")
+
+
+def g3_graph_info_get(graph: "Graph") -> dict:
+    info = g3_graph_info()
+    _check(lib().g3_graph_info_get(graph.handle, ctypes.byref(info)), "g3_graph_info_get")
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def g3_get_perm(graph: "Graph", old_of_new=None, new_of_old=None, stream=None):
+    _check(lib().g3_get_perm(graph.handle, _ptr(old_of_new) if old_of_new is not None else None,
+                             _ptr(new_of_old) if new_of_old is not None else None,
+                             _stream(stream)), "g3_get_perm")
+
+
+def g3_get_csr(graph: "Graph", off=None, col=None, stream=None):
+    _check(lib().g3_get_csr(graph.handle, _ptr(off) if off is not None else None,
+                            _ptr(col) if col is not None else None, _stream(stream)),
+           "g3_get_csr")
+
+
+def g3_bfs(graph: "Graph", root: int, parent, level, options: g3_bfs_opts | None = None,
+           max_stats: int = 0, stream=None):
+    """BFS from root (original ID) into parent/level (int32, n entries, device
+    tensors or host tensors/arrays). Returns the list of per-level stats."""
+    stats = (g3_level_stats * max_stats)() if max_stats > 0 else None
+    nlev = ctypes.c_int32(0)
+
+    def addr(x):
+        if hasattr(x, "data_ptr"):
+            return ctypes.c_void_p(x.data_ptr())
+        return ctypes.c_void_p(x.ctypes.data)
+
+    _check(lib().g3_bfs(graph.handle, int(root),
+                        ctypes.byref(options) if options is not None else None,
+                        addr(parent), addr(level), stats, max_stats, ctypes.byref(nlev),
+                        _stream(stream)), "g3_bfs")
+    if stats is None:
+        return []
+    return [stats[i].to_dict() for i in range(min(nlev.value, max_stats))]
+
+
+def g3_graph_free(graph: "Graph"):
+    graph.free()
+
+
+class Graph:
+    """Owner of a g3_graph*; frees it on free() or garbage collection."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+
+    def free(self):
+        if self.handle and self.handle.value:
+            import torch
+            torch.cuda.synchronize()
+            lib().g3_graph_free(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self.handle and self.handle.value:
+                lib().g3_graph_free(self.handle)
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        return g3_graph_info_get(self)
+
+    def perm(self, device="cuda"):
+        import torch
+        n = self.info["n"]
+        a = torch.empty(n, dtype=torch.int32, device=device)
+        b = torch.empty(n, dtype=torch.int32, device=device)
+        g3_get_perm(self, a, b)
+        return a, b
+
+    def csr(self, device="cuda"):
+        import torch
+        i = self.info
+        off = torch.empty(i["n_bfs"] + 1, dtype=torch.int64, device=device)
+        col = torch.empty(max(i["nnz"], 1), dtype=torch.int32, device=device)
+        g3_get_csr(self, off, col)
+        return off, col[:i["nnz"]]

@@ -1,0 +1,783 @@
+// Hybrid breadth-first search (Algorithm 2) on the graph's current CSR.
+//
+// Per level L the frontier F_L is either a queue (after a top-down level) or
+// a bitmap (after a bottom-up level). A one-warp controller kernel decides
+// the direction of every level on the device from the frontier statistics;
+// the host reads the decision back (one small copy per level) and launches:
+//
+//   top-down (Algorithms 1 and 4): td_front walks the queue one thread per
+//     vertex; vertices with degree < t1 are expanded on the spot, the others
+//     go to three bins expanded by one warp (t1 <= deg < t2), one CTA
+//     (t2 <= deg < t3) or the whole grid (deg >= t3) -- the GPU form of
+//     Algorithm 4's even split of a long neighbour list over all threads.
+//     Neighbour lists are read with aligned 128-bit loads. A neighbour is
+//     claimed by an atomicOr on its word of the visited bitmap; the winner
+//     writes parent/level and appends it to the next queue with one
+//     warp-aggregated atomic per warp.
+//   bottom-up (Algorithm 5): one warp per 32-vertex word of the visited
+//     bitmap; each unvisited vertex scans its row until the first neighbour
+//     whose bit is set in the current-frontier bitmap (early break). The
+//     word's owner writes the next-frontier word and ORs it into visited (no
+//     atomics: the paper's "visited |= F_next" folded into the same pass).
+//
+// Statistics of the next frontier (size, degree sum, label range, degree
+// histogram, edges examined) are reduced per block and added with one atomic
+// per block.
+#include <math.h>
+#include <string.h>
+
+#include "g3_prims.cuh"
+
+#define G3_MAX_LEVELS_GUARD (1 << 30)
+#define BFS_GRID (G3_NUM_SMS * 8)
+
+// Device-side controller record; mirrored to pinned host memory each level.
+struct Ctrl {
+  // accumulators for the frontier being produced (reset before expansion)
+  unsigned long long q_len;     // top-down: next queue length
+  unsigned long long nx_nf;     // bottom-up: next frontier size
+  unsigned long long nx_mf;     // sum of degrees of the next frontier
+  unsigned long long nx_exam;   // bottom-up: edges examined
+  unsigned long long nx_hist[4];
+  unsigned int nx_min, nx_max;
+  unsigned long long bin_len[4];  // top-down bins of the current level
+  unsigned long long conv_len;    // bitmap -> queue conversion length
+  // current frontier F_L and its decision
+  long long nf, mf, nu, mu, exam_prev;
+  long long hist[4];
+  int id_min, id_max;
+  int level;
+  int dir;
+  int t1, t2, t3;
+  float mlp_out[4];
+  long long prev_nf;
+  long long n_visited, m_visited;
+};
+
+struct g3_bfs_ws {
+  int32_t nb;
+  int64_t nwords;
+  uint32_t *visited, *fa, *fb, *vis_save;
+  int32_t *qa, *qb, *bins;  // bins: 3 segments of nb entries (warp, CTA, grid)
+  int32_t *parent, *level;  // BFS-graph labels
+  int32_t *out_parent, *out_level;  // staging for host outputs (n entries)
+  Ctrl* ctrl;
+  Ctrl* h_ctrl;  // pinned
+  cudaEvent_t ev[4];
+};
+
+void g3_bfs_ws_free(g3_bfs_ws* ws) {
+  if (!ws) return;
+  void* all[] = {ws->visited, ws->fa, ws->fb, ws->vis_save, ws->qa, ws->qb, ws->bins,
+                 ws->parent, ws->level, ws->out_parent, ws->out_level, ws->ctrl};
+  for (void* p : all)
+    if (p) cudaFree(p);
+  if (ws->h_ctrl) cudaFreeHost(ws->h_ctrl);
+  for (int i = 0; i < 4; ++i)
+    if (ws->ev[i]) cudaEventDestroy(ws->ev[i]);
+  free(ws);
+}
+
+static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
+  g3_bfs_ws* ws = (g3_bfs_ws*)calloc(1, sizeof(g3_bfs_ws));
+  if (!ws) return G3_ENOMEM;
+  ws->nb = g->n_bfs;
+  ws->nwords = ((int64_t)g->n_bfs + 31) / 32;
+  const size_t nb1 = (size_t)g->n_bfs + 4, nw = (size_t)ws->nwords + 4, n1 = (size_t)g->n + 4;
+  struct {
+    void** p;
+    size_t bytes;
+  } req[] = {
+      {(void**)&ws->visited, nw * 4},     {(void**)&ws->fa, nw * 4},
+      {(void**)&ws->fb, nw * 4},          {(void**)&ws->vis_save, nw * 4},
+      {(void**)&ws->qa, nb1 * 4},         {(void**)&ws->qb, nb1 * 4},
+      {(void**)&ws->bins, nb1 * 4 * 3},   {(void**)&ws->parent, nb1 * 4},
+      {(void**)&ws->level, nb1 * 4},      {(void**)&ws->out_parent, n1 * 4},
+      {(void**)&ws->out_level, n1 * 4},   {(void**)&ws->ctrl, sizeof(Ctrl)},
+  };
+  for (auto& r : req) {
+    cudaError_t e = cudaMalloc(r.p, r.bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g3_set_error("g3_bfs workspace: cudaMalloc(%zu): %s", r.bytes, cudaGetErrorString(e));
+      g3_bfs_ws_free(ws);
+      return G3_ENOMEM;
+    }
+  }
+  if (cudaMallocHost((void**)&ws->h_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+    cudaGetLastError();
+    g3_bfs_ws_free(ws);
+    return G3_ENOMEM;
+  }
+  for (int i = 0; i < 4; ++i)
+    if (cudaEventCreate(&ws->ev[i]) != cudaSuccess) {
+      cudaGetLastError();
+      g3_bfs_ws_free(ws);
+      return G3_ECUDA;
+    }
+  *out = ws;
+  return G3_OK;
+}
+
+// ----------------------------------------------------------- device helpers
+__device__ __forceinline__ int deg_bucket(int64_t d) {
+  return d < 32 ? 0 : (d < 1024 ? 1 : (d < 32768 ? 2 : 3));
+}
+
+struct StatAcc {
+  unsigned long long nf, mf, ex, h[4];
+  unsigned int mn, mx;
+  __device__ void init() {
+    nf = mf = ex = 0;
+    h[0] = h[1] = h[2] = h[3] = 0;
+    mn = 0xFFFFFFFFu;
+    mx = 0;
+  }
+  __device__ void add_vertex(int32_t v, int64_t d) {
+    nf++;
+    mf += (unsigned long long)d;
+    h[deg_bucket(d)]++;
+    mn = min(mn, (unsigned)v);
+    mx = max(mx, (unsigned)v);
+  }
+  // block reduction then one atomic per block and field
+  __device__ void flush(Ctrl* c, bool with_nf) {
+    __shared__ unsigned long long s[8][8];
+    __shared__ unsigned int smn[8], smx[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long v[7] = {nf, mf, ex, h[0], h[1], h[2], h[3]};
+    unsigned a = mn, b = mx;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+      a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if (lane == 0) {
+      for (int k = 0; k < 7; ++k) s[warp][k] = v[k];
+      smn[warp] = a;
+      smx[warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t[7] = {0, 0, 0, 0, 0, 0, 0};
+      unsigned tmn = 0xFFFFFFFFu, tmx = 0;
+      for (int w = 0; w < nw; ++w) {
+        for (int k = 0; k < 7; ++k) t[k] += s[w][k];
+        tmn = min(tmn, smn[w]);
+        tmx = max(tmx, smx[w]);
+      }
+      if (with_nf && t[0]) atomicAdd(&c->nx_nf, t[0]);
+      if (t[1]) atomicAdd(&c->nx_mf, t[1]);
+      if (t[2]) atomicAdd(&c->nx_exam, t[2]);
+      for (int k = 0; k < 4; ++k)
+        if (t[3 + k]) atomicAdd(&c->nx_hist[k], t[3 + k]);
+      if (t[0]) {
+        atomicMin(&c->nx_min, tmn);
+        atomicMax(&c->nx_max, tmx);
+      }
+    }
+  }
+};
+
+__device__ __forceinline__ bool td_claim(uint32_t* visited, int32_t w) {
+  const uint32_t bit = 1u << (w & 31);
+  uint32_t* word = &visited[w >> 5];
+  if (__ldcg(word) & bit) return false;
+  return !(atomicOr(word, bit) & bit);
+}
+
+// ------------------------------------------------------------------- init
+__global__ void bfs_init(int32_t nb, int64_t nwords, uint32_t* visited, int32_t* parent,
+                         int32_t* level) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    parent[i] = -1;
+    level[i] = -1;
+    if (i < nwords) visited[i] = 0u;
+  }
+  for (int64_t i = nb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
+       i += (int64_t)gridDim.x * blockDim.x)
+    visited[i] = 0u;
+}
+
+// Sets up F_0 = {root} (root_new < 0 or >= nb: no BFS-graph vertex).
+__global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, int64_t nnz,
+                         const int64_t* off, uint32_t* visited, int32_t* parent,
+                         int32_t* level, int32_t* q, Ctrl* c, int t1, int t2, int t3) {
+  int32_t r = new_of_old ? new_of_old[root] : root;
+  memset(c, 0, sizeof(Ctrl));
+  c->t1 = t1;
+  c->t2 = t2;
+  c->t3 = t3;
+  c->dir = G3_DIR_TD;  // Algorithm 2 starts top-down
+  c->nx_min = 0xFFFFFFFFu;
+  if (r < 0 || r >= nb) {
+    c->nf = 0;
+    c->nu = nb;
+    c->mu = nnz;
+    return;
+  }
+  visited[r >> 5] |= 1u << (r & 31);
+  parent[r] = r;
+  level[r] = 0;
+  q[0] = r;
+  long long d = off[r + 1] - off[r];
+  c->nf = 1;
+  c->mf = d;
+  c->hist[deg_bucket(d)] = 1;
+  c->id_min = c->id_max = r;
+  c->n_visited = 1;
+  c->m_visited = d;
+  c->nu = nb - 1;
+  c->mu = nnz - d;
+  c->prev_nf = 0;
+}
+
+__global__ void bfs_reset_next(Ctrl* c) {
+  c->q_len = 0;
+  c->nx_nf = 0;
+  c->nx_mf = 0;
+  c->nx_exam = 0;
+  for (int k = 0; k < 4; ++k) {
+    c->nx_hist[k] = 0;
+    c->bin_len[k] = 0;
+  }
+  c->nx_min = 0xFFFFFFFFu;
+  c->nx_max = 0;
+  c->conv_len = 0;
+}
+
+// --------------------------------------------------------------- top-down
+struct TdArgs {
+  const int64_t* off;
+  const int32_t* col;
+  uint32_t* visited;
+  int32_t* parent;
+  int32_t* level;
+  int32_t lnext;
+  int32_t* qnext;
+  Ctrl* c;
+};
+
+// Claims w for v; appends claimed vertices with one atomic per warp. All 32
+// lanes must call it together.
+__device__ __forceinline__ void td_visit(const TdArgs& a, bool has, int32_t w, int32_t v) {
+  bool claim = has && td_claim(a.visited, w);
+  if (claim) {
+    a.parent[w] = v;
+    a.level[w] = a.lnext;
+  }
+  g3_warp_append(0xffffffffu, claim, w, a.qnext, &a.c->q_len);
+}
+
+// Processes row entries [b, e) of vertex v with `nthr` cooperating threads
+// (index t), four entries per thread per step through aligned 128-bit loads.
+// Every lane of each participating warp runs the same number of steps.
+__device__ __forceinline__ void td_row_vec4(const TdArgs& a, int32_t v, int64_t b, int64_t e,
+                                            int64_t t, int64_t nthr, int64_t steps) {
+  const int64_t a0 = b & ~3ll;
+  for (int64_t s = 0; s < steps; ++s) {
+    const int64_t j = a0 + 4 * (t + s * nthr);
+    int4 x = make_int4(0, 0, 0, 0);
+    if (j < e) x = *reinterpret_cast<const int4*>(a.col + j);
+    td_visit(a, j + 0 >= b && j + 0 < e, x.x, v);
+    td_visit(a, j + 1 >= b && j + 1 < e, x.y, v);
+    td_visit(a, j + 2 >= b && j + 2 < e, x.z, v);
+    td_visit(a, j + 3 >= b && j + 3 < e, x.w, v);
+  }
+}
+
+__global__ void __launch_bounds__(256) td_front(TdArgs a, const int32_t* __restrict__ q,
+                                                int64_t qlen, int32_t* bins, int64_t nb1) {
+  const int t1 = a.c->t1, t2 = a.c->t2, t3 = a.c->t3;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < qlen;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const bool act = i < qlen;
+    int32_t v = act ? q[i] : 0;
+    int64_t b = act ? a.off[v] : 0, e = act ? a.off[v + 1] : 0, d = e - b;
+    bool small = act && d < t1;
+    int bin = !act || small ? -1 : (d < t2 ? 0 : (d < t3 ? 1 : 2));
+    for (int k = 0; k < 3; ++k)
+      g3_warp_append(0xffffffffu, bin == k, v, bins + k * nb1, &a.c->bin_len[1 + k]);
+    const int cnt = small ? (int)d : 0;
+    const int maxc = __reduce_max_sync(0xffffffffu, cnt);
+    for (int k = 0; k < maxc; ++k) {
+      bool has = k < cnt;
+      int32_t w = has ? a.col[b + k] : 0;
+      td_visit(a, has, w, v);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) td_warp(TdArgs a, const int32_t* __restrict__ bin) {
+  const int64_t len = (int64_t)a.c->bin_len[1];
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < len; i += nwarps) {
+    int32_t v = bin[i];
+    int64_t b = a.off[v], e = a.off[v + 1];
+    int64_t steps = (e - (b & ~3ll) + 127) / 128;
+    td_row_vec4(a, v, b, e, lane, 32, steps);
+  }
+}
+
+__global__ void __launch_bounds__(256) td_cta(TdArgs a, const int32_t* __restrict__ bin) {
+  const int64_t len = (int64_t)a.c->bin_len[2];
+  for (int64_t i = blockIdx.x; i < len; i += gridDim.x) {
+    int32_t v = bin[i];
+    int64_t b = a.off[v], e = a.off[v + 1];
+    int64_t steps = (e - (b & ~3ll) + 4 * blockDim.x - 1) / (4 * blockDim.x);
+    td_row_vec4(a, v, b, e, threadIdx.x, blockDim.x, steps);
+  }
+}
+
+__global__ void __launch_bounds__(256) td_grid(TdArgs a, const int32_t* __restrict__ bin) {
+  const int64_t len = (int64_t)a.c->bin_len[3];
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = 0; i < len; ++i) {
+    int32_t v = bin[i];
+    int64_t b = a.off[v], e = a.off[v + 1];
+    int64_t steps = (e - (b & ~3ll) + 4 * nthr - 1) / (4 * nthr);
+    td_row_vec4(a, v, b, e, t, nthr, steps);
+  }
+}
+
+// Statistics of the queue F_{L+1} produced by a top-down level.
+__global__ void __launch_bounds__(256) td_stats(const int32_t* __restrict__ q,
+                                                const int64_t* __restrict__ off, Ctrl* c) {
+  const int64_t len = (int64_t)c->q_len;
+  StatAcc acc;
+  acc.init();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = q[i];
+    acc.add_vertex(v, off[v + 1] - off[v]);
+  }
+  acc.flush(c, true);
+}
+
+// -------------------------------------------------------------- bottom-up
+__global__ void __launch_bounds__(256) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
+                                               const uint32_t* __restrict__ fcur,
+                                               uint32_t* __restrict__ fnext,
+                                               const int64_t* __restrict__ off,
+                                               const int32_t* __restrict__ col,
+                                               int32_t* parent, int32_t* level, int32_t lnext,
+                                               int reverse, Ctrl* c) {
+  StatAcc acc;
+  acc.init();
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t word = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; word < nwords;
+       word += nwarps) {
+    const uint32_t vis = visited[word];
+    const int64_t v = word * 32 + lane;
+    const bool cand = v < nb && !((vis >> lane) & 1u);
+    if (!__any_sync(0xffffffffu, cand)) {
+      if (lane == 0) fnext[word] = 0u;
+      continue;
+    }
+    bool found = false;
+    int64_t d = 0;
+    if (cand) {
+      const int64_t b = off[v], e = off[v + 1];
+      d = e - b;
+      int64_t k = 0;
+      int32_t par = -1;
+      for (; k < d; ++k) {
+        const int32_t w = col[reverse ? e - 1 - k : b + k];
+        if ((__ldg(&fcur[w >> 5]) >> (w & 31)) & 1u) {
+          par = w;
+          ++k;
+          break;
+        }
+      }
+      acc.ex += (unsigned long long)k;
+      if (par >= 0) {
+        found = true;
+        parent[v] = par;
+        level[v] = lnext;
+      }
+    }
+    const uint32_t nbits = __ballot_sync(0xffffffffu, found);
+    if (lane == 0) {
+      fnext[word] = nbits;
+      if (nbits) visited[word] = vis | nbits;
+    }
+    if (found) acc.add_vertex((int32_t)v, d);
+  }
+  acc.flush(c, true);
+}
+
+// ------------------------------------------------------------ conversions
+__global__ void q_to_bitmap(const int32_t* __restrict__ q, int64_t len, uint32_t* bm) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = q[i];
+    atomicOr(&bm[v >> 5], 1u << (v & 31));
+  }
+}
+
+__global__ void bitmap_to_q(const uint32_t* __restrict__ bm, int64_t nwords, int32_t* q,
+                            unsigned long long* len) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+       base < nwords; base += nwarps * 32) {
+    const int64_t w = base + lane;
+    uint32_t bits = w < nwords ? bm[w] : 0u;
+    unsigned c = __popc(bits), inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, inc, 31);
+    if (total == 0) continue;
+    unsigned long long start = 0;
+    if (lane == 31) start = atomicAdd(len, (unsigned long long)total);
+    start = __shfl_sync(0xffffffffu, start, 31);
+    unsigned long long p = start + inc - c;
+    while (bits) {
+      int b = __ffs(bits) - 1;
+      q[p++] = (int32_t)(w * 32 + b);
+      bits &= bits - 1u;
+    }
+  }
+}
+
+// ------------------------------------------------------------- controller
+// Learned controller: 12-32-4 MLP (ReLU) evaluated by one warp, lane j =
+// hidden unit j. Parameter layout: W1[32][12], b1[32], W2[4][32], b2[4].
+__device__ void mlp_features(const Ctrl* c, int32_t nb, int prev_dir, float* f) {
+  const float nf = (float)c->nf, mf = (float)c->mf, nu = (float)c->nu, mu = (float)c->mu;
+  f[0] = log2f(1.f + nf);
+  f[1] = log2f(1.f + mf);
+  f[2] = log2f(1.f + nu);
+  f[3] = log2f(1.f + mu);
+  f[4] = (c->nf > 0 && nb > 0) ? (float)(c->id_max - c->id_min) / (float)nb : 0.f;
+  f[5] = log2f((1.f + mf) / (1.f + mu));
+  f[6] = (float)c->level / 32.f;
+  f[7] = (float)prev_dir;
+  const float tot = c->nf > 0 ? (float)c->nf : 1.f;
+  for (int k = 0; k < 4; ++k) f[8 + k] = (float)c->hist[k] / tot;
+}
+
+__device__ void mlp_eval_warp(const float* __restrict__ P, const float* f, float* out) {
+  const int j = threadIdx.x & 31;
+  const float* W1 = P;
+  const float* b1 = P + 32 * 12;
+  const float* W2 = b1 + 32;
+  const float* b2 = W2 + 4 * 32;
+  float z = b1[j];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) z = fmaf(W1[j * 12 + i], f[i], z);
+  const float h = fmaxf(z, 0.f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float s = W2[k * 32 + j] * h;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    out[k] = s + b2[k];
+  }
+}
+
+__device__ __forceinline__ int clamp_thr(float lg, int lo, int hi) {
+  float x = fminf(fmaxf(rintf(lg), (float)lo), (float)hi);
+  return 1 << (int)x;
+}
+
+// After the expansion of level L: promote the produced frontier to F_{L+1},
+// update the visited totals and decide its direction.
+__global__ void bfs_control(Ctrl* c, int32_t nb, int64_t nnz, int controller, int alpha,
+                            int beta, const float* __restrict__ mlp, int t1d, int t2d, int t3d,
+                            int was_td) {
+  __shared__ float feat[12];
+  __shared__ int decide;
+  const int lane = threadIdx.x;
+  if (lane == 0) {
+    const int prev_dir = c->dir;
+    const long long prev_nf = c->nf;
+    const long long nf = was_td ? (long long)c->q_len : (long long)c->nx_nf;
+    c->exam_prev = (long long)c->nx_exam;
+    c->nf = nf;
+    c->mf = (long long)c->nx_mf;
+    for (int k = 0; k < 4; ++k) c->hist[k] = (long long)c->nx_hist[k];
+    c->id_min = nf ? (int)c->nx_min : 0;
+    c->id_max = nf ? (int)c->nx_max : 0;
+    c->n_visited += nf;
+    c->m_visited += c->mf;
+    c->nu = nb - c->n_visited;
+    c->mu = nnz - c->m_visited;
+    c->level += 1;
+    c->prev_nf = prev_nf;
+    int d;
+    if (controller == G3_CTRL_TOPDOWN) {
+      d = G3_DIR_TD;
+    } else if (controller == G3_CTRL_BOTTOMUP) {
+      d = G3_DIR_BU;
+    } else if (prev_dir == G3_DIR_TD) {
+      d = (c->mf * (long long)alpha > c->mu) ? G3_DIR_BU : G3_DIR_TD;
+    } else {
+      d = (nf < prev_nf && nf * (long long)beta < (long long)nb) ? G3_DIR_TD : G3_DIR_BU;
+    }
+    c->t1 = t1d;
+    c->t2 = t2d;
+    c->t3 = t3d;
+    decide = d;
+    if (controller == G3_CTRL_LEARNED) mlp_features(c, nb, prev_dir, feat);
+  }
+  __syncwarp();
+  if (controller == G3_CTRL_LEARNED) {
+    float out[4];
+    mlp_eval_warp(mlp, feat, out);
+    if (lane == 0) {
+      for (int k = 0; k < 4; ++k) c->mlp_out[k] = out[k];
+      decide = out[0] < 0.f ? G3_DIR_BU : G3_DIR_TD;
+      int a1 = clamp_thr(out[1], 2, 12), a2 = clamp_thr(out[2], 6, 18),
+          a3 = clamp_thr(out[3], 10, 26);
+      if (a2 <= a1) a2 = a1 * 2;
+      if (a3 <= a2) a3 = a2 * 2;
+      c->t1 = a1;
+      c->t2 = a2;
+      c->t3 = a3;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) c->dir = decide;
+}
+
+// --------------------------------------------------------- output mapping
+__global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
+                              const int32_t* __restrict__ new_of_old,
+                              const int32_t* __restrict__ old_of_new,
+                              const int32_t* __restrict__ parent_new,
+                              const int32_t* __restrict__ level_new, int32_t* parent,
+                              int32_t* level) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t p = -1, l = -1;
+    int32_t x = new_of_old ? new_of_old[v] : (int32_t)v;
+    if (x < nb) {
+      l = level_new[x];
+      if (l >= 0) {
+        int32_t pn = parent_new[x];
+        p = old_of_new ? old_of_new[pn] : pn;
+      }
+    }
+    if (v == root) {
+      p = root;
+      l = 0;
+    }
+    parent[v] = p;
+    level[v] = l;
+  }
+}
+
+// ------------------------------------------------------------------ host
+extern "C" void g3_bfs_opts_default(g3_bfs_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->controller = G3_CTRL_HEURISTIC;
+  o->alpha = 14;
+  o->beta = 24;
+  o->t1 = 32;
+  o->t2 = 1024;
+  o->t3 = 32768;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct Level {
+  g3_graph* g;
+  g3_bfs_ws* ws;
+  const g3_bfs_opts* o;
+  cudaStream_t s;
+  uint32_t *fcur, *fnext;
+  int32_t *qcur, *qnext;
+  bool fmt_queue;
+};
+
+// Top-down expansion of F_L (queue qcur of length nf) into qnext.
+static g3_status run_td(Level& S, int64_t nf, int32_t lnext) {
+  g3_bfs_ws* ws = S.ws;
+  cudaStream_t s = S.s;
+  if (!S.fmt_queue) {
+    bitmap_to_q<<<g3_grid_for(ws->nwords, 256, BFS_GRID), 256, 0, s>>>(
+        S.fcur, ws->nwords, S.qcur, &ws->ctrl->conv_len);
+    G3_CHECK_LAUNCH();
+  }
+  if (S.o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[1], s));
+  TdArgs a{S.g->off, S.g->col, ws->visited, ws->parent, ws->level, lnext, S.qnext, ws->ctrl};
+  const int64_t nb1 = ws->nb + 4;
+  td_front<<<g3_grid_for(nf, 256, BFS_GRID * 2), 256, 0, s>>>(a, S.qcur, nf, ws->bins, nb1);
+  G3_CHECK_LAUNCH();
+  td_warp<<<g3_grid_for(nf, 8, BFS_GRID), 256, 0, s>>>(a, ws->bins);
+  G3_CHECK_LAUNCH();
+  td_cta<<<g3_grid_for(nf, 1, BFS_GRID), 256, 0, s>>>(a, ws->bins + nb1);
+  G3_CHECK_LAUNCH();
+  td_grid<<<G3_NUM_SMS * 4, 256, 0, s>>>(a, ws->bins + 2 * nb1);
+  G3_CHECK_LAUNCH();
+  td_stats<<<g3_grid_for(ws->nb, 256, BFS_GRID), 256, 0, s>>>(S.qnext, S.g->off, ws->ctrl);
+  G3_CHECK_LAUNCH();
+  return G3_OK;
+}
+
+// Bottom-up expansion of F_L (bitmap) into fnext.
+static g3_status run_bu(Level& S, int64_t nf, int32_t lnext) {
+  g3_bfs_ws* ws = S.ws;
+  cudaStream_t s = S.s;
+  if (S.fmt_queue) {
+    G3_TRY_CUDA(cudaMemsetAsync(S.fcur, 0, (size_t)ws->nwords * 4, s));
+    q_to_bitmap<<<g3_grid_for(nf, 256), 256, 0, s>>>(S.qcur, nf, S.fcur);
+    G3_CHECK_LAUNCH();
+  }
+  if (S.o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[1], s));
+  bu_pull<<<BFS_GRID, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.fcur, S.fnext, S.g->off,
+                                   S.g->col, ws->parent, ws->level, lnext, S.o->bu_reverse,
+                                   ws->ctrl);
+  G3_CHECK_LAUNCH();
+  return G3_OK;
+}
+
+static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32_t* parent,
+                          int32_t* level, g3_level_stats* stats, int32_t max_stats,
+                          int32_t* n_levels, cudaStream_t s) {
+  if (!g->ws) G3_TRY(ws_create(g, &g->ws));
+  g3_bfs_ws* ws = g->ws;
+  const int32_t nb = ws->nb;
+  const int64_t nnz = g->nnz;
+  Ctrl* h = ws->h_ctrl;
+
+  bfs_init<<<g3_grid_for(nb > ws->nwords ? nb : ws->nwords, 256), 256, 0, s>>>(
+      nb, ws->nwords, ws->visited, ws->parent, ws->level);
+  G3_CHECK_LAUNCH();
+  bfs_root<<<1, 1, 0, s>>>(g->relabelled ? g->new_of_old : nullptr, root, nb, nnz, g->off,
+                           ws->visited, ws->parent, ws->level, ws->qa, ws->ctrl, o->t1, o->t2,
+                           o->t3);
+  G3_CHECK_LAUNCH();
+
+  Level S{g, ws, o, s, ws->fa, ws->fb, ws->qa, ws->qb, true};
+  int32_t L = 0;
+  int nrec = 0;
+  for (;; ++L) {
+    G3_TRY_CUDA(cudaMemcpyAsync(h, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    G3_TRY_CUDA(cudaStreamSynchronize(s));
+    if (L > 0 && stats && nrec - 1 < max_stats && nrec >= 1) {
+      // close the previous record: examined edges and next size
+      g3_level_stats& r = stats[nrec - 1];
+      r.n_next = h->nf;
+      if (r.dir == G3_DIR_BU) r.examined = h->exam_prev;
+      if (o->timing) {
+        cudaEventElapsedTime(&r.ms, ws->ev[0], ws->ev[3]);
+        cudaEventElapsedTime(&r.ms_expand, ws->ev[1], ws->ev[2]);
+      }
+    }
+    const int64_t nf = h->nf;
+    if (nf <= 0) break;
+    if (L > G3_MAX_LEVELS_GUARD) {
+      g3_set_error("g3_bfs: level guard exceeded");
+      return G3_ETIMEOUT;
+    }
+    const int dir = h->dir;
+    if (stats && nrec < max_stats) {
+      g3_level_stats& r = stats[nrec];
+      memset(&r, 0, sizeof(r));
+      r.level = L;
+      r.dir = dir;
+      r.n_f = h->nf;
+      r.m_f = h->mf;
+      r.n_u = h->nu;
+      r.m_u = h->mu;
+      r.examined = h->mf;
+      r.id_min = h->id_min;
+      r.id_max = h->id_max;
+      for (int k = 0; k < 4; ++k) r.hist[k] = h->hist[k];
+      r.t1 = h->t1;
+      r.t2 = h->t2;
+      r.t3 = h->t3;
+      for (int k = 0; k < 4; ++k) r.mlp_out[k] = h->mlp_out[k];
+    }
+    ++nrec;
+    if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[0], s));
+    bfs_reset_next<<<1, 1, 0, s>>>(ws->ctrl);
+    G3_CHECK_LAUNCH();
+    if (dir == G3_DIR_TD) {
+      G3_TRY(run_td(S, nf, L + 1));
+    } else {
+      G3_TRY(run_bu(S, nf, L + 1));
+    }
+    if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[2], s));
+    bfs_control<<<1, 32, 0, s>>>(ws->ctrl, nb, nnz, o->controller, o->alpha, o->beta,
+                                 o->mlp_params, o->t1, o->t2, o->t3, dir == G3_DIR_TD);
+    G3_CHECK_LAUNCH();
+    if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[3], s));
+    if (dir == G3_DIR_TD) {
+      int32_t* t = S.qcur;
+      S.qcur = S.qnext;
+      S.qnext = t;
+      S.fmt_queue = true;
+    } else {
+      uint32_t* t = S.fcur;
+      S.fcur = S.fnext;
+      S.fnext = t;
+      S.fmt_queue = false;
+    }
+  }
+  if (n_levels) *n_levels = nrec;
+
+  // outputs in original IDs
+  const bool dev_p = is_device_ptr(parent), dev_l = is_device_ptr(level);
+  int32_t* op = dev_p ? parent : ws->out_parent;
+  int32_t* ol = dev_l ? level : ws->out_level;
+  bfs_translate<<<g3_grid_for(g->n, 256), 256, 0, s>>>(
+      g->n, nb, root, g->relabelled ? g->new_of_old : nullptr,
+      g->relabelled ? g->old_of_new : nullptr, ws->parent, ws->level, op, ol);
+  G3_CHECK_LAUNCH();
+  if (!dev_p)
+    G3_TRY_CUDA(cudaMemcpyAsync(parent, op, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+  if (!dev_l)
+    G3_TRY_CUDA(cudaMemcpyAsync(level, ol, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
+  G3_TRY_CUDA(cudaStreamSynchronize(s));
+  return G3_OK;
+}
+
+extern "C" g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, int32_t* parent,
+                            int32_t* level, g3_level_stats* stats, int32_t max_stats,
+                            int32_t* n_levels, void* stream) {
+  if (!g || !parent || !level) {
+    g3_set_error("g3_bfs: null graph or output");
+    return G3_EINVAL;
+  }
+  if (root < 0 || root >= g->n) {
+    g3_set_error("g3_bfs: root %d outside [0, %d)", root, g->n);
+    return G3_EINVAL;
+  }
+  g3_bfs_opts o;
+  if (opts) o = *opts; else g3_bfs_opts_default(&o);
+  if (o.controller < 0 || o.controller > 3 || o.alpha <= 0 || o.beta <= 0 || o.t1 < 1 ||
+      o.t2 <= o.t1 || o.t3 <= o.t2) {
+    g3_set_error("g3_bfs: bad options");
+    return G3_EINVAL;
+  }
+  if (o.controller == G3_CTRL_LEARNED && !o.mlp_params) {
+    g3_set_error("g3_bfs: learned controller needs mlp_params");
+    return G3_EINVAL;
+  }
+  if (max_stats < 0) max_stats = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  g3_status st = bfs_impl(g, root, &o, parent, level, stats, max_stats, n_levels, s);
+  if (st != G3_OK) cudaStreamSynchronize(s);
+  return st;
+}

@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs. CSR and RCM permutation bit-exact, level[] bit-exact,
+parent[] valid under the BFS-tree rules, per-level statistics and the
+direction sequence equal to the oracle's."""
+import numpy as np
+import pytest
+from conftest import read_golden_cases
+
+import graphgen
+import oracle
+from oracle import direction
+from _graphs import band_graph, path_graph, random_graph, star_graph
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2012_10026_gb300 as g3  # noqa: E402
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def gpu_pipeline(src, dst, n, relabel=True):
+    g = g3.g3_build_csr(_dev(src), _dev(dst), n)
+    if relabel:
+        g3.g3_rcm_relabel(g)
+    return g
+
+
+def gpu_csr(g):
+    off, col = g.csr()
+    return off.cpu().numpy(), col.cpu().numpy()
+
+
+def run_bfs(g, root, n, max_stats=0, **kw):
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = g3.g3_bfs(g, root, parent, level, g3.opts(**kw) if kw else None, max_stats=max_stats)
+    return parent.cpu().numpy(), level.cpu().numpy(), st
+
+
+def small_cases():
+    cases = []
+    for c in read_golden_cases("rcm_bfs_cases.txt"):
+        cases.append((c["name"], np.array(c["src"], np.int32), np.array(c["dst"], np.int32),
+                      c["n"]))
+    rng = np.random.default_rng(77)
+    for i in range(12):
+        n = int(rng.integers(1, 300))
+        s, d = random_graph(rng, n, int(rng.integers(0, 4 * n)))
+        cases.append((f"random{i}", s, d, n))
+    cases.append(("path", *path_graph(50), 50))
+    cases.append(("star", *star_graph(40, 7), 40))
+    sigma = np.random.default_rng(5).permutation(120).astype(np.int32)
+    cases.append(("band", *band_graph(120, 4, sigma), 120))
+    cases.append(("empty", np.zeros(0, np.int32), np.zeros(0, np.int32), 9))
+    cases.append(("loops_only", np.array([1, 2], np.int32), np.array([1, 2], np.int32), 4))
+    cases.append(("single_vertex", np.zeros(0, np.int32), np.zeros(0, np.int32), 1))
+    for sc, ef, seed in ((10, 16, 1), (13, 8, 9)):
+        s, d = graphgen.kronecker_edges(sc, ef, seed=seed)
+        cases.append((f"kron{sc}", s, d, 1 << sc))
+    s, d = graphgen.chunglu_edges(3000, seed=3)
+    cases.append(("chunglu3000", s, d, 3000))
+    return cases
+
+
+CASES = small_cases()
+
+
+# ------------------------------------------------------------ generators
+@pytest.mark.parametrize("scale", [10, 14])
+def test_kronecker_device_twin_matches_host(scale):
+    hs, hd = graphgen.kronecker_edges(scale, 16, seed=1)
+    ds, dd = graphgen.kronecker_edges_dev(scale, 16, seed=1)
+    assert np.array_equal(ds.cpu().numpy(), hs) and np.array_equal(dd.cpu().numpy(), hd)
+    f = graphgen.nonisolated_flags_dev(ds, dd, 1 << scale).cpu().numpy()
+    assert np.array_equal(f, graphgen.nonisolated_flags(hs, hd, 1 << scale))
+
+
+def test_chunglu_device_twin_matches_host():
+    hs, hd = graphgen.chunglu_edges(5000, seed=3)
+    ds, dd = graphgen.chunglu_edges_dev(5000, seed=3)
+    assert np.array_equal(ds.cpu().numpy(), hs) and np.array_equal(dd.cpu().numpy(), hd)
+
+
+# ------------------------------------------------------------ CSR and RCM
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_csr_and_rcm_bit_exact(case):
+    name, src, dst, n = case
+    off_o, col_o = oracle.build_csr(src, dst, n)
+    g = gpu_pipeline(src, dst, n, relabel=False)
+    off_g, col_g = gpu_csr(g)
+    assert np.array_equal(off_g, off_o) and np.array_equal(col_g, col_o)
+    info = g.info
+    assert info["nnz"] == len(col_o) and info["max_degree"] == (np.diff(off_o).max() if n else 0)
+    g3.g3_rcm_relabel(g)
+    P, n_plus = oracle.rcm(off_o, col_o)
+    old_of_new, new_of_old = g.perm()
+    assert np.array_equal(old_of_new.cpu().numpy(), P)
+    assert np.array_equal(new_of_old.cpu().numpy(), oracle.permutation_arrays(P)[1])
+    assert g.info["n_plus"] == n_plus and g.info["n_bfs"] == n_plus
+    off_r, col_r = oracle.permute_csr(off_o, col_o, P, n_plus)
+    off_g, col_g = gpu_csr(g)
+    assert np.array_equal(off_g, off_r) and np.array_equal(col_g, col_r)
+    with pytest.raises(g3.G3Error) as e:
+        g3.g3_rcm_relabel(g)
+    assert e.value.status == g3.G3_ESTATE
+    g.free()
+
+
+# ------------------------------------------------------------ BFS
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("relabel", [True, False])
+def test_bfs_small_cases(case, relabel):
+    name, src, dst, n = case
+    off_o, col_o = oracle.build_csr(src, dst, n)
+    g = gpu_pipeline(src, dst, n, relabel)
+    rng = np.random.default_rng(n)
+    roots = sorted(set([0, n - 1] + rng.integers(0, n, 6).tolist()))
+    for ctrl in (g3.G3_CTRL_HEURISTIC, g3.G3_CTRL_TOPDOWN, g3.G3_CTRL_BOTTOMUP):
+        for root in roots:
+            parent, level, _ = run_bfs(g, root, n, controller=ctrl)
+            _, lref = oracle.bfs(off_o, col_o, root)
+            assert np.array_equal(level, lref), (name, root, ctrl)
+            assert oracle.validate(off_o, col_o, root, parent, level) == 0, (name, root, ctrl)
+    g.free()
+
+
+@pytest.fixture(scope="module")
+def kron16():
+    scale, n = 16, 1 << 16
+    src, dst = graphgen.kronecker_edges(scale, 16, seed=1)
+    ref = oracle.pipeline(src, dst, n)
+    roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), 64, seed=2)
+    g = gpu_pipeline(src, dst, n)
+    yield dict(src=src, dst=dst, n=n, ref=ref, roots=roots, g=g)
+    g.free()
+
+
+def _levels_new(ref, level_orig):
+    return level_orig[ref["old_of_new"][:ref["n_plus"]]]
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(controller=g3.G3_CTRL_TOPDOWN),
+                                dict(controller=g3.G3_CTRL_BOTTOMUP), dict(bu_reverse=1),
+                                dict(t1=2, t2=4, t3=8), dict(alpha=64, beta=8)],
+                         ids=["heuristic", "topdown", "bottomup", "reverse", "tiny_bins",
+                              "alpha64_beta8"])
+def test_bfs_kron16_all_roots(kron16, kw):
+    K = kron16
+    ref = K["ref"]
+    for root in K["roots"].tolist():
+        parent, level, st = run_bfs(K["g"], root, K["n"], max_stats=64, **kw)
+        _, lref = oracle.bfs(ref["off"], ref["col"], root)
+        assert np.array_equal(level, lref), root
+        assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0, root
+        # per-level statistics equal the oracle's level sets
+        lnew = _levels_new(ref, lref)
+        ost = direction.level_stats(ref["off_r"], lnew)
+        assert len(st) == len(ost)
+        for L, (a, b) in enumerate(zip(st, ost)):
+            assert (a["n_f"], a["m_f"], a["n_u"], a["m_u"]) == (b["n_f"], b["m_f"], b["n_u"],
+                                                                b["m_u"]), (root, L)
+            f = np.nonzero(lnew == L)[0]
+            assert a["id_min"] == f.min() and a["id_max"] == f.max()
+            if a["dir"] == g3.G3_DIR_BU:
+                assert a["examined"] == oracle.bu_examined(ref["off_r"], ref["col_r"], lnew, L,
+                                                           reverse=bool(kw.get("bu_reverse")))
+        if not kw.get("controller"):
+            expect = direction.heuristic_directions(ref["off_r"], lnew, kw.get("alpha", 14),
+                                                    kw.get("beta", 24))
+            assert [a["dir"] for a in st] == expect, root
+
+
+def test_bfs_host_outputs_equal_device_outputs(kron16):
+    K = kron16
+    root = int(K["roots"][0])
+    pd, ld, _ = run_bfs(K["g"], root, K["n"])
+    ph = np.full(K["n"], 7, np.int32)
+    lh = np.full(K["n"], 7, np.int32)
+    g3.g3_bfs(K["g"], root, ph, lh)
+    assert np.array_equal(lh, ld)
+    assert oracle.validate(K["ref"]["off"], K["ref"]["col"], root, ph, lh) == 0
+    pinned_p = torch.empty(K["n"], dtype=torch.int32).pin_memory()
+    pinned_l = torch.empty(K["n"], dtype=torch.int32).pin_memory()
+    g3.g3_bfs(K["g"], root, pinned_p, pinned_l)
+    assert np.array_equal(pinned_l.numpy(), ld)
+
+
+def test_bfs_isolated_root_and_bad_root(kron16):
+    K = kron16
+    deg = np.diff(K["ref"]["off"])
+    iso = int(np.nonzero(deg == 0)[0][0])
+    parent, level, st = run_bfs(K["g"], iso, K["n"], max_stats=4)
+    assert level[iso] == 0 and parent[iso] == iso
+    assert (level >= 0).sum() == 1 and (parent >= 0).sum() == 1 and st == []
+    with pytest.raises(g3.G3Error) as e:
+        run_bfs(K["g"], K["n"], K["n"])
+    assert e.value.status == g3.G3_EINVAL
+    with pytest.raises(g3.G3Error):
+        run_bfs(K["g"], -1, K["n"])
+
+
+def test_learned_controller_random_params_stays_exact(kron16):
+    from oracle import mlp
+    K = kron16
+    ref = K["ref"]
+    params = torch.from_numpy(mlp.init_params(5).astype(np.float32)).cuda()
+    for root in K["roots"][:8].tolist():
+        parent, level, st = run_bfs(K["g"], root, K["n"], max_stats=64,
+                                    controller=g3.G3_CTRL_LEARNED, mlp_params=params)
+        _, lref = oracle.bfs(ref["off"], ref["col"], root)
+        assert np.array_equal(level, lref)
+        assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
+        for a in st[1:]:
+            f = mlp.features(a["n_f"], a["m_f"], a["n_u"], a["m_u"], a["id_min"], a["id_max"],
+                             ref["n_plus"], a["level"], st[a["level"] - 1]["dir"], a["hist"])
+            o = mlp.forward(mlp.init_params(5), f[None])[0]
+            assert np.allclose(a["mlp_out"], o, rtol=1e-4, atol=1e-4)
+            if abs(o[0]) > 1e-3:
+                assert a["dir"] == (g3.G3_DIR_BU if o[0] < 0 else g3.G3_DIR_TD)
+
+
+def test_bad_edge_endpoint_rejected():
+    with pytest.raises(g3.G3Error) as e:
+        g3.g3_build_csr(_dev([0, 1]), _dev([1, 5]), 5)
+    assert e.value.status == g3.G3_EINVAL
+
+
+def test_kron22_permutation_and_levels():
+    scale, n = 22, 1 << 22
+    src, dst = graphgen.kronecker_edges(scale, 16, seed=1)
+    ref = oracle.pipeline(src, dst, n)
+    g = gpu_pipeline(src, dst, n)
+    old_of_new, _ = g.perm()
+    assert np.array_equal(old_of_new.cpu().numpy(), ref["P"])
+    off_g, col_g = gpu_csr(g)
+    assert np.array_equal(off_g, ref["off_r"]) and np.array_equal(col_g, ref["col_r"])
+    roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), 64, seed=2)
+    for root in roots[:4].tolist():
+        parent, level, _ = run_bfs(g, root, n)
+        _, lref = oracle.bfs(ref["off"], ref["col"], root)
+        assert np.array_equal(level, lref)
+        assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
+    g.free()
