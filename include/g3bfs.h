@@ -194,6 +194,34 @@ g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, int32_t* pa
                  int32_t* level, g3_level_stats* stats, int32_t max_stats,
                  int32_t* n_levels, void* stream);
 
+/* ------------------------------------------------- allocation-free BFS */
+
+/* The paper has no counterpart to this entry point: it serves callers that
+ * cannot allocate device memory when they search -- code running inside a
+ * host framework that has already reserved the device memory for its own
+ * pool, or latency-critical paths where cudaMalloc / cudaFree could
+ * synchronise the device. It performs a top-down BFS (Algorithm 1) over a
+ * caller-provided CSR and allocates nothing: its scratch (visited bitmap, two
+ * frontier queues, counters) is one fixed-size static device array of about
+ * 8.4 MB that every GPU loading the library holds until the process exits.
+ *   off, col      : device pointers, CSR of an undirected graph with n rows
+ *                   (off: n+1 int64, col: off[n] int32 entries, as produced by
+ *                   g3_get_csr), read only.
+ *   n             : 1 <= n <= G3_NOALLOC_MAX_N; larger n is rejected with
+ *                   G3_EINVAL before anything runs.
+ *   root          : in [0, n).
+ *   parent, level : device pointers, n int32 entries each, in the CSR's own
+ *                   vertex IDs (no relabelling); -1 for unreachable vertices.
+ * All calls on a device share the scratch array, which keeps the last call's
+ * contents (each call clears what must start at zero): calls whose GPU work
+ * overlaps race, so serialise them. The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress, that device current); make that
+ * first call before any stream capture. Synchronises `stream` once per level.
+ * Errors: G3_EINVAL, G3_ECUDA. */
+#define G3_NOALLOC_MAX_N (1 << 20)
+g3_status g3_bfs_noalloc(const int64_t* off, const int32_t* col, int32_t n, int32_t root,
+                         int32_t* parent, int32_t* level, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,7 +82,10 @@ _SIGS = {
     "g3_bfs": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(g3_bfs_opts), _vp, _vp,
                               ctypes.POINTER(g3_level_stats), ctypes.c_int32,
                               ctypes.POINTER(ctypes.c_int32), _vp]),
+    "g3_bfs_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
+                                      _vp]),
 }
+NOALLOC_MAX_N = 1 << 20
 
 
 def lib():
@@ -187,6 +190,15 @@ def g3_bfs(graph: "Graph", root: int, parent, level, options: g3_bfs_opts | None
     if stats is None:
         return []
     return [stats[i].to_dict() for i in range(min(nlev.value, max_stats))]
+
+
+def g3_bfs_noalloc(off, col, n: int, root: int, parent, level, stream=None):
+    """Top-down BFS over a caller-provided device CSR that allocates nothing
+    (scratch in a fixed static device array; n <= NOALLOC_MAX_N). For callers
+    that cannot allocate device memory while they search. Calls sharing a
+    device must not overlap on the GPU."""
+    _check(lib().g3_bfs_noalloc(_ptr(off), _ptr(col), int(n), int(root), _ptr(parent),
+                                _ptr(level), _stream(stream)), "g3_bfs_noalloc")
 
 
 def g3_graph_free(graph: "Graph"):
