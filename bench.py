@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--cpu-roots", type=int, default=1, help="roots in the oracle sample")
     ap.add_argument("--cpu-timeout", type=float, default=600.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--bu-reverse", type=int, default=1,
+                    help="bottom-up scans rows from the highest label (degree-aware order)")
     ap.add_argument("--stats-out", default="")
     return ap.parse_args()
 
@@ -224,6 +226,7 @@ def workload_config(args):
             "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
             "initiator": [0.57, 0.19, 0.19, 0.05], "gen_seed": args.seed,
             "root_seed": args.root_seed, "controller": args.controller,
+            "bu_reverse": args.bu_reverse,
             "l2": "256 MB write between roots (L2 flush); CSR larger than L2",
             "parallelism": "replicas"}
 
@@ -262,7 +265,7 @@ def gpu_arm(args, rank, world):
     info = g.info
     ctrl = {"heuristic": g3.G3_CTRL_HEURISTIC, "learned": g3.G3_CTRL_LEARNED,
             "topdown": g3.G3_CTRL_TOPDOWN, "bottomup": g3.G3_CTRL_BOTTOMUP}[args.controller]
-    kw = dict(controller=ctrl, timing=1)
+    kw = dict(controller=ctrl, timing=1, bu_reverse=args.bu_reverse)
     mlp_t = None
     if ctrl == g3.G3_CTRL_LEARNED:
         with open(args.mlp) as f:

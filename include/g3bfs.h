@@ -131,9 +131,10 @@ typedef struct {
                                the frontier shrank and n_f*beta < n_bfs (14, 24) */
   int32_t t1, t2, t3;       /* top-down degree bins: thread < t1 <= warp < t2 <=
                                CTA < t3 <= whole grid (32, 1024, 32768) */
-  int32_t bu_reverse;       /* bottom-up scans each row from its end (highest
-                               label first), the degree-aware order of
-                               Algorithm 6 approximated under RCM */
+  int32_t bu_reverse;       /* 1 (default): bottom-up scans each row from its
+                               end (highest label first), Algorithm 6's
+                               degree-aware order approximated under RCM;
+                               0: CSR order as in Algorithm 5 */
   int32_t timing;           /* record per-level CUDA-event times in stats */
   const float* mlp_params;  /* device pointer, G3_MLP_NPARAMS floats, for
                                G3_CTRL_LEARNED */
@@ -166,7 +167,9 @@ typedef struct {
                          controller kernels (opts.timing) */
   float ms_expand;    /* expansion kernels only: td_front..td_stats for a
                          top-down level, bu_pull for a bottom-up one */
-  float t_td_ms, t_bu_ms; /* record_both: time of each direction */
+  float t_td_ms, t_bu_ms; /* record_both: best top-down time over the
+                             threshold candidates, bottom-up time */
+  int32_t best_t1, best_t2, best_t3; /* record_both: fastest top-down bins */
   float mlp_out[4];   /* learned controller outputs for this level */
 } g3_level_stats;
 

@@ -53,7 +53,8 @@ class g3_level_stats(ctypes.Structure):
                 ("hist", ctypes.c_int64 * 4), ("t1", ctypes.c_int32), ("t2", ctypes.c_int32),
                 ("t3", ctypes.c_int32), ("ms", ctypes.c_float), ("ms_expand", ctypes.c_float),
                 ("t_td_ms", ctypes.c_float), ("t_bu_ms", ctypes.c_float),
-                ("mlp_out", ctypes.c_float * 4)]
+                ("best_t1", ctypes.c_int32), ("best_t2", ctypes.c_int32),
+                ("best_t3", ctypes.c_int32), ("mlp_out", ctypes.c_float * 4)]
 
     def to_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -12,28 +12,31 @@
 //     Algorithm 4's even split of a long neighbour list over all threads.
 //     Neighbour lists are read with aligned 128-bit loads. A neighbour is
 //     claimed by an atomicOr on its word of the visited bitmap; the winner
-//     writes parent/level and appends it to the next queue with one
-//     warp-aggregated atomic per warp.
-//   bottom-up (Algorithm 5): one warp per 32-vertex word of the visited
-//     bitmap; each unvisited vertex scans its row until the first neighbour
-//     whose bit is set in the current-frontier bitmap (early break). The
-//     word's owner writes the next-frontier word and ORs it into visited (no
-//     atomics: the paper's "visited |= F_next" folded into the same pass).
+//     writes (parent, level) and appends it to the next queue through a
+//     per-warp shared-memory buffer (one global atomic per ~224 vertices).
+//   bottom-up (Algorithms 5 and 6): one warp per pair of 32-vertex words of
+//     the visited bitmap; each unvisited vertex scans its row until the first
+//     neighbour whose bit is set in the current-frontier bitmap (early break).
+//     The first probe of both words is issued before any continuation so that
+//     each lane keeps two independent load chains in flight. Rows are scanned
+//     from their end by default: under RCM labels grow with degree, so this is
+//     Algorithm 6's highest-degree-first order. The word's owner writes the
+//     next-frontier word and ORs it into visited (no atomics: the paper's
+//     "visited |= F_next" folded into the same pass).
 //
 // Statistics of the next frontier (size, degree sum, label range, degree
 // histogram, edges examined) are reduced per block and added with one atomic
-// per block.
+// per block. (parent, level) of BFS-graph vertices are kept packed as int2 and
+// are only meaningful where the visited bit is set, so nothing but the
+// visited bitmap is cleared per search.
 #include <math.h>
 #include <string.h>
 
 #include "g3_prims.cuh"
 
-#define G3_MAX_LEVELS_GUARD (1 << 30)
-#define BFS_GRID (G3_NUM_SMS * 8)
-
 // Device-side controller record; mirrored to pinned host memory each level.
 struct Ctrl {
-  // accumulators for the frontier being produced (reset before expansion)
+  // accumulators for the frontier being produced (reset by the controller)
   unsigned long long q_len;     // top-down: next queue length
   unsigned long long nx_nf;     // bottom-up: next frontier size
   unsigned long long nx_mf;     // sum of degrees of the next frontier
@@ -59,64 +62,25 @@ struct g3_bfs_ws {
   int64_t nwords;
   uint32_t *visited, *fa, *fb, *vis_save;
   int32_t *qa, *qb, *bins;  // bins: 3 segments of nb entries (warp, CTA, grid)
-  int32_t *parent, *level;  // BFS-graph labels
+  int2* pl;                 // (parent, level) per BFS-graph vertex
   int32_t *out_parent, *out_level;  // staging for host outputs (n entries)
   Ctrl* ctrl;
   Ctrl* h_ctrl;  // pinned
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[6];
+  // resident-grid sizes (SMs x blocks per SM) per kernel
+  int grid_front, grid_warp, grid_cta, grid_grid, grid_stats, grid_bu, grid_conv, grid_tr;
 };
 
 void g3_bfs_ws_free(g3_bfs_ws* ws) {
   if (!ws) return;
-  void* all[] = {ws->visited, ws->fa, ws->fb, ws->vis_save, ws->qa, ws->qb, ws->bins,
-                 ws->parent, ws->level, ws->out_parent, ws->out_level, ws->ctrl};
+  void* all[] = {ws->visited, ws->fa,  ws->fb,         ws->vis_save,  ws->qa,  ws->qb,
+                 ws->bins,    ws->pl,  ws->out_parent, ws->out_level, ws->ctrl};
   for (void* p : all)
     if (p) cudaFree(p);
   if (ws->h_ctrl) cudaFreeHost(ws->h_ctrl);
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 6; ++i)
     if (ws->ev[i]) cudaEventDestroy(ws->ev[i]);
   free(ws);
-}
-
-static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
-  g3_bfs_ws* ws = (g3_bfs_ws*)calloc(1, sizeof(g3_bfs_ws));
-  if (!ws) return G3_ENOMEM;
-  ws->nb = g->n_bfs;
-  ws->nwords = ((int64_t)g->n_bfs + 31) / 32;
-  const size_t nb1 = (size_t)g->n_bfs + 4, nw = (size_t)ws->nwords + 4, n1 = (size_t)g->n + 4;
-  struct {
-    void** p;
-    size_t bytes;
-  } req[] = {
-      {(void**)&ws->visited, nw * 4},     {(void**)&ws->fa, nw * 4},
-      {(void**)&ws->fb, nw * 4},          {(void**)&ws->vis_save, nw * 4},
-      {(void**)&ws->qa, nb1 * 4},         {(void**)&ws->qb, nb1 * 4},
-      {(void**)&ws->bins, nb1 * 4 * 3},   {(void**)&ws->parent, nb1 * 4},
-      {(void**)&ws->level, nb1 * 4},      {(void**)&ws->out_parent, n1 * 4},
-      {(void**)&ws->out_level, n1 * 4},   {(void**)&ws->ctrl, sizeof(Ctrl)},
-  };
-  for (auto& r : req) {
-    cudaError_t e = cudaMalloc(r.p, r.bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      g3_set_error("g3_bfs workspace: cudaMalloc(%zu): %s", r.bytes, cudaGetErrorString(e));
-      g3_bfs_ws_free(ws);
-      return G3_ENOMEM;
-    }
-  }
-  if (cudaMallocHost((void**)&ws->h_ctrl, sizeof(Ctrl)) != cudaSuccess) {
-    cudaGetLastError();
-    g3_bfs_ws_free(ws);
-    return G3_ENOMEM;
-  }
-  for (int i = 0; i < 4; ++i)
-    if (cudaEventCreate(&ws->ev[i]) != cudaSuccess) {
-      cudaGetLastError();
-      g3_bfs_ws_free(ws);
-      return G3_ECUDA;
-    }
-  *out = ws;
-  return G3_OK;
 }
 
 // ----------------------------------------------------------- device helpers
@@ -124,28 +88,31 @@ __device__ __forceinline__ int deg_bucket(int64_t d) {
   return d < 32 ? 0 : (d < 1024 ? 1 : (d < 32768 ? 2 : 3));
 }
 
+// Per-thread statistics in 32-bit registers (a thread sees far fewer than
+// 2^32 vertices or edges per launch); reduced per block in 64 bits.
 struct StatAcc {
-  unsigned long long nf, mf, ex, h[4];
-  unsigned int mn, mx;
+  unsigned nf, mf, ex, h0, h1, h2, h3, mn, mx;
   __device__ void init() {
-    nf = mf = ex = 0;
-    h[0] = h[1] = h[2] = h[3] = 0;
+    nf = mf = ex = h0 = h1 = h2 = h3 = 0;
     mn = 0xFFFFFFFFu;
     mx = 0;
   }
   __device__ void add_vertex(int32_t v, int64_t d) {
     nf++;
-    mf += (unsigned long long)d;
-    h[deg_bucket(d)]++;
+    mf += (unsigned)d;
+    int b = deg_bucket(d);
+    h0 += b == 0;
+    h1 += b == 1;
+    h2 += b == 2;
+    h3 += b == 3;
     mn = min(mn, (unsigned)v);
     mx = max(mx, (unsigned)v);
   }
-  // block reduction then one atomic per block and field
-  __device__ void flush(Ctrl* c, bool with_nf) {
-    __shared__ unsigned long long s[8][8];
+  __device__ void flush(Ctrl* c) {
+    __shared__ unsigned long long s[8][7];
     __shared__ unsigned int smn[8], smx[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned long long v[7] = {nf, mf, ex, h[0], h[1], h[2], h[3]};
+    unsigned long long v[7] = {nf, mf, ex, h0, h1, h2, h3};
     unsigned a = mn, b = mx;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -168,7 +135,7 @@ struct StatAcc {
         tmn = min(tmn, smn[w]);
         tmx = max(tmx, smx[w]);
       }
-      if (with_nf && t[0]) atomicAdd(&c->nx_nf, t[0]);
+      if (t[0]) atomicAdd(&c->nx_nf, t[0]);
       if (t[1]) atomicAdd(&c->nx_mf, t[1]);
       if (t[2]) atomicAdd(&c->nx_exam, t[2]);
       for (int k = 0; k < 4; ++k)
@@ -188,54 +155,7 @@ __device__ __forceinline__ bool td_claim(uint32_t* visited, int32_t w) {
   return !(atomicOr(word, bit) & bit);
 }
 
-// ------------------------------------------------------------------- init
-__global__ void bfs_init(int32_t nb, int64_t nwords, uint32_t* visited, int32_t* parent,
-                         int32_t* level) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    parent[i] = -1;
-    level[i] = -1;
-    if (i < nwords) visited[i] = 0u;
-  }
-  for (int64_t i = nb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
-       i += (int64_t)gridDim.x * blockDim.x)
-    visited[i] = 0u;
-}
-
-// Sets up F_0 = {root} (root_new < 0 or >= nb: no BFS-graph vertex).
-__global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, int64_t nnz,
-                         const int64_t* off, uint32_t* visited, int32_t* parent,
-                         int32_t* level, int32_t* q, Ctrl* c, int t1, int t2, int t3) {
-  int32_t r = new_of_old ? new_of_old[root] : root;
-  memset(c, 0, sizeof(Ctrl));
-  c->t1 = t1;
-  c->t2 = t2;
-  c->t3 = t3;
-  c->dir = G3_DIR_TD;  // Algorithm 2 starts top-down
-  c->nx_min = 0xFFFFFFFFu;
-  if (r < 0 || r >= nb) {
-    c->nf = 0;
-    c->nu = nb;
-    c->mu = nnz;
-    return;
-  }
-  visited[r >> 5] |= 1u << (r & 31);
-  parent[r] = r;
-  level[r] = 0;
-  q[0] = r;
-  long long d = off[r + 1] - off[r];
-  c->nf = 1;
-  c->mf = d;
-  c->hist[deg_bucket(d)] = 1;
-  c->id_min = c->id_max = r;
-  c->n_visited = 1;
-  c->m_visited = d;
-  c->nu = nb - 1;
-  c->mu = nnz - d;
-  c->prev_nf = 0;
-}
-
-__global__ void bfs_reset_next(Ctrl* c) {
+__device__ __forceinline__ void reset_next(Ctrl* c) {
   c->q_len = 0;
   c->nx_nf = 0;
   c->nx_mf = 0;
@@ -249,49 +169,119 @@ __global__ void bfs_reset_next(Ctrl* c) {
   c->conv_len = 0;
 }
 
+// ------------------------------------------------------------------- init
+// Sets up F_0 = {root} (root_new < 0 or >= nb: no BFS-graph vertex). The
+// visited bitmap has been cleared on the stream before.
+__global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, int64_t nnz,
+                         const int64_t* off, uint32_t* visited, int2* pl, int32_t* q, Ctrl* c,
+                         int t1, int t2, int t3) {
+  int32_t r = new_of_old ? new_of_old[root] : root;
+  memset(c, 0, sizeof(Ctrl));
+  reset_next(c);
+  c->t1 = t1;
+  c->t2 = t2;
+  c->t3 = t3;
+  c->dir = G3_DIR_TD;  // Algorithm 2 starts top-down
+  if (r < 0 || r >= nb) {
+    c->nf = 0;
+    c->nu = nb;
+    c->mu = nnz;
+    return;
+  }
+  visited[r >> 5] |= 1u << (r & 31);
+  pl[r] = make_int2(r, 0);
+  q[0] = r;
+  long long d = off[r + 1] - off[r];
+  c->nf = 1;
+  c->mf = d;
+  c->hist[deg_bucket(d)] = 1;
+  c->id_min = c->id_max = r;
+  c->n_visited = 1;
+  c->m_visited = d;
+  c->nu = nb - 1;
+  c->mu = nnz - d;
+  c->prev_nf = 0;
+}
+
 // --------------------------------------------------------------- top-down
 struct TdArgs {
   const int64_t* off;
   const int32_t* col;
   uint32_t* visited;
-  int32_t* parent;
-  int32_t* level;
+  int2* pl;
   int32_t lnext;
   int32_t* qnext;
   Ctrl* c;
 };
 
-// Claims w for v; appends claimed vertices with one atomic per warp. All 32
-// lanes must call it together.
-__device__ __forceinline__ void td_visit(const TdArgs& a, bool has, int32_t w, int32_t v) {
+// Per-warp staging of the next queue in shared memory: claimed vertices are
+// compacted into the warp's buffer with a ballot and written to the global
+// queue in one coalesced burst, reserving space with one atomic per ~224
+// vertices instead of one per warp step (the queue counter is a single
+// address that every warp of the grid would otherwise hit).
+#define WQ_CAP 256
+#define WQ_FLUSH (WQ_CAP - 32)
+struct WarpQueue {
+  int32_t* buf;  // this warp's WQ_CAP-entry shared buffer
+  int cnt;       // warp-uniform fill level
+};
+
+__device__ __forceinline__ void wq_flush(WarpQueue& q, int32_t* gq, unsigned long long* glen) {
+  if (q.cnt == 0) return;
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(glen, (unsigned long long)q.cnt);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  __syncwarp();
+  for (int i = lane; i < q.cnt; i += 32) gq[base + i] = q.buf[i];
+  __syncwarp();
+  q.cnt = 0;
+}
+
+// All 32 lanes call it together.
+__device__ __forceinline__ void wq_push(WarpQueue& q, bool want, int32_t item, int32_t* gq,
+                                        unsigned long long* glen) {
+  const unsigned bal = __ballot_sync(0xffffffffu, want);
+  if (bal == 0) return;
+  if (want) q.buf[q.cnt + __popc(bal & g3_lanemask_lt())] = item;
+  q.cnt += __popc(bal);
+  __syncwarp();
+  if (q.cnt > WQ_FLUSH) wq_flush(q, gq, glen);
+}
+
+#define WQ_DECLARE(q)                                      \
+  __shared__ int32_t wq_mem[8][WQ_CAP];                    \
+  WarpQueue q{wq_mem[threadIdx.x >> 5], 0}
+
+// Claims w for v. All 32 lanes must call it together.
+__device__ __forceinline__ void td_visit(const TdArgs& a, WarpQueue& q, bool has, int32_t w,
+                                         int32_t v) {
   bool claim = has && td_claim(a.visited, w);
-  if (claim) {
-    a.parent[w] = v;
-    a.level[w] = a.lnext;
-  }
-  g3_warp_append(0xffffffffu, claim, w, a.qnext, &a.c->q_len);
+  if (claim) a.pl[w] = make_int2(v, a.lnext);
+  wq_push(q, claim, w, a.qnext, &a.c->q_len);
 }
 
 // Processes row entries [b, e) of vertex v with `nthr` cooperating threads
 // (index t), four entries per thread per step through aligned 128-bit loads.
 // Every lane of each participating warp runs the same number of steps.
-__device__ __forceinline__ void td_row_vec4(const TdArgs& a, int32_t v, int64_t b, int64_t e,
-                                            int64_t t, int64_t nthr, int64_t steps) {
+__device__ __forceinline__ void td_row_vec4(const TdArgs& a, WarpQueue& q, int32_t v, int64_t b,
+                                            int64_t e, int64_t t, int64_t nthr, int64_t steps) {
   const int64_t a0 = b & ~3ll;
   for (int64_t s = 0; s < steps; ++s) {
     const int64_t j = a0 + 4 * (t + s * nthr);
     int4 x = make_int4(0, 0, 0, 0);
     if (j < e) x = *reinterpret_cast<const int4*>(a.col + j);
-    td_visit(a, j + 0 >= b && j + 0 < e, x.x, v);
-    td_visit(a, j + 1 >= b && j + 1 < e, x.y, v);
-    td_visit(a, j + 2 >= b && j + 2 < e, x.z, v);
-    td_visit(a, j + 3 >= b && j + 3 < e, x.w, v);
+    td_visit(a, q, j + 0 >= b && j + 0 < e, x.x, v);
+    td_visit(a, q, j + 1 >= b && j + 1 < e, x.y, v);
+    td_visit(a, q, j + 2 >= b && j + 2 < e, x.z, v);
+    td_visit(a, q, j + 3 >= b && j + 3 < e, x.w, v);
   }
 }
 
 __global__ void __launch_bounds__(256) td_front(TdArgs a, const int32_t* __restrict__ q,
                                                 int64_t qlen, int32_t* bins, int64_t nb1) {
   const int t1 = a.c->t1, t2 = a.c->t2, t3 = a.c->t3;
+  WQ_DECLARE(wq);
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < qlen;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
@@ -307,43 +297,50 @@ __global__ void __launch_bounds__(256) td_front(TdArgs a, const int32_t* __restr
     for (int k = 0; k < maxc; ++k) {
       bool has = k < cnt;
       int32_t w = has ? a.col[b + k] : 0;
-      td_visit(a, has, w, v);
+      td_visit(a, wq, has, w, v);
     }
   }
+  wq_flush(wq, a.qnext, &a.c->q_len);
 }
 
 __global__ void __launch_bounds__(256) td_warp(TdArgs a, const int32_t* __restrict__ bin) {
   const int64_t len = (int64_t)a.c->bin_len[1];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  WQ_DECLARE(wq);
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < len; i += nwarps) {
     int32_t v = bin[i];
     int64_t b = a.off[v], e = a.off[v + 1];
     int64_t steps = (e - (b & ~3ll) + 127) / 128;
-    td_row_vec4(a, v, b, e, lane, 32, steps);
+    td_row_vec4(a, wq, v, b, e, lane, 32, steps);
   }
+  wq_flush(wq, a.qnext, &a.c->q_len);
 }
 
 __global__ void __launch_bounds__(256) td_cta(TdArgs a, const int32_t* __restrict__ bin) {
   const int64_t len = (int64_t)a.c->bin_len[2];
+  WQ_DECLARE(wq);
   for (int64_t i = blockIdx.x; i < len; i += gridDim.x) {
     int32_t v = bin[i];
     int64_t b = a.off[v], e = a.off[v + 1];
     int64_t steps = (e - (b & ~3ll) + 4 * blockDim.x - 1) / (4 * blockDim.x);
-    td_row_vec4(a, v, b, e, threadIdx.x, blockDim.x, steps);
+    td_row_vec4(a, wq, v, b, e, threadIdx.x, blockDim.x, steps);
   }
+  wq_flush(wq, a.qnext, &a.c->q_len);
 }
 
 __global__ void __launch_bounds__(256) td_grid(TdArgs a, const int32_t* __restrict__ bin) {
   const int64_t len = (int64_t)a.c->bin_len[3];
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  WQ_DECLARE(wq);
   for (int64_t i = 0; i < len; ++i) {
     int32_t v = bin[i];
     int64_t b = a.off[v], e = a.off[v + 1];
     int64_t steps = (e - (b & ~3ll) + 4 * nthr - 1) / (4 * nthr);
-    td_row_vec4(a, v, b, e, t, nthr, steps);
+    td_row_vec4(a, wq, v, b, e, t, nthr, steps);
   }
+  wq_flush(wq, a.qnext, &a.c->q_len);
 }
 
 // Statistics of the queue F_{L+1} produced by a top-down level.
@@ -357,60 +354,94 @@ __global__ void __launch_bounds__(256) td_stats(const int32_t* __restrict__ q,
     int32_t v = q[i];
     acc.add_vertex(v, off[v + 1] - off[v]);
   }
-  acc.flush(c, true);
+  acc.flush(c);
 }
 
 // -------------------------------------------------------------- bottom-up
+__device__ __forceinline__ bool in_frontier(const uint32_t* __restrict__ f, int32_t w) {
+  return (__ldg(&f[w >> 5]) >> (w & 31)) & 1u;
+}
+
+// Scans the rest of a row after a missed first probe; returns the parent or
+// -1 and advances k (edges examined).
+template <int REV>
+__device__ __forceinline__ int32_t bu_scan_rest(const int32_t* __restrict__ col,
+                                                const uint32_t* __restrict__ fcur, int64_t b,
+                                                int64_t e, int64_t& k) {
+  const int64_t d = e - b;
+  while (k < d) {
+    const int32_t w = col[REV ? e - 1 - k : b + k];
+    ++k;
+    if (in_frontier(fcur, w)) return w;
+  }
+  return -1;
+}
+
+template <int REV>
 __global__ void __launch_bounds__(256) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
                                                const uint32_t* __restrict__ fcur,
                                                uint32_t* __restrict__ fnext,
                                                const int64_t* __restrict__ off,
-                                               const int32_t* __restrict__ col,
-                                               int32_t* parent, int32_t* level, int32_t lnext,
-                                               int reverse, Ctrl* c) {
+                                               const int32_t* __restrict__ col, int2* pl,
+                                               int32_t lnext, Ctrl* c) {
   StatAcc acc;
   acc.init();
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t word = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; word < nwords;
-       word += nwarps) {
-    const uint32_t vis = visited[word];
-    const int64_t v = word * 32 + lane;
-    const bool cand = v < nb && !((vis >> lane) & 1u);
-    if (!__any_sync(0xffffffffu, cand)) {
-      if (lane == 0) fnext[word] = 0u;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t w0 = 2 * wid; w0 < nwords; w0 += 2 * nwarps) {
+    const bool has1 = w0 + 1 < nwords;
+    const uint32_t vis0 = visited[w0];
+    const uint32_t vis1 = has1 ? visited[w0 + 1] : 0xFFFFFFFFu;
+    const int64_t v0 = w0 * 32 + lane, v1 = v0 + 32;
+    const bool c0 = v0 < nb && !((vis0 >> lane) & 1u);
+    const bool c1 = v1 < nb && !((vis1 >> lane) & 1u);
+    if (!__any_sync(0xffffffffu, c0 || c1)) {
+      if (lane == 0) {
+        fnext[w0] = 0u;
+        if (has1) fnext[w0 + 1] = 0u;
+      }
       continue;
     }
-    bool found = false;
-    int64_t d = 0;
-    if (cand) {
-      const int64_t b = off[v], e = off[v + 1];
-      d = e - b;
-      int64_t k = 0;
-      int32_t par = -1;
-      for (; k < d; ++k) {
-        const int32_t w = col[reverse ? e - 1 - k : b + k];
-        if ((__ldg(&fcur[w >> 5]) >> (w & 31)) & 1u) {
-          par = w;
-          ++k;
-          break;
-        }
-      }
-      acc.ex += (unsigned long long)k;
-      if (par >= 0) {
-        found = true;
-        parent[v] = par;
-        level[v] = lnext;
-      }
+    int64_t b0 = 0, e0 = 0, b1 = 0, e1 = 0;
+    if (c0) {
+      b0 = off[v0];
+      e0 = off[v0 + 1];
     }
-    const uint32_t nbits = __ballot_sync(0xffffffffu, found);
+    if (c1) {
+      b1 = off[v1];
+      e1 = off[v1 + 1];
+    }
+    // first probes of both vertices, independent of each other
+    int32_t x0 = -1, x1 = -1;
+    if (e0 > b0) x0 = col[REV ? e0 - 1 : b0];
+    if (e1 > b1) x1 = col[REV ? e1 - 1 : b1];
+    int32_t p0 = (x0 >= 0 && in_frontier(fcur, x0)) ? x0 : -1;
+    int32_t p1 = (x1 >= 0 && in_frontier(fcur, x1)) ? x1 : -1;
+    int64_t k0 = e0 > b0 ? 1 : 0, k1 = e1 > b1 ? 1 : 0;
+    if (p0 < 0) p0 = bu_scan_rest<REV>(col, fcur, b0, e0, k0);
+    if (p1 < 0) p1 = bu_scan_rest<REV>(col, fcur, b1, e1, k1);
+    acc.ex += (unsigned)(k0 + k1);
+    const uint32_t n0 = __ballot_sync(0xffffffffu, p0 >= 0);
+    const uint32_t n1 = __ballot_sync(0xffffffffu, p1 >= 0);
+    if (p0 >= 0) {
+      pl[v0] = make_int2(p0, lnext);
+      acc.add_vertex((int32_t)v0, e0 - b0);
+    }
+    if (p1 >= 0) {
+      pl[v1] = make_int2(p1, lnext);
+      acc.add_vertex((int32_t)v1, e1 - b1);
+    }
     if (lane == 0) {
-      fnext[word] = nbits;
-      if (nbits) visited[word] = vis | nbits;
+      fnext[w0] = n0;
+      if (n0) visited[w0] = vis0 | n0;
+      if (has1) {
+        fnext[w0 + 1] = n1;
+        if (n1) visited[w0 + 1] = vis1 | n1;
+      }
     }
-    if (found) acc.add_vertex((int32_t)v, d);
   }
-  acc.flush(c, true);
+  acc.flush(c);
 }
 
 // ------------------------------------------------------------ conversions
@@ -492,7 +523,8 @@ __device__ __forceinline__ int clamp_thr(float lg, int lo, int hi) {
 }
 
 // After the expansion of level L: promote the produced frontier to F_{L+1},
-// update the visited totals and decide its direction.
+// update the visited totals, decide its direction and clear the accumulators
+// for the next expansion.
 __global__ void bfs_control(Ctrl* c, int32_t nb, int64_t nnz, int controller, int alpha,
                             int beta, const float* __restrict__ mlp, int t1d, int t2d, int t3d,
                             int was_td) {
@@ -530,6 +562,7 @@ __global__ void bfs_control(Ctrl* c, int32_t nb, int64_t nnz, int controller, in
     c->t3 = t3d;
     decide = d;
     if (controller == G3_CTRL_LEARNED) mlp_features(c, nb, prev_dir, feat);
+    reset_next(c);
   }
   __syncwarp();
   if (controller == G3_CTRL_LEARNED) {
@@ -555,19 +588,16 @@ __global__ void bfs_control(Ctrl* c, int32_t nb, int64_t nnz, int controller, in
 __global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
                               const int32_t* __restrict__ new_of_old,
                               const int32_t* __restrict__ old_of_new,
-                              const int32_t* __restrict__ parent_new,
-                              const int32_t* __restrict__ level_new, int32_t* parent,
-                              int32_t* level) {
+                              const uint32_t* __restrict__ visited,
+                              const int2* __restrict__ pl, int32_t* parent, int32_t* level) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     int32_t p = -1, l = -1;
-    int32_t x = new_of_old ? new_of_old[v] : (int32_t)v;
-    if (x < nb) {
-      l = level_new[x];
-      if (l >= 0) {
-        int32_t pn = parent_new[x];
-        p = old_of_new ? old_of_new[pn] : pn;
-      }
+    const int32_t x = new_of_old ? new_of_old[v] : (int32_t)v;
+    if (x < nb && ((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u)) {
+      const int2 t = pl[x];
+      p = old_of_new ? old_of_new[t.x] : t.x;
+      l = t.y;
     }
     if (v == root) {
       p = root;
@@ -588,6 +618,70 @@ extern "C" void g3_bfs_opts_default(g3_bfs_opts* o) {
   o->t1 = 32;
   o->t2 = 1024;
   o->t3 = 32768;
+  o->bu_reverse = 1;
+}
+
+template <class K>
+static int resident_grid(K kernel, int block) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, 0);
+  cudaGetLastError();
+  if (sms < 1) sms = G3_NUM_SMS;
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
+  g3_bfs_ws* ws = (g3_bfs_ws*)calloc(1, sizeof(g3_bfs_ws));
+  if (!ws) return G3_ENOMEM;
+  ws->nb = g->n_bfs;
+  ws->nwords = ((int64_t)g->n_bfs + 31) / 32;
+  const size_t nb1 = (size_t)g->n_bfs + 4, nw = (size_t)ws->nwords + 4, n1 = (size_t)g->n + 4;
+  struct {
+    void** p;
+    size_t bytes;
+  } req[] = {
+      {(void**)&ws->visited, nw * 4},     {(void**)&ws->fa, nw * 4},
+      {(void**)&ws->fb, nw * 4},          {(void**)&ws->vis_save, nw * 4},
+      {(void**)&ws->qa, nb1 * 4},         {(void**)&ws->qb, nb1 * 4},
+      {(void**)&ws->bins, nb1 * 4 * 3},   {(void**)&ws->pl, nb1 * 8},
+      {(void**)&ws->out_parent, n1 * 4},  {(void**)&ws->out_level, n1 * 4},
+      {(void**)&ws->ctrl, sizeof(Ctrl)},
+  };
+  for (auto& r : req) {
+    cudaError_t e = cudaMalloc(r.p, r.bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g3_set_error("g3_bfs workspace: cudaMalloc(%zu): %s", r.bytes, cudaGetErrorString(e));
+      g3_bfs_ws_free(ws);
+      return G3_ENOMEM;
+    }
+  }
+  if (cudaMallocHost((void**)&ws->h_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+    cudaGetLastError();
+    g3_bfs_ws_free(ws);
+    return G3_ENOMEM;
+  }
+  for (int i = 0; i < 6; ++i)
+    if (cudaEventCreate(&ws->ev[i]) != cudaSuccess) {
+      cudaGetLastError();
+      g3_bfs_ws_free(ws);
+      return G3_ECUDA;
+    }
+  ws->grid_front = resident_grid(td_front, 256);
+  ws->grid_warp = resident_grid(td_warp, 256);
+  ws->grid_cta = resident_grid(td_cta, 256);
+  ws->grid_grid = resident_grid(td_grid, 256);
+  ws->grid_stats = resident_grid(td_stats, 256);
+  ws->grid_bu = resident_grid(bu_pull<1>, 256);
+  int g0 = resident_grid(bu_pull<0>, 256);
+  if (g0 < ws->grid_bu) ws->grid_bu = g0;
+  ws->grid_conv = resident_grid(bitmap_to_q, 256);
+  ws->grid_tr = resident_grid(bfs_translate, 256);
+  *out = ws;
+  return G3_OK;
 }
 
 static bool is_device_ptr(const void* p) {
@@ -597,6 +691,12 @@ static bool is_device_ptr(const void* p) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static inline int cap_grid(int64_t items, int per_block, int resident) {
+  int64_t b = (items + per_block - 1) / per_block;
+  if (b > resident) b = resident;
+  return b < 1 ? 1 : (int)b;
 }
 
 struct Level {
@@ -609,33 +709,34 @@ struct Level {
   bool fmt_queue;
 };
 
-// Top-down expansion of F_L (queue qcur of length nf) into qnext.
-static g3_status run_td(Level& S, int64_t nf, int32_t lnext) {
+// Top-down expansion of F_L (queue qcur of length nf) into qnext. Records
+// event `ev_mid` after the format conversion when given.
+static g3_status run_td(Level& S, int64_t nf, int32_t lnext, cudaEvent_t ev_mid) {
   g3_bfs_ws* ws = S.ws;
   cudaStream_t s = S.s;
   if (!S.fmt_queue) {
-    bitmap_to_q<<<g3_grid_for(ws->nwords, 256, BFS_GRID), 256, 0, s>>>(
+    bitmap_to_q<<<cap_grid(ws->nwords, 256, ws->grid_conv), 256, 0, s>>>(
         S.fcur, ws->nwords, S.qcur, &ws->ctrl->conv_len);
     G3_CHECK_LAUNCH();
   }
-  if (S.o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[1], s));
-  TdArgs a{S.g->off, S.g->col, ws->visited, ws->parent, ws->level, lnext, S.qnext, ws->ctrl};
+  if (ev_mid) G3_TRY_CUDA(cudaEventRecord(ev_mid, s));
+  TdArgs a{S.g->off, S.g->col, ws->visited, ws->pl, lnext, S.qnext, ws->ctrl};
   const int64_t nb1 = ws->nb + 4;
-  td_front<<<g3_grid_for(nf, 256, BFS_GRID * 2), 256, 0, s>>>(a, S.qcur, nf, ws->bins, nb1);
+  td_front<<<cap_grid(nf, 256, ws->grid_front), 256, 0, s>>>(a, S.qcur, nf, ws->bins, nb1);
   G3_CHECK_LAUNCH();
-  td_warp<<<g3_grid_for(nf, 8, BFS_GRID), 256, 0, s>>>(a, ws->bins);
+  td_warp<<<cap_grid(nf, 8, ws->grid_warp), 256, 0, s>>>(a, ws->bins);
   G3_CHECK_LAUNCH();
-  td_cta<<<g3_grid_for(nf, 1, BFS_GRID), 256, 0, s>>>(a, ws->bins + nb1);
+  td_cta<<<cap_grid(nf, 1, ws->grid_cta), 256, 0, s>>>(a, ws->bins + nb1);
   G3_CHECK_LAUNCH();
-  td_grid<<<G3_NUM_SMS * 4, 256, 0, s>>>(a, ws->bins + 2 * nb1);
+  td_grid<<<ws->grid_grid, 256, 0, s>>>(a, ws->bins + 2 * nb1);
   G3_CHECK_LAUNCH();
-  td_stats<<<g3_grid_for(ws->nb, 256, BFS_GRID), 256, 0, s>>>(S.qnext, S.g->off, ws->ctrl);
+  td_stats<<<cap_grid(ws->nb, 256, ws->grid_stats), 256, 0, s>>>(S.qnext, S.g->off, ws->ctrl);
   G3_CHECK_LAUNCH();
   return G3_OK;
 }
 
 // Bottom-up expansion of F_L (bitmap) into fnext.
-static g3_status run_bu(Level& S, int64_t nf, int32_t lnext) {
+static g3_status run_bu(Level& S, int64_t nf, int32_t lnext, cudaEvent_t ev_mid) {
   g3_bfs_ws* ws = S.ws;
   cudaStream_t s = S.s;
   if (S.fmt_queue) {
@@ -643,11 +744,65 @@ static g3_status run_bu(Level& S, int64_t nf, int32_t lnext) {
     q_to_bitmap<<<g3_grid_for(nf, 256), 256, 0, s>>>(S.qcur, nf, S.fcur);
     G3_CHECK_LAUNCH();
   }
-  if (S.o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[1], s));
-  bu_pull<<<BFS_GRID, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.fcur, S.fnext, S.g->off,
-                                   S.g->col, ws->parent, ws->level, lnext, S.o->bu_reverse,
-                                   ws->ctrl);
+  if (ev_mid) G3_TRY_CUDA(cudaEventRecord(ev_mid, s));
+  const int grid = cap_grid(ws->nwords, 16, ws->grid_bu);
+  if (S.o->bu_reverse)
+    bu_pull<1><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.fcur, S.fnext, S.g->off,
+                                    S.g->col, ws->pl, lnext, ws->ctrl);
+  else
+    bu_pull<0><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.fcur, S.fnext, S.g->off,
+                                    S.g->col, ws->pl, lnext, ws->ctrl);
   G3_CHECK_LAUNCH();
+  return G3_OK;
+}
+
+// Candidate top-down bin thresholds timed in record_both mode.
+static const int kSweep[5][3] = {
+    {8, 256, 8192}, {16, 512, 16384}, {32, 1024, 32768}, {64, 2048, 65536}, {128, 4096, 131072}};
+
+// record_both mode: time every candidate top-down expansion and the
+// bottom-up one from the same state, restoring the visited bitmap and the
+// controller record after each trial. Fills r (times, best thresholds); the
+// state afterwards is the state before the trials.
+static g3_status record_trials(Level& S, int64_t nf, int32_t L, g3_level_stats* r) {
+  g3_bfs_ws* ws = S.ws;
+  cudaStream_t s = S.s;
+  const size_t vbytes = (size_t)ws->nwords * 4;
+  G3_TRY_CUDA(cudaMemcpyAsync(ws->vis_save, ws->visited, vbytes, cudaMemcpyDeviceToDevice, s));
+  Ctrl save;
+  G3_TRY_CUDA(cudaMemcpyAsync(&save, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  G3_TRY_CUDA(cudaStreamSynchronize(s));
+  float best = 1e30f;
+  for (int k = 0; k < 6; ++k) {
+    Ctrl c = save;
+    const bool td = k < 5;
+    if (td) {
+      c.t1 = kSweep[k][0];
+      c.t2 = kSweep[k][1];
+      c.t3 = kSweep[k][2];
+    }
+    G3_TRY_CUDA(cudaMemcpyAsync(ws->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    G3_TRY_CUDA(cudaEventRecord(ws->ev[4], s));
+    if (td)
+      G3_TRY(run_td(S, nf, L + 1, nullptr));
+    else
+      G3_TRY(run_bu(S, nf, L + 1, nullptr));
+    G3_TRY_CUDA(cudaEventRecord(ws->ev[5], s));
+    G3_TRY_CUDA(cudaMemcpyAsync(ws->visited, ws->vis_save, vbytes, cudaMemcpyDeviceToDevice, s));
+    G3_TRY_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ws->ev[4], ws->ev[5]);
+    if (td && ms < best) {
+      best = ms;
+      r->best_t1 = kSweep[k][0];
+      r->best_t2 = kSweep[k][1];
+      r->best_t3 = kSweep[k][2];
+    }
+    if (!td) r->t_bu_ms = ms;
+  }
+  r->t_td_ms = best;
+  G3_TRY_CUDA(cudaMemcpyAsync(ws->ctrl, &save, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+  G3_TRY_CUDA(cudaStreamSynchronize(s));
   return G3_OK;
 }
 
@@ -660,22 +815,18 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   const int64_t nnz = g->nnz;
   Ctrl* h = ws->h_ctrl;
 
-  bfs_init<<<g3_grid_for(nb > ws->nwords ? nb : ws->nwords, 256), 256, 0, s>>>(
-      nb, ws->nwords, ws->visited, ws->parent, ws->level);
-  G3_CHECK_LAUNCH();
+  G3_TRY_CUDA(cudaMemsetAsync(ws->visited, 0, (size_t)(ws->nwords + 1) * 4, s));
   bfs_root<<<1, 1, 0, s>>>(g->relabelled ? g->new_of_old : nullptr, root, nb, nnz, g->off,
-                           ws->visited, ws->parent, ws->level, ws->qa, ws->ctrl, o->t1, o->t2,
-                           o->t3);
+                           ws->visited, ws->pl, ws->qa, ws->ctrl, o->t1, o->t2, o->t3);
   G3_CHECK_LAUNCH();
 
   Level S{g, ws, o, s, ws->fa, ws->fb, ws->qa, ws->qb, true};
-  int32_t L = 0;
   int nrec = 0;
-  for (;; ++L) {
+  for (int32_t L = 0;; ++L) {
     G3_TRY_CUDA(cudaMemcpyAsync(h, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     G3_TRY_CUDA(cudaStreamSynchronize(s));
-    if (L > 0 && stats && nrec - 1 < max_stats && nrec >= 1) {
-      // close the previous record: examined edges and next size
+    if (L > 0 && stats && nrec >= 1 && nrec - 1 < max_stats) {
+      // close the previous record: examined edges, next size, times
       g3_level_stats& r = stats[nrec - 1];
       r.n_next = h->nf;
       if (r.dir == G3_DIR_BU) r.examined = h->exam_prev;
@@ -686,37 +837,32 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
     }
     const int64_t nf = h->nf;
     if (nf <= 0) break;
-    if (L > G3_MAX_LEVELS_GUARD) {
-      g3_set_error("g3_bfs: level guard exceeded");
-      return G3_ETIMEOUT;
-    }
     const int dir = h->dir;
-    if (stats && nrec < max_stats) {
-      g3_level_stats& r = stats[nrec];
-      memset(&r, 0, sizeof(r));
-      r.level = L;
-      r.dir = dir;
-      r.n_f = h->nf;
-      r.m_f = h->mf;
-      r.n_u = h->nu;
-      r.m_u = h->mu;
-      r.examined = h->mf;
-      r.id_min = h->id_min;
-      r.id_max = h->id_max;
-      for (int k = 0; k < 4; ++k) r.hist[k] = h->hist[k];
-      r.t1 = h->t1;
-      r.t2 = h->t2;
-      r.t3 = h->t3;
-      for (int k = 0; k < 4; ++k) r.mlp_out[k] = h->mlp_out[k];
+    g3_level_stats* rec = (stats && nrec < max_stats) ? &stats[nrec] : nullptr;
+    if (rec) {
+      memset(rec, 0, sizeof(*rec));
+      rec->level = L;
+      rec->dir = dir;
+      rec->n_f = h->nf;
+      rec->m_f = h->mf;
+      rec->n_u = h->nu;
+      rec->m_u = h->mu;
+      rec->examined = h->mf;
+      rec->id_min = h->id_min;
+      rec->id_max = h->id_max;
+      for (int k = 0; k < 4; ++k) rec->hist[k] = h->hist[k];
+      rec->t1 = h->t1;
+      rec->t2 = h->t2;
+      rec->t3 = h->t3;
+      for (int k = 0; k < 4; ++k) rec->mlp_out[k] = h->mlp_out[k];
     }
     ++nrec;
+    if (o->record_both && rec) G3_TRY(record_trials(S, nf, L, rec));
     if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[0], s));
-    bfs_reset_next<<<1, 1, 0, s>>>(ws->ctrl);
-    G3_CHECK_LAUNCH();
     if (dir == G3_DIR_TD) {
-      G3_TRY(run_td(S, nf, L + 1));
+      G3_TRY(run_td(S, nf, L + 1, o->timing ? ws->ev[1] : nullptr));
     } else {
-      G3_TRY(run_bu(S, nf, L + 1));
+      G3_TRY(run_bu(S, nf, L + 1, o->timing ? ws->ev[1] : nullptr));
     }
     if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[2], s));
     bfs_control<<<1, 32, 0, s>>>(ws->ctrl, nb, nnz, o->controller, o->alpha, o->beta,
@@ -741,9 +887,9 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   const bool dev_p = is_device_ptr(parent), dev_l = is_device_ptr(level);
   int32_t* op = dev_p ? parent : ws->out_parent;
   int32_t* ol = dev_l ? level : ws->out_level;
-  bfs_translate<<<g3_grid_for(g->n, 256), 256, 0, s>>>(
+  bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, s>>>(
       g->n, nb, root, g->relabelled ? g->new_of_old : nullptr,
-      g->relabelled ? g->old_of_new : nullptr, ws->parent, ws->level, op, ol);
+      g->relabelled ? g->old_of_new : nullptr, ws->visited, ws->pl, op, ol);
   G3_CHECK_LAUNCH();
   if (!dev_p)
     G3_TRY_CUDA(cudaMemcpyAsync(parent, op, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));

@@ -40,7 +40,7 @@ def test_status_strings_and_version(L):
 def test_default_options(L):
     o = g3.opts()
     assert (o.controller, o.alpha, o.beta, o.t1, o.t2, o.t3) == (0, 14, 24, 32, 1024, 32768)
-    assert o.bu_reverse == 0 and o.timing == 0 and not o.mlp_params
+    assert o.bu_reverse == 1 and o.timing == 0 and not o.mlp_params
 
 
 def test_bad_arguments_rejected_on_host(L):

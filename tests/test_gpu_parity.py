@@ -118,9 +118,10 @@ def test_bfs_small_cases(case, relabel):
     g = gpu_pipeline(src, dst, n, relabel)
     rng = np.random.default_rng(n)
     roots = sorted(set([0, n - 1] + rng.integers(0, n, 6).tolist()))
-    for ctrl in (g3.G3_CTRL_HEURISTIC, g3.G3_CTRL_TOPDOWN, g3.G3_CTRL_BOTTOMUP):
+    for ctrl, rev in ((g3.G3_CTRL_HEURISTIC, 1), (g3.G3_CTRL_TOPDOWN, 1),
+                      (g3.G3_CTRL_BOTTOMUP, 1), (g3.G3_CTRL_BOTTOMUP, 0)):
         for root in roots:
-            parent, level, _ = run_bfs(g, root, n, controller=ctrl)
+            parent, level, _ = run_bfs(g, root, n, controller=ctrl, bu_reverse=rev)
             _, lref = oracle.bfs(off_o, col_o, root)
             assert np.array_equal(level, lref), (name, root, ctrl)
             assert oracle.validate(off_o, col_o, root, parent, level) == 0, (name, root, ctrl)
@@ -143,10 +144,11 @@ def _levels_new(ref, level_orig):
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(controller=g3.G3_CTRL_TOPDOWN),
-                                dict(controller=g3.G3_CTRL_BOTTOMUP), dict(bu_reverse=1),
+                                dict(controller=g3.G3_CTRL_BOTTOMUP), dict(bu_reverse=0),
+                                dict(controller=g3.G3_CTRL_BOTTOMUP, bu_reverse=0),
                                 dict(t1=2, t2=4, t3=8), dict(alpha=64, beta=8)],
-                         ids=["heuristic", "topdown", "bottomup", "reverse", "tiny_bins",
-                              "alpha64_beta8"])
+                         ids=["heuristic", "topdown", "bottomup", "forward_scan",
+                              "bottomup_forward", "tiny_bins", "alpha64_beta8"])
 def test_bfs_kron16_all_roots(kron16, kw):
     K = kron16
     ref = K["ref"]
@@ -166,7 +168,7 @@ def test_bfs_kron16_all_roots(kron16, kw):
             assert a["id_min"] == f.min() and a["id_max"] == f.max()
             if a["dir"] == g3.G3_DIR_BU:
                 assert a["examined"] == oracle.bu_examined(ref["off_r"], ref["col_r"], lnew, L,
-                                                           reverse=bool(kw.get("bu_reverse")))
+                                                           reverse=bool(kw.get("bu_reverse", 1)))
         if not kw.get("controller"):
             expect = direction.heuristic_directions(ref["off_r"], lnew, kw.get("alpha", 14),
                                                     kw.get("beta", 24))
@@ -244,3 +246,17 @@ def test_kron22_permutation_and_levels():
         assert np.array_equal(level, lref)
         assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
     g.free()
+
+
+def test_record_both_mode_keeps_results_exact(kron16):
+    K = kron16
+    ref = K["ref"]
+    sweep = {(8, 256, 8192), (16, 512, 16384), (32, 1024, 32768), (64, 2048, 65536),
+             (128, 4096, 131072)}
+    for root in K["roots"][:4].tolist():
+        parent, level, st = run_bfs(K["g"], root, K["n"], max_stats=64, record_both=1, timing=1)
+        _, lref = oracle.bfs(ref["off"], ref["col"], root)
+        assert np.array_equal(level, lref)
+        assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
+        assert st and all(a["t_td_ms"] > 0 and a["t_bu_ms"] > 0 for a in st)
+        assert all((a["best_t1"], a["best_t2"], a["best_t3"]) in sweep for a in st)
