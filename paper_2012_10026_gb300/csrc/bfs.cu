@@ -44,6 +44,7 @@ struct Ctrl {
   unsigned long long nx_hist[4];
   unsigned int nx_min, nx_max;
   unsigned long long bin_len[4];  // top-down bins of the current level
+  unsigned long long g_pack;      // grid bin: slots << 38 | edge total
   unsigned long long conv_len;    // bitmap -> queue conversion length
   // current frontier F_L and its decision
   long long nf, mf, nu, mu, exam_prev;
@@ -62,19 +63,20 @@ struct g3_bfs_ws {
   int64_t nwords;
   uint32_t *visited, *fa, *fb, *vis_save;
   int32_t *qa, *qb, *bins;  // bins: 3 segments of nb entries (warp, CTA, grid)
+  int64_t* goff;            // edge offset of each grid-bin vertex
   int2* pl;                 // (parent, level) per BFS-graph vertex
   int32_t *out_parent, *out_level;  // staging for host outputs (n entries)
   Ctrl* ctrl;
   Ctrl* h_ctrl;  // pinned
   cudaEvent_t ev[6];
   // resident-grid sizes (SMs x blocks per SM) per kernel
-  int grid_front, grid_warp, grid_cta, grid_grid, grid_stats, grid_bu, grid_conv, grid_tr;
+  int grid_front, grid_bins, grid_bu, grid_conv, grid_tr;
 };
 
 void g3_bfs_ws_free(g3_bfs_ws* ws) {
   if (!ws) return;
   void* all[] = {ws->visited, ws->fa,  ws->fb,         ws->vis_save,  ws->qa,  ws->qb,
-                 ws->bins,    ws->pl,  ws->out_parent, ws->out_level, ws->ctrl};
+                 ws->bins,    ws->pl,  ws->out_parent, ws->out_level, ws->ctrl, ws->goff};
   for (void* p : all)
     if (p) cudaFree(p);
   if (ws->h_ctrl) cudaFreeHost(ws->h_ctrl);
@@ -166,6 +168,7 @@ __device__ __forceinline__ void reset_next(Ctrl* c) {
   }
   c->nx_min = 0xFFFFFFFFu;
   c->nx_max = 0;
+  c->g_pack = 0;
   c->conv_len = 0;
 }
 
@@ -253,35 +256,52 @@ __device__ __forceinline__ void wq_push(WarpQueue& q, bool want, int32_t item, i
   __shared__ int32_t wq_mem[8][WQ_CAP];                    \
   WarpQueue q{wq_mem[threadIdx.x >> 5], 0}
 
-// Claims w for v. All 32 lanes must call it together.
-__device__ __forceinline__ void td_visit(const TdArgs& a, WarpQueue& q, bool has, int32_t w,
-                                         int32_t v) {
+// Claims w for v and records the statistics of the claimed vertex (the next
+// frontier's degree sum, label range and histogram). All 32 lanes must call
+// it together.
+__device__ __forceinline__ void td_visit(const TdArgs& a, WarpQueue& q, StatAcc& acc, bool has,
+                                         int32_t w, int32_t v) {
   bool claim = has && td_claim(a.visited, w);
-  if (claim) a.pl[w] = make_int2(v, a.lnext);
+  if (claim) {
+    a.pl[w] = make_int2(v, a.lnext);
+    acc.add_vertex(w, a.off[w + 1] - a.off[w]);
+  }
   wq_push(q, claim, w, a.qnext, &a.c->q_len);
 }
 
 // Processes row entries [b, e) of vertex v with `nthr` cooperating threads
 // (index t), four entries per thread per step through aligned 128-bit loads.
 // Every lane of each participating warp runs the same number of steps.
-__device__ __forceinline__ void td_row_vec4(const TdArgs& a, WarpQueue& q, int32_t v, int64_t b,
-                                            int64_t e, int64_t t, int64_t nthr, int64_t steps) {
+__device__ __forceinline__ void td_row_vec4(const TdArgs& a, WarpQueue& q, StatAcc& acc,
+                                            int32_t v, int64_t b, int64_t e, int64_t t,
+                                            int64_t nthr, int64_t steps) {
   const int64_t a0 = b & ~3ll;
   for (int64_t s = 0; s < steps; ++s) {
     const int64_t j = a0 + 4 * (t + s * nthr);
     int4 x = make_int4(0, 0, 0, 0);
     if (j < e) x = *reinterpret_cast<const int4*>(a.col + j);
-    td_visit(a, q, j + 0 >= b && j + 0 < e, x.x, v);
-    td_visit(a, q, j + 1 >= b && j + 1 < e, x.y, v);
-    td_visit(a, q, j + 2 >= b && j + 2 < e, x.z, v);
-    td_visit(a, q, j + 3 >= b && j + 3 < e, x.w, v);
+    td_visit(a, q, acc, j + 0 >= b && j + 0 < e, x.x, v);
+    td_visit(a, q, acc, j + 1 >= b && j + 1 < e, x.y, v);
+    td_visit(a, q, acc, j + 2 >= b && j + 2 < e, x.z, v);
+    td_visit(a, q, acc, j + 3 >= b && j + 3 < e, x.w, v);
   }
 }
 
+// Grid-bin slots and their edge offsets are handed out by one 64-bit atomic
+// (slot count in the high bits, edge total in the low 38 bits), so the offsets
+// ascend with the slot index.
+#define GP_SHIFT 38
+#define GP_MASK ((1ull << GP_SHIFT) - 1ull)
+
+// Thread per frontier vertex: degree < t1 expanded here, larger degrees
+// binned (warp / CTA / grid).
 __global__ void __launch_bounds__(256) td_front(TdArgs a, const int32_t* __restrict__ q,
-                                                int64_t qlen, int32_t* bins, int64_t nb1) {
+                                                int64_t qlen, int32_t* bins, int64_t* goff,
+                                                int64_t nb1) {
   const int t1 = a.c->t1, t2 = a.c->t2, t3 = a.c->t3;
   WQ_DECLARE(wq);
+  StatAcc acc;
+  acc.init();
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < qlen;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
@@ -290,71 +310,75 @@ __global__ void __launch_bounds__(256) td_front(TdArgs a, const int32_t* __restr
     int64_t b = act ? a.off[v] : 0, e = act ? a.off[v + 1] : 0, d = e - b;
     bool small = act && d < t1;
     int bin = !act || small ? -1 : (d < t2 ? 0 : (d < t3 ? 1 : 2));
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 2; ++k)
       g3_warp_append(0xffffffffu, bin == k, v, bins + k * nb1, &a.c->bin_len[1 + k]);
+    if (bin == 2) {
+      const unsigned long long old =
+          atomicAdd(&a.c->g_pack, (1ull << GP_SHIFT) | (unsigned long long)d);
+      const int64_t slot = (int64_t)(old >> GP_SHIFT);
+      bins[2 * nb1 + slot] = v;
+      goff[slot] = (int64_t)(old & GP_MASK);
+    }
     const int cnt = small ? (int)d : 0;
     const int maxc = __reduce_max_sync(0xffffffffu, cnt);
     for (int k = 0; k < maxc; ++k) {
       bool has = k < cnt;
       int32_t w = has ? a.col[b + k] : 0;
-      td_visit(a, wq, has, w, v);
+      td_visit(a, wq, acc, has, w, v);
     }
   }
   wq_flush(wq, a.qnext, &a.c->q_len);
+  acc.flush(a.c);
 }
 
-__global__ void __launch_bounds__(256) td_warp(TdArgs a, const int32_t* __restrict__ bin) {
-  const int64_t len = (int64_t)a.c->bin_len[1];
+// The three bins in one launch: warp per warp-bin vertex, CTA per CTA-bin
+// vertex, and the grid bin as one flattened edge range split evenly over all
+// warps of the grid (Algorithm 4's even split, applied to every hub at once).
+__global__ void __launch_bounds__(256) td_bins(TdArgs a, const int32_t* __restrict__ bins,
+                                               const int64_t* __restrict__ goff, int64_t nb1) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   WQ_DECLARE(wq);
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < len; i += nwarps) {
-    int32_t v = bin[i];
-    int64_t b = a.off[v], e = a.off[v + 1];
-    int64_t steps = (e - (b & ~3ll) + 127) / 128;
-    td_row_vec4(a, wq, v, b, e, lane, 32, steps);
-  }
-  wq_flush(wq, a.qnext, &a.c->q_len);
-}
-
-__global__ void __launch_bounds__(256) td_cta(TdArgs a, const int32_t* __restrict__ bin) {
-  const int64_t len = (int64_t)a.c->bin_len[2];
-  WQ_DECLARE(wq);
-  for (int64_t i = blockIdx.x; i < len; i += gridDim.x) {
-    int32_t v = bin[i];
-    int64_t b = a.off[v], e = a.off[v + 1];
-    int64_t steps = (e - (b & ~3ll) + 4 * blockDim.x - 1) / (4 * blockDim.x);
-    td_row_vec4(a, wq, v, b, e, threadIdx.x, blockDim.x, steps);
-  }
-  wq_flush(wq, a.qnext, &a.c->q_len);
-}
-
-__global__ void __launch_bounds__(256) td_grid(TdArgs a, const int32_t* __restrict__ bin) {
-  const int64_t len = (int64_t)a.c->bin_len[3];
-  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  WQ_DECLARE(wq);
-  for (int64_t i = 0; i < len; ++i) {
-    int32_t v = bin[i];
-    int64_t b = a.off[v], e = a.off[v + 1];
-    int64_t steps = (e - (b & ~3ll) + 4 * nthr - 1) / (4 * nthr);
-    td_row_vec4(a, wq, v, b, e, t, nthr, steps);
-  }
-  wq_flush(wq, a.qnext, &a.c->q_len);
-}
-
-// Statistics of the queue F_{L+1} produced by a top-down level.
-__global__ void __launch_bounds__(256) td_stats(const int32_t* __restrict__ q,
-                                                const int64_t* __restrict__ off, Ctrl* c) {
-  const int64_t len = (int64_t)c->q_len;
   StatAcc acc;
   acc.init();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t v = q[i];
-    acc.add_vertex(v, off[v + 1] - off[v]);
+  const int64_t len1 = (int64_t)a.c->bin_len[1];
+  for (int64_t i = gw; i < len1; i += nwarps) {
+    int32_t v = bins[i];
+    int64_t b = a.off[v], e = a.off[v + 1];
+    int64_t steps = (e - (b & ~3ll) + 127) / 128;
+    td_row_vec4(a, wq, acc, v, b, e, lane, 32, steps);
   }
-  acc.flush(c);
+  const int64_t len2 = (int64_t)a.c->bin_len[2];
+  for (int64_t i = blockIdx.x; i < len2; i += gridDim.x) {
+    int32_t v = bins[nb1 + i];
+    int64_t b = a.off[v], e = a.off[v + 1];
+    int64_t steps = (e - (b & ~3ll) + 4 * blockDim.x - 1) / (4 * blockDim.x);
+    td_row_vec4(a, wq, acc, v, b, e, threadIdx.x, blockDim.x, steps);
+  }
+  const unsigned long long gp = a.c->g_pack;
+  const int64_t nh = (int64_t)(gp >> GP_SHIFT), E = (int64_t)(gp & GP_MASK);
+  if (E > 0) {
+    const int32_t* gbin = bins + 2 * nb1;
+    const int64_t per = (((E + nwarps - 1) / nwarps) + 31) & ~31ll;
+    const int64_t j0 = gw * per, j1 = min(E, j0 + per);
+    if (j0 < j1) {
+      int64_t h = g3_upper_bound_i64(goff, nh, j0) - 1;
+      for (int64_t base = j0; base < j1; base += 32) {
+        const int64_t j = base + lane;
+        const bool act = j < j1;
+        int32_t v = 0, w = 0;
+        if (act) {
+          while (h + 1 < nh && goff[h + 1] <= j) ++h;
+          v = gbin[h];
+          w = a.col[a.off[v] + (j - goff[h])];
+        }
+        td_visit(a, wq, acc, act, w, v);
+      }
+    }
+  }
+  wq_flush(wq, a.qnext, &a.c->q_len);
+  acc.flush(a.c);
 }
 
 // -------------------------------------------------------------- bottom-up
@@ -647,6 +671,7 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
       {(void**)&ws->fb, nw * 4},          {(void**)&ws->vis_save, nw * 4},
       {(void**)&ws->qa, nb1 * 4},         {(void**)&ws->qb, nb1 * 4},
       {(void**)&ws->bins, nb1 * 4 * 3},   {(void**)&ws->pl, nb1 * 8},
+      {(void**)&ws->goff, nb1 * 8},
       {(void**)&ws->out_parent, n1 * 4},  {(void**)&ws->out_level, n1 * 4},
       {(void**)&ws->ctrl, sizeof(Ctrl)},
   };
@@ -671,10 +696,7 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
       return G3_ECUDA;
     }
   ws->grid_front = resident_grid(td_front, 256);
-  ws->grid_warp = resident_grid(td_warp, 256);
-  ws->grid_cta = resident_grid(td_cta, 256);
-  ws->grid_grid = resident_grid(td_grid, 256);
-  ws->grid_stats = resident_grid(td_stats, 256);
+  ws->grid_bins = resident_grid(td_bins, 256);
   ws->grid_bu = resident_grid(bu_pull<1>, 256);
   int g0 = resident_grid(bu_pull<0>, 256);
   if (g0 < ws->grid_bu) ws->grid_bu = g0;
@@ -722,15 +744,10 @@ static g3_status run_td(Level& S, int64_t nf, int32_t lnext, cudaEvent_t ev_mid)
   if (ev_mid) G3_TRY_CUDA(cudaEventRecord(ev_mid, s));
   TdArgs a{S.g->off, S.g->col, ws->visited, ws->pl, lnext, S.qnext, ws->ctrl};
   const int64_t nb1 = ws->nb + 4;
-  td_front<<<cap_grid(nf, 256, ws->grid_front), 256, 0, s>>>(a, S.qcur, nf, ws->bins, nb1);
+  td_front<<<cap_grid(nf, 256, ws->grid_front), 256, 0, s>>>(a, S.qcur, nf, ws->bins, ws->goff,
+                                                             nb1);
   G3_CHECK_LAUNCH();
-  td_warp<<<cap_grid(nf, 8, ws->grid_warp), 256, 0, s>>>(a, ws->bins);
-  G3_CHECK_LAUNCH();
-  td_cta<<<cap_grid(nf, 1, ws->grid_cta), 256, 0, s>>>(a, ws->bins + nb1);
-  G3_CHECK_LAUNCH();
-  td_grid<<<ws->grid_grid, 256, 0, s>>>(a, ws->bins + 2 * nb1);
-  G3_CHECK_LAUNCH();
-  td_stats<<<cap_grid(ws->nb, 256, ws->grid_stats), 256, 0, s>>>(S.qnext, S.g->off, ws->ctrl);
+  td_bins<<<ws->grid_bins, 256, 0, s>>>(a, ws->bins, ws->goff, nb1);
   G3_CHECK_LAUNCH();
   return G3_OK;
 }
