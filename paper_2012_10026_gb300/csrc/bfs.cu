@@ -66,17 +66,21 @@ struct g3_bfs_ws {
   int64_t* goff;            // edge offset of each grid-bin vertex
   int2* pl;                 // (parent, level) per BFS-graph vertex
   int32_t *out_parent, *out_level;  // staging for host outputs (n entries)
+  unsigned* bcount;                 // translation: entries per window
+  unsigned long long* bucket;       // translation: TR_W slots per window
+  int64_t nbuckets;
   Ctrl* ctrl;
   Ctrl* h_ctrl;  // pinned
   cudaEvent_t ev[6];
   // resident-grid sizes (SMs x blocks per SM) per kernel
-  int grid_front, grid_bins, grid_bu, grid_conv, grid_tr;
+  int grid_front, grid_bins, grid_bu, grid_conv, grid_tr, grid_trb, grid_trw;
 };
 
 void g3_bfs_ws_free(g3_bfs_ws* ws) {
   if (!ws) return;
   void* all[] = {ws->visited, ws->fa,  ws->fb,         ws->vis_save,  ws->qa,  ws->qb,
-                 ws->bins,    ws->pl,  ws->out_parent, ws->out_level, ws->ctrl, ws->goff};
+                 ws->bins,    ws->pl,  ws->out_parent, ws->out_level, ws->ctrl, ws->goff,
+                 ws->bcount,  ws->bucket};
   for (void* p : all)
     if (p) cudaFree(p);
   if (ws->h_ctrl) cudaFreeHost(ws->h_ctrl);
@@ -632,6 +636,68 @@ __global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
   }
 }
 
+// Output translation of a relabelled graph in two streaming passes instead of
+// one random gather per vertex. The original IDs are cut into windows of
+// TR_W; pass 1 walks the BFS-graph labels in order (coalesced) and appends
+// each reached vertex to its window's bucket (one counter atomic, writes
+// that stay sequential per bucket); pass 2 gives each window to one block,
+// which assembles the window's parent[] and level[] in shared memory (-1 for
+// unreached) and writes them out coalesced.
+#define TR_SHIFT 12
+#define TR_W (1 << TR_SHIFT)
+#define TR_LEVEL_BITS 20
+
+__global__ void tr_bucket(int32_t nb, const uint32_t* __restrict__ visited,
+                          const int2* __restrict__ pl, const int32_t* __restrict__ old_of_new,
+                          unsigned* bcount, unsigned long long* bucket) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nb;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    if (!((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u)) continue;
+    const int2 t = pl[x];
+    const int32_t o = old_of_new[x];
+    const int32_t po = __ldg(&old_of_new[t.x]);
+    const int64_t b = o >> TR_SHIFT;
+    const unsigned slot = atomicAdd(&bcount[b], 1u);
+    bucket[b * TR_W + slot] = ((unsigned long long)(o & (TR_W - 1)) << 52) |
+                              ((unsigned long long)(t.y & ((1 << TR_LEVEL_BITS) - 1)) << 32) |
+                              (unsigned)po;
+  }
+}
+
+__global__ void __launch_bounds__(256) tr_window(int32_t n, int32_t root,
+                                                 const unsigned* __restrict__ bcount,
+                                                 const unsigned long long* __restrict__ bucket,
+                                                 int32_t* parent, int32_t* level) {
+  __shared__ int32_t sp[TR_W], sl[TR_W];
+  const int64_t nbk = ((int64_t)n + TR_W - 1) >> TR_SHIFT;
+  for (int64_t b = blockIdx.x; b < nbk; b += gridDim.x) {
+    const int64_t base = b << TR_SHIFT;
+    for (int i = threadIdx.x; i < TR_W; i += blockDim.x) {
+      sp[i] = -1;
+      sl[i] = -1;
+    }
+    __syncthreads();
+    const unsigned cnt = bcount[b];
+    for (unsigned i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const unsigned long long e = bucket[base + i];
+      const int lo = (int)(e >> 52);
+      sp[lo] = (int32_t)(unsigned)(e & 0xFFFFFFFFull);
+      sl[lo] = (int32_t)((e >> 32) & ((1u << TR_LEVEL_BITS) - 1));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && root >= base && root < base + TR_W) {
+      sp[root - base] = root;  // also an isolated root
+      sl[root - base] = 0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TR_W && base + i < n; i += blockDim.x) {
+      parent[base + i] = sp[i];
+      level[base + i] = sl[i];
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ host
 extern "C" void g3_bfs_opts_default(g3_bfs_opts* o) {
   if (!o) return;
@@ -673,6 +739,8 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
       {(void**)&ws->bins, nb1 * 4 * 3},   {(void**)&ws->pl, nb1 * 8},
       {(void**)&ws->goff, nb1 * 8},
       {(void**)&ws->out_parent, n1 * 4},  {(void**)&ws->out_level, n1 * 4},
+      {(void**)&ws->bcount, ((size_t)(g->n >> TR_SHIFT) + 2) * 4},
+      {(void**)&ws->bucket, ((size_t)(g->n >> TR_SHIFT) + 2) * TR_W * 8},
       {(void**)&ws->ctrl, sizeof(Ctrl)},
   };
   for (auto& r : req) {
@@ -702,6 +770,9 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
   if (g0 < ws->grid_bu) ws->grid_bu = g0;
   ws->grid_conv = resident_grid(bitmap_to_q, 256);
   ws->grid_tr = resident_grid(bfs_translate, 256);
+  ws->grid_trb = resident_grid(tr_bucket, 256);
+  ws->grid_trw = resident_grid(tr_window, 256);
+  ws->nbuckets = ((int64_t)g->n + TR_W - 1) >> TR_SHIFT;
   *out = ws;
   return G3_OK;
 }
@@ -904,10 +975,21 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   const bool dev_p = is_device_ptr(parent), dev_l = is_device_ptr(level);
   int32_t* op = dev_p ? parent : ws->out_parent;
   int32_t* ol = dev_l ? level : ws->out_level;
-  bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, s>>>(
-      g->n, nb, root, g->relabelled ? g->new_of_old : nullptr,
-      g->relabelled ? g->old_of_new : nullptr, ws->visited, ws->pl, op, ol);
-  G3_CHECK_LAUNCH();
+  if (g->relabelled && nrec < (1 << TR_LEVEL_BITS)) {
+    G3_TRY_CUDA(cudaMemsetAsync(ws->bcount, 0, (size_t)ws->nbuckets * 4, s));
+    tr_bucket<<<cap_grid(nb, 256, ws->grid_trb), 256, 0, s>>>(nb, ws->visited, ws->pl,
+                                                               g->old_of_new, ws->bcount,
+                                                               ws->bucket);
+    G3_CHECK_LAUNCH();
+    tr_window<<<cap_grid(ws->nbuckets, 1, ws->grid_trw), 256, 0, s>>>(
+        g->n, root, ws->bcount, ws->bucket, op, ol);
+    G3_CHECK_LAUNCH();
+  } else {  // labels are the original IDs, or levels too deep for the bucket format
+    bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, s>>>(
+        g->n, nb, root, g->relabelled ? g->new_of_old : nullptr,
+        g->relabelled ? g->old_of_new : nullptr, ws->visited, ws->pl, op, ol);
+    G3_CHECK_LAUNCH();
+  }
   if (!dev_p)
     G3_TRY_CUDA(cudaMemcpyAsync(parent, op, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
   if (!dev_l)
