@@ -265,13 +265,14 @@ def gpu_arm(args, rank, world):
     info = g.info
     ctrl = {"heuristic": g3.G3_CTRL_HEURISTIC, "learned": g3.G3_CTRL_LEARNED,
             "topdown": g3.G3_CTRL_TOPDOWN, "bottomup": g3.G3_CTRL_BOTTOMUP}[args.controller]
-    kw = dict(controller=ctrl, timing=1, bu_reverse=args.bu_reverse)
+    kw = dict(controller=ctrl, bu_reverse=args.bu_reverse)
     mlp_t = None
     if ctrl == g3.G3_CTRL_LEARNED:
         with open(args.mlp) as f:
             mlp_t = torch.tensor(json.load(f)["params"], dtype=torch.float32, device="cuda")
         kw["mlp_params"] = mlp_t
-    opts = g3.opts(**kw)
+    opts = g3.opts(**kw)  # default path: the level loop runs as one CUDA graph
+    opts_timed = g3.opts(timing=1, **kw)  # host-driven, CUDA events around each level
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
     level = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -289,21 +290,20 @@ def gpu_arm(args, rank, world):
     ev_s = torch.cuda.Event(enable_timing=True)
     ev_e = torch.cuda.Event(enable_timing=True)
 
-    def one_step(record):
+    def one_step(o, nstats):
         times, stats = [], []
         for r in roots:
             flush.fill_(1)
             ev_s.record()
-            st = g3.g3_bfs(g, r, parent, level, opts, max_stats=256)
+            st = g3.g3_bfs(g, r, parent, level, o, max_stats=nstats)
             ev_e.record()
             ev_e.synchronize()
             times.append(ev_s.elapsed_time(ev_e))
-            if record:
-                stats.append(st)
+            stats.append(st)
         return times, stats
 
     for _ in range(args.warmup):
-        one_step(False)
+        one_step(opts, 0)
     clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") \
         if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/g3_clocks_{rank}.csv"
     sampler = start_clock_sampler(clk_path)
@@ -312,14 +312,17 @@ def gpu_arm(args, rank, world):
     torch.cuda.synchronize()
     launches0 = L.g3_kernel_launches()
     w0 = time.perf_counter()
-    all_t, all_st = [], []
+    all_t = []
     for _ in range(args.steps):
-        t, st = one_step(True)
+        t, _ = one_step(opts, 0)
         all_t += t
-        all_st += st
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
     launches = L.g3_kernel_launches() - launches0
+    graph_launches = len(roots) * args.steps  # one level-loop graph per search
+    # instrumented step: the same kernels launched level by level with CUDA
+    # events around each level's expansion, for the per-kernel roofline
+    inst_t, all_st = one_step(opts_timed, 256)
     if dist:
         dist.barrier()
     clocks = stop_clock_sampler(sampler, clk_path, local)
@@ -346,13 +349,26 @@ def gpu_arm(args, rank, world):
     peak, peak_kind = load_peaks()
     bytes_, tms, launches_dom = agg[dom]
     achieved = bytes_ / (tms / 1e3) / 1e9 if tms > 0 else 0.0
+    # kernels run inside the level-loop graphs (not host launches): per level
+    # the body selector and the controller, plus the SWITCH body's kernels
+    # (top-down 2, bottom-up 1, and 1 or 2 more for a format conversion)
+    graph_kernels = 0
+    for st in all_st:
+        prev = 0
+        for s in st:
+            body = 2 if s["dir"] == 0 else 1
+            if s["level"] > 0 and s["dir"] != prev:
+                body += 1 if s["dir"] == 0 else 2
+            graph_kernels += 2 + body
+            prev = s["dir"]
+    launches += graph_kernels * args.steps
 
     # end to end through the C ABI with pinned host outputs
     e2e = None
     if not args.no_e2e:
         hp = torch.empty(n, dtype=torch.int32).pin_memory()
         hl = torch.empty(n, dtype=torch.int32).pin_memory()
-        plain = g3.opts(**{k: v for k, v in kw.items() if k != "timing"})
+        plain = opts
         et = []
         for i in range(args.warmup + args.steps):
             for r in roots:
@@ -391,13 +407,19 @@ def gpu_arm(args, rank, world):
             "warmup": args.warmup, "ms_per_step": sum(all_t) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": workload_config(args),
-            "roofline": {"bound": "hbm", "kernel": "bu_pull" if dom == 1 else "td_expand",
+            "roofline": {"bound": "hbm",
+                         "kernel": "bu_pull" if dom == 1 else "td_front+td_bins",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "peak_kind": peak_kind, "launches": launches_dom,
                          "avg_launch_ms": tms / max(launches_dom, 1),
-                         "bytes_per_launch": bytes_ / max(launches_dom, 1)},
+                         "bytes_per_launch": bytes_ / max(launches_dom, 1),
+                         "timed_in": "instrumented step after the timed region: the same "
+                                     "kernels launched level by level, CUDA events on the "
+                                     "launching stream around each level's expansion"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "graph_launches": graph_launches,
+            "instrumented_hm_gteps": harmonic_gteps([m_r[r] for r in roots], inst_t),
             "clocks": clocks,
             "wall_s_timed": wall,
             "graph": {"n": info["n"], "n_plus": info["n_plus"], "nnz": info["nnz"],

@@ -2,16 +2,27 @@
 //
 // Per level L the frontier F_L is either a queue (after a top-down level) or
 // a bitmap (after a bottom-up level). A one-warp controller kernel decides
-// the direction of every level on the device from the frontier statistics;
-// the host reads the decision back (one small copy per level) and launches:
+// the direction of every level on the device from the frontier statistics
+// and records which buffers hold the frontier; every expansion kernel reads
+// its direction, sizes and buffers from that device-side record. So the whole
+// level loop can run without the host:
+//
+//   graph mode (default): one CUDA graph per search -- a WHILE node whose body
+//     is a SWITCH over the four level kinds {top-down from a queue, top-down
+//     from a bitmap, bottom-up from a bitmap, bottom-up from a queue} followed
+//     by the controller, which sets the next kind and ends the loop. A launch
+//     runs at most GRAPH_LEVEL_CAP levels; deeper searches continue on the
+//     host-driven path from the same state.
+//   host-driven mode (per-level timing or record_both): the host reads the
+//     controller record after every level and launches the same kernels.
 //
 //   top-down (Algorithms 1 and 4): td_front walks the queue one thread per
 //     vertex; vertices with degree < t1 are expanded on the spot, the others
-//     go to three bins expanded by one warp (t1 <= deg < t2), one CTA
-//     (t2 <= deg < t3) or the whole grid (deg >= t3) -- the GPU form of
-//     Algorithm 4's even split of a long neighbour list over all threads.
-//     Neighbour lists are read with aligned 128-bit loads. A neighbour is
-//     claimed by an atomicOr on its word of the visited bitmap; the winner
+//     go to three bins: one warp (t1 <= deg < t2), one CTA (t2 <= deg < t3)
+//     or the grid bin (deg >= t3), whose lists are flattened into one edge
+//     range split evenly over all warps -- the GPU form of Algorithm 4's even
+//     split. Neighbour lists are read with aligned 128-bit loads. A neighbour
+//     is claimed by an atomicOr on its word of the visited bitmap; the winner
 //     writes (parent, level) and appends it to the next queue through a
 //     per-warp shared-memory buffer (one global atomic per ~224 vertices).
 //   bottom-up (Algorithms 5 and 6): one warp per pair of 32-vertex words of
@@ -26,15 +37,20 @@
 //
 // Statistics of the next frontier (size, degree sum, label range, degree
 // histogram, edges examined) are reduced per block and added with one atomic
-// per block. (parent, level) of BFS-graph vertices are kept packed as int2 and
-// are only meaningful where the visited bit is set, so nothing but the
-// visited bitmap is cleared per search.
+// per block; the controller logs them per level. (parent, level) of BFS-graph
+// vertices are kept packed as int2 and are only meaningful where the visited
+// bit is set, so nothing but the visited bitmap is cleared per search.
 #include <math.h>
 #include <string.h>
 
 #include "g3_prims.cuh"
 
-// Device-side controller record; mirrored to pinned host memory each level.
+#define LOG_MAX 4096           // per-level records kept on the device
+#define GRAPH_LEVEL_CAP 4096   // levels one graph launch may run
+
+enum { MODE_TD_Q = 0, MODE_TD_B = 1, MODE_BU_B = 2, MODE_BU_Q = 3, MODE_DONE = 4 };
+
+// Device-side controller record.
 struct Ctrl {
   // accumulators for the frontier being produced (reset by the controller)
   unsigned long long q_len;     // top-down: next queue length
@@ -47,15 +63,32 @@ struct Ctrl {
   unsigned long long g_pack;      // grid bin: slots << 38 | edge total
   unsigned long long conv_len;    // bitmap -> queue conversion length
   // current frontier F_L and its decision
-  long long nf, mf, nu, mu, exam_prev;
+  long long nf, mf, nu, mu;
   long long hist[4];
   int id_min, id_max;
   int level;
   int dir;
   int t1, t2, t3;
   float mlp_out[4];
-  long long prev_nf;
   long long n_visited, m_visited;
+  // where F_L lives: queue q[qsel] when fmt_queue, else bitmap f[fsel]
+  int qsel, fsel, fmt_queue;
+  int mode;  // MODE_* of the current level
+  int cap;   // the controller ends the search at this level (graph launches)
+};
+
+// Per-level record written by the controller (and bfs_root for level 0).
+struct LevelLog {
+  int dir, t1, t2, t3;
+  long long nf, mf, nu, mu, examined, n_next;
+  int id_min, id_max;
+  long long hist[4];
+  float mlp_out[4];
+};
+
+struct Bufs {
+  int32_t* q[2];
+  uint32_t* f[2];
 };
 
 struct g3_bfs_ws {
@@ -71,21 +104,27 @@ struct g3_bfs_ws {
   int64_t nbuckets;
   Ctrl* ctrl;
   Ctrl* h_ctrl;  // pinned
+  LevelLog* log;
   cudaEvent_t ev[6];
   // resident-grid sizes (SMs x blocks per SM) per kernel
   int grid_front, grid_bins, grid_bu, grid_conv, grid_tr, grid_trb, grid_trw;
+  // graph mode: instantiated level loop and the options it was built for
+  cudaGraphExec_t gexec;
+  g3_bfs_opts gopts;
 };
 
 void g3_bfs_ws_free(g3_bfs_ws* ws) {
   if (!ws) return;
-  void* all[] = {ws->visited, ws->fa,  ws->fb,         ws->vis_save,  ws->qa,  ws->qb,
-                 ws->bins,    ws->pl,  ws->out_parent, ws->out_level, ws->ctrl, ws->goff,
-                 ws->bcount,  ws->bucket};
+  void* all[] = {ws->visited,    ws->fa,        ws->fb,   ws->vis_save, ws->qa,
+                 ws->qb,         ws->bins,      ws->pl,   ws->out_parent,
+                 ws->out_level,  ws->ctrl,      ws->goff, ws->bcount,   ws->bucket,
+                 ws->log};
   for (void* p : all)
     if (p) cudaFree(p);
   if (ws->h_ctrl) cudaFreeHost(ws->h_ctrl);
   for (int i = 0; i < 6; ++i)
     if (ws->ev[i]) cudaEventDestroy(ws->ev[i]);
+  if (ws->gexec) cudaGraphExecDestroy(ws->gexec);
   free(ws);
 }
 
@@ -176,12 +215,39 @@ __device__ __forceinline__ void reset_next(Ctrl* c) {
   c->conv_len = 0;
 }
 
+__device__ __forceinline__ int mode_of(const Ctrl* c) {
+  if (c->nf <= 0) return MODE_DONE;
+  if (c->dir == G3_DIR_TD) return c->fmt_queue ? MODE_TD_Q : MODE_TD_B;
+  return c->fmt_queue ? MODE_BU_Q : MODE_BU_B;
+}
+
+__device__ __forceinline__ void log_frontier(LevelLog* log, const Ctrl* c) {
+  if (c->level >= LOG_MAX) return;
+  LevelLog& r = log[c->level];
+  r.dir = c->dir;
+  r.t1 = c->t1;
+  r.t2 = c->t2;
+  r.t3 = c->t3;
+  r.nf = c->nf;
+  r.mf = c->mf;
+  r.nu = c->nu;
+  r.mu = c->mu;
+  r.examined = c->mf;
+  r.n_next = 0;
+  r.id_min = c->id_min;
+  r.id_max = c->id_max;
+  for (int k = 0; k < 4; ++k) {
+    r.hist[k] = c->hist[k];
+    r.mlp_out[k] = c->mlp_out[k];
+  }
+}
+
 // ------------------------------------------------------------------- init
 // Sets up F_0 = {root} (root_new < 0 or >= nb: no BFS-graph vertex). The
 // visited bitmap has been cleared on the stream before.
 __global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, int64_t nnz,
                          const int64_t* off, uint32_t* visited, int2* pl, int32_t* q, Ctrl* c,
-                         int t1, int t2, int t3) {
+                         LevelLog* log, int t1, int t2, int t3, int cap) {
   int32_t r = new_of_old ? new_of_old[root] : root;
   memset(c, 0, sizeof(Ctrl));
   reset_next(c);
@@ -189,10 +255,13 @@ __global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, in
   c->t2 = t2;
   c->t3 = t3;
   c->dir = G3_DIR_TD;  // Algorithm 2 starts top-down
+  c->fmt_queue = 1;
+  c->cap = cap;
   if (r < 0 || r >= nb) {
     c->nf = 0;
     c->nu = nb;
     c->mu = nnz;
+    c->mode = MODE_DONE;
     return;
   }
   visited[r >> 5] |= 1u << (r & 31);
@@ -207,7 +276,8 @@ __global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, in
   c->m_visited = d;
   c->nu = nb - 1;
   c->mu = nnz - d;
-  c->prev_nf = 0;
+  c->mode = MODE_TD_Q;
+  log_frontier(log, c);
 }
 
 // --------------------------------------------------------------- top-down
@@ -297,12 +367,23 @@ __device__ __forceinline__ void td_row_vec4(const TdArgs& a, WarpQueue& q, StatA
 #define GP_SHIFT 38
 #define GP_MASK ((1ull << GP_SHIFT) - 1ull)
 
+__device__ __forceinline__ TdArgs td_args(const int64_t* off, const int32_t* col,
+                                          uint32_t* visited, int2* pl, const Bufs& B, Ctrl* c) {
+  return TdArgs{off, col, visited, pl, c->level + 1, (c->qsel ? B.q[0] : B.q[1]), c};
+}
+
 // Thread per frontier vertex: degree < t1 expanded here, larger degrees
 // binned (warp / CTA / grid).
-__global__ void __launch_bounds__(256) td_front(TdArgs a, const int32_t* __restrict__ q,
-                                                int64_t qlen, int32_t* bins, int64_t* goff,
-                                                int64_t nb1) {
-  const int t1 = a.c->t1, t2 = a.c->t2, t3 = a.c->t3;
+__global__ void __launch_bounds__(256) td_front(const int64_t* __restrict__ off,
+                                                const int32_t* __restrict__ col,
+                                                uint32_t* visited, int2* pl, Bufs B,
+                                                int32_t* bins, int64_t* goff, int64_t nb1,
+                                                Ctrl* c) {
+  if (c->dir != G3_DIR_TD) return;
+  const TdArgs a = td_args(off, col, visited, pl, B, c);
+  const int32_t* __restrict__ q = (c->qsel ? B.q[1] : B.q[0]);
+  const int64_t qlen = c->nf;
+  const int t1 = c->t1, t2 = c->t2, t3 = c->t3;
   WQ_DECLARE(wq);
   StatAcc acc;
   acc.init();
@@ -311,14 +392,14 @@ __global__ void __launch_bounds__(256) td_front(TdArgs a, const int32_t* __restr
     const int64_t i = base + threadIdx.x;
     const bool act = i < qlen;
     int32_t v = act ? q[i] : 0;
-    int64_t b = act ? a.off[v] : 0, e = act ? a.off[v + 1] : 0, d = e - b;
+    int64_t b = act ? off[v] : 0, e = act ? off[v + 1] : 0, d = e - b;
     bool small = act && d < t1;
     int bin = !act || small ? -1 : (d < t2 ? 0 : (d < t3 ? 1 : 2));
     for (int k = 0; k < 2; ++k)
-      g3_warp_append(0xffffffffu, bin == k, v, bins + k * nb1, &a.c->bin_len[1 + k]);
+      g3_warp_append(0xffffffffu, bin == k, v, bins + k * nb1, &c->bin_len[1 + k]);
     if (bin == 2) {
       const unsigned long long old =
-          atomicAdd(&a.c->g_pack, (1ull << GP_SHIFT) | (unsigned long long)d);
+          atomicAdd(&c->g_pack, (1ull << GP_SHIFT) | (unsigned long long)d);
       const int64_t slot = (int64_t)(old >> GP_SHIFT);
       bins[2 * nb1 + slot] = v;
       goff[slot] = (int64_t)(old & GP_MASK);
@@ -327,40 +408,46 @@ __global__ void __launch_bounds__(256) td_front(TdArgs a, const int32_t* __restr
     const int maxc = __reduce_max_sync(0xffffffffu, cnt);
     for (int k = 0; k < maxc; ++k) {
       bool has = k < cnt;
-      int32_t w = has ? a.col[b + k] : 0;
+      int32_t w = has ? col[b + k] : 0;
       td_visit(a, wq, acc, has, w, v);
     }
   }
-  wq_flush(wq, a.qnext, &a.c->q_len);
-  acc.flush(a.c);
+  wq_flush(wq, a.qnext, &c->q_len);
+  acc.flush(c);
 }
 
 // The three bins in one launch: warp per warp-bin vertex, CTA per CTA-bin
 // vertex, and the grid bin as one flattened edge range split evenly over all
 // warps of the grid (Algorithm 4's even split, applied to every hub at once).
-__global__ void __launch_bounds__(256) td_bins(TdArgs a, const int32_t* __restrict__ bins,
-                                               const int64_t* __restrict__ goff, int64_t nb1) {
+__global__ void __launch_bounds__(256) td_bins(const int64_t* __restrict__ off,
+                                               const int32_t* __restrict__ col,
+                                               uint32_t* visited, int2* pl, Bufs B,
+                                               const int32_t* __restrict__ bins,
+                                               const int64_t* __restrict__ goff, int64_t nb1,
+                                               Ctrl* c) {
+  if (c->dir != G3_DIR_TD) return;
+  const TdArgs a = td_args(off, col, visited, pl, B, c);
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   WQ_DECLARE(wq);
   StatAcc acc;
   acc.init();
-  const int64_t len1 = (int64_t)a.c->bin_len[1];
+  const int64_t len1 = (int64_t)c->bin_len[1];
   for (int64_t i = gw; i < len1; i += nwarps) {
     int32_t v = bins[i];
-    int64_t b = a.off[v], e = a.off[v + 1];
+    int64_t b = off[v], e = off[v + 1];
     int64_t steps = (e - (b & ~3ll) + 127) / 128;
     td_row_vec4(a, wq, acc, v, b, e, lane, 32, steps);
   }
-  const int64_t len2 = (int64_t)a.c->bin_len[2];
+  const int64_t len2 = (int64_t)c->bin_len[2];
   for (int64_t i = blockIdx.x; i < len2; i += gridDim.x) {
     int32_t v = bins[nb1 + i];
-    int64_t b = a.off[v], e = a.off[v + 1];
+    int64_t b = off[v], e = off[v + 1];
     int64_t steps = (e - (b & ~3ll) + 4 * blockDim.x - 1) / (4 * blockDim.x);
     td_row_vec4(a, wq, acc, v, b, e, threadIdx.x, blockDim.x, steps);
   }
-  const unsigned long long gp = a.c->g_pack;
+  const unsigned long long gp = c->g_pack;
   const int64_t nh = (int64_t)(gp >> GP_SHIFT), E = (int64_t)(gp & GP_MASK);
   if (E > 0) {
     const int32_t* gbin = bins + 2 * nb1;
@@ -375,14 +462,14 @@ __global__ void __launch_bounds__(256) td_bins(TdArgs a, const int32_t* __restri
         if (act) {
           while (h + 1 < nh && goff[h + 1] <= j) ++h;
           v = gbin[h];
-          w = a.col[a.off[v] + (j - goff[h])];
+          w = col[off[v] + (j - goff[h])];
         }
         td_visit(a, wq, acc, act, w, v);
       }
     }
   }
-  wq_flush(wq, a.qnext, &a.c->q_len);
-  acc.flush(a.c);
+  wq_flush(wq, a.qnext, &c->q_len);
+  acc.flush(c);
 }
 
 // -------------------------------------------------------------- bottom-up
@@ -407,11 +494,13 @@ __device__ __forceinline__ int32_t bu_scan_rest(const int32_t* __restrict__ col,
 
 template <int REV>
 __global__ void __launch_bounds__(256) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
-                                               const uint32_t* __restrict__ fcur,
-                                               uint32_t* __restrict__ fnext,
-                                               const int64_t* __restrict__ off,
+                                               Bufs B, const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col, int2* pl,
-                                               int32_t lnext, Ctrl* c) {
+                                               Ctrl* c) {
+  if (c->dir != G3_DIR_BU) return;
+  const uint32_t* __restrict__ fcur = (c->fsel ? B.f[1] : B.f[0]);
+  uint32_t* __restrict__ fnext = (c->fsel ? B.f[0] : B.f[1]);
+  const int32_t lnext = c->level + 1;
   StatAcc acc;
   acc.init();
   const int lane = threadIdx.x & 31;
@@ -473,7 +562,21 @@ __global__ void __launch_bounds__(256) bu_pull(int32_t nb, int64_t nwords, uint3
 }
 
 // ------------------------------------------------------------ conversions
-__global__ void q_to_bitmap(const int32_t* __restrict__ q, int64_t len, uint32_t* bm) {
+// queue -> bitmap before a bottom-up level that follows a top-down one:
+// clear f[fsel], then set the bit of every queued vertex.
+__global__ void bm_clear(Bufs B, int64_t nwords, const Ctrl* c) {
+  if (c->dir != G3_DIR_BU || !c->fmt_queue) return;
+  uint32_t* f = (c->fsel ? B.f[1] : B.f[0]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
+       i += (int64_t)gridDim.x * blockDim.x)
+    f[i] = 0u;
+}
+
+__global__ void q_to_bitmap(Bufs B, const Ctrl* c) {
+  if (c->dir != G3_DIR_BU || !c->fmt_queue) return;
+  const int32_t* __restrict__ q = (c->qsel ? B.q[1] : B.q[0]);
+  uint32_t* bm = (c->fsel ? B.f[1] : B.f[0]);
+  const int64_t len = c->nf;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x) {
     int32_t v = q[i];
@@ -481,15 +584,19 @@ __global__ void q_to_bitmap(const int32_t* __restrict__ q, int64_t len, uint32_t
   }
 }
 
-__global__ void bitmap_to_q(const uint32_t* __restrict__ bm, int64_t nwords, int32_t* q,
-                            unsigned long long* len) {
+// bitmap -> queue before a top-down level that follows a bottom-up one.
+__global__ void bitmap_to_q(Bufs B, int64_t nwords, Ctrl* c) {
+  if (c->dir != G3_DIR_TD || c->fmt_queue) return;
+  const uint32_t* __restrict__ bm = (c->fsel ? B.f[1] : B.f[0]);
+  int32_t* q = (c->qsel ? B.q[1] : B.q[0]);
+  unsigned long long* len = &c->conv_len;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
        base < nwords; base += nwarps * 32) {
     const int64_t w = base + lane;
     uint32_t bits = w < nwords ? bm[w] : 0u;
-    unsigned c = __popc(bits), inc = c;
+    unsigned cnt = __popc(bits), inc = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       unsigned t = __shfl_up_sync(0xffffffffu, inc, o);
@@ -500,7 +607,7 @@ __global__ void bitmap_to_q(const uint32_t* __restrict__ bm, int64_t nwords, int
     unsigned long long start = 0;
     if (lane == 31) start = atomicAdd(len, (unsigned long long)total);
     start = __shfl_sync(0xffffffffu, start, 31);
-    unsigned long long p = start + inc - c;
+    unsigned long long p = start + inc - cnt;
     while (bits) {
       int b = __ffs(bits) - 1;
       q[p++] = (int32_t)(w * 32 + b);
@@ -550,52 +657,75 @@ __device__ __forceinline__ int clamp_thr(float lg, int lo, int hi) {
   return 1 << (int)x;
 }
 
-// After the expansion of level L: promote the produced frontier to F_{L+1},
-// update the visited totals, decide its direction and clear the accumulators
-// for the next expansion.
-__global__ void bfs_control(Ctrl* c, int32_t nb, int64_t nnz, int controller, int alpha,
-                            int beta, const float* __restrict__ mlp, int t1d, int t2d, int t3d,
-                            int was_td) {
+struct CtrlArgs {
+  int32_t nb;
+  int64_t nnz;
+  int controller, alpha, beta;
+  const float* mlp;
+  int t1, t2, t3;
+  LevelLog* log;
+  int graph_mode;
+  cudaGraphConditionalHandle h_loop;
+};
+
+// After the expansion of level L: record where the produced frontier lives,
+// promote it to F_{L+1}, update the visited totals, decide its direction,
+// log it and clear the accumulators for the next expansion. In graph mode it
+// also ends the loop (done, or the launch's level cap reached).
+__global__ void bfs_control(Ctrl* c, CtrlArgs A) {
   __shared__ float feat[12];
-  __shared__ int decide;
+  __shared__ int decide, active;
   const int lane = threadIdx.x;
   if (lane == 0) {
-    const int prev_dir = c->dir;
-    const long long prev_nf = c->nf;
-    const long long nf = was_td ? (long long)c->q_len : (long long)c->nx_nf;
-    c->exam_prev = (long long)c->nx_exam;
-    c->nf = nf;
-    c->mf = (long long)c->nx_mf;
-    for (int k = 0; k < 4; ++k) c->hist[k] = (long long)c->nx_hist[k];
-    c->id_min = nf ? (int)c->nx_min : 0;
-    c->id_max = nf ? (int)c->nx_max : 0;
-    c->n_visited += nf;
-    c->m_visited += c->mf;
-    c->nu = nb - c->n_visited;
-    c->mu = nnz - c->m_visited;
-    c->level += 1;
-    c->prev_nf = prev_nf;
-    int d;
-    if (controller == G3_CTRL_TOPDOWN) {
-      d = G3_DIR_TD;
-    } else if (controller == G3_CTRL_BOTTOMUP) {
-      d = G3_DIR_BU;
-    } else if (prev_dir == G3_DIR_TD) {
-      d = (c->mf * (long long)alpha > c->mu) ? G3_DIR_BU : G3_DIR_TD;
-    } else {
-      d = (nf < prev_nf && nf * (long long)beta < (long long)nb) ? G3_DIR_TD : G3_DIR_BU;
+    active = c->mode != MODE_DONE && c->nf > 0;
+    if (active) {
+      const int prev_dir = c->dir;
+      const bool was_td = prev_dir == G3_DIR_TD;
+      const long long prev_nf = c->nf;
+      const long long nf = was_td ? (long long)c->q_len : (long long)c->nx_nf;
+      if (was_td) {
+        c->qsel ^= 1;
+        c->fmt_queue = 1;
+      } else {
+        c->fsel ^= 1;
+        c->fmt_queue = 0;
+      }
+      if (c->level < LOG_MAX) {
+        A.log[c->level].n_next = nf;
+        if (!was_td) A.log[c->level].examined = (long long)c->nx_exam;
+      }
+      c->nf = nf;
+      c->mf = (long long)c->nx_mf;
+      for (int k = 0; k < 4; ++k) c->hist[k] = (long long)c->nx_hist[k];
+      c->id_min = nf ? (int)c->nx_min : 0;
+      c->id_max = nf ? (int)c->nx_max : 0;
+      c->n_visited += nf;
+      c->m_visited += c->mf;
+      c->nu = A.nb - c->n_visited;
+      c->mu = A.nnz - c->m_visited;
+      c->level += 1;
+      int d;
+      if (A.controller == G3_CTRL_TOPDOWN) {
+        d = G3_DIR_TD;
+      } else if (A.controller == G3_CTRL_BOTTOMUP) {
+        d = G3_DIR_BU;
+      } else if (prev_dir == G3_DIR_TD) {
+        d = (c->mf * (long long)A.alpha > c->mu) ? G3_DIR_BU : G3_DIR_TD;
+      } else {
+        d = (nf < prev_nf && nf * (long long)A.beta < (long long)A.nb) ? G3_DIR_TD : G3_DIR_BU;
+      }
+      c->t1 = A.t1;
+      c->t2 = A.t2;
+      c->t3 = A.t3;
+      decide = d;
+      if (A.controller == G3_CTRL_LEARNED) mlp_features(c, A.nb, prev_dir, feat);
+      reset_next(c);
     }
-    c->t1 = t1d;
-    c->t2 = t2d;
-    c->t3 = t3d;
-    decide = d;
-    if (controller == G3_CTRL_LEARNED) mlp_features(c, nb, prev_dir, feat);
-    reset_next(c);
   }
   __syncwarp();
-  if (controller == G3_CTRL_LEARNED) {
+  if (active && A.controller == G3_CTRL_LEARNED) {
     float out[4];
-    mlp_eval_warp(mlp, feat, out);
+    mlp_eval_warp(A.mlp, feat, out);
     if (lane == 0) {
       for (int k = 0; k < 4; ++k) c->mlp_out[k] = out[k];
       decide = out[0] < 0.f ? G3_DIR_BU : G3_DIR_TD;
@@ -609,7 +739,22 @@ __global__ void bfs_control(Ctrl* c, int32_t nb, int64_t nnz, int controller, in
     }
     __syncwarp();
   }
-  if (lane == 0) c->dir = decide;
+  if (lane == 0) {
+    if (active) {
+      c->dir = decide;
+      c->mode = mode_of(c);
+      if (c->mode != MODE_DONE) log_frontier(A.log, c);
+    }
+    if (A.graph_mode) {
+      const bool go = c->mode != MODE_DONE && c->level < c->cap;
+      cudaGraphSetConditional(A.h_loop, go ? 1u : 0u);
+    }
+  }
+}
+
+// Graph mode: picks the SWITCH body of the level about to run.
+__global__ void bfs_select(const Ctrl* c, cudaGraphConditionalHandle h_mode) {
+  cudaGraphSetConditional(h_mode, (unsigned)c->mode);
 }
 
 // --------------------------------------------------------- output mapping
@@ -729,19 +874,19 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
   ws->nb = g->n_bfs;
   ws->nwords = ((int64_t)g->n_bfs + 31) / 32;
   const size_t nb1 = (size_t)g->n_bfs + 4, nw = (size_t)ws->nwords + 4, n1 = (size_t)g->n + 4;
+  const size_t nbk = (size_t)(g->n >> TR_SHIFT) + 2;
   struct {
     void** p;
     size_t bytes;
   } req[] = {
-      {(void**)&ws->visited, nw * 4},     {(void**)&ws->fa, nw * 4},
-      {(void**)&ws->fb, nw * 4},          {(void**)&ws->vis_save, nw * 4},
-      {(void**)&ws->qa, nb1 * 4},         {(void**)&ws->qb, nb1 * 4},
-      {(void**)&ws->bins, nb1 * 4 * 3},   {(void**)&ws->pl, nb1 * 8},
-      {(void**)&ws->goff, nb1 * 8},
-      {(void**)&ws->out_parent, n1 * 4},  {(void**)&ws->out_level, n1 * 4},
-      {(void**)&ws->bcount, ((size_t)(g->n >> TR_SHIFT) + 2) * 4},
-      {(void**)&ws->bucket, ((size_t)(g->n >> TR_SHIFT) + 2) * TR_W * 8},
-      {(void**)&ws->ctrl, sizeof(Ctrl)},
+      {(void**)&ws->visited, nw * 4},        {(void**)&ws->fa, nw * 4},
+      {(void**)&ws->fb, nw * 4},             {(void**)&ws->vis_save, nw * 4},
+      {(void**)&ws->qa, nb1 * 4},            {(void**)&ws->qb, nb1 * 4},
+      {(void**)&ws->bins, nb1 * 4 * 3},      {(void**)&ws->pl, nb1 * 8},
+      {(void**)&ws->goff, nb1 * 8},          {(void**)&ws->out_parent, n1 * 4},
+      {(void**)&ws->out_level, n1 * 4},      {(void**)&ws->bcount, nbk * 4},
+      {(void**)&ws->bucket, nbk * TR_W * 8}, {(void**)&ws->ctrl, sizeof(Ctrl)},
+      {(void**)&ws->log, sizeof(LevelLog) * LOG_MAX},
   };
   for (auto& r : req) {
     cudaError_t e = cudaMalloc(r.p, r.bytes);
@@ -792,56 +937,176 @@ static inline int cap_grid(int64_t items, int per_block, int resident) {
   return b < 1 ? 1 : (int)b;
 }
 
-struct Level {
+// Everything the expansion kernels of one search take as arguments.
+struct Launch {
   g3_graph* g;
   g3_bfs_ws* ws;
   const g3_bfs_opts* o;
-  cudaStream_t s;
-  uint32_t *fcur, *fnext;
-  int32_t *qcur, *qnext;
-  bool fmt_queue;
+  Bufs B;
+  int64_t nb1;
 };
 
-// Top-down expansion of F_L (queue qcur of length nf) into qnext. Records
-// event `ev_mid` after the format conversion when given.
-static g3_status run_td(Level& S, int64_t nf, int32_t lnext, cudaEvent_t ev_mid) {
+static CtrlArgs ctrl_args(const Launch& S, int graph_mode, cudaGraphConditionalHandle h_loop) {
+  return CtrlArgs{S.ws->nb,     S.g->nnz,     S.o->controller, S.o->alpha,
+                  S.o->beta,    S.o->mlp_params, S.o->t1,     S.o->t2,
+                  S.o->t3,      S.ws->log,    graph_mode,      h_loop};
+}
+
+// Host-driven launch of the kernels of one level of the given mode. Every
+// kernel checks the controller record itself, so the set is the same as in
+// the graph's SWITCH body for that mode. Records ev_mid after the format
+// conversion when given.
+static g3_status launch_level(const Launch& S, int mode, int64_t nf, cudaEvent_t ev_mid,
+                              cudaStream_t s) {
   g3_bfs_ws* ws = S.ws;
-  cudaStream_t s = S.s;
-  if (!S.fmt_queue) {
-    bitmap_to_q<<<cap_grid(ws->nwords, 256, ws->grid_conv), 256, 0, s>>>(
-        S.fcur, ws->nwords, S.qcur, &ws->ctrl->conv_len);
+  Ctrl* c = ws->ctrl;
+  if (mode == MODE_TD_B) {
+    bitmap_to_q<<<cap_grid(ws->nwords, 256, ws->grid_conv), 256, 0, s>>>(S.B, ws->nwords, c);
+    G3_CHECK_LAUNCH();
+  } else if (mode == MODE_BU_Q) {
+    bm_clear<<<g3_grid_for(ws->nwords, 256), 256, 0, s>>>(S.B, ws->nwords, c);
+    G3_CHECK_LAUNCH();
+    q_to_bitmap<<<g3_grid_for(nf, 256), 256, 0, s>>>(S.B, c);
     G3_CHECK_LAUNCH();
   }
   if (ev_mid) G3_TRY_CUDA(cudaEventRecord(ev_mid, s));
-  TdArgs a{S.g->off, S.g->col, ws->visited, ws->pl, lnext, S.qnext, ws->ctrl};
-  const int64_t nb1 = ws->nb + 4;
-  td_front<<<cap_grid(nf, 256, ws->grid_front), 256, 0, s>>>(a, S.qcur, nf, ws->bins, ws->goff,
-                                                             nb1);
-  G3_CHECK_LAUNCH();
-  td_bins<<<ws->grid_bins, 256, 0, s>>>(a, ws->bins, ws->goff, nb1);
-  G3_CHECK_LAUNCH();
+  if (mode == MODE_TD_Q || mode == MODE_TD_B) {
+    td_front<<<cap_grid(nf, 256, ws->grid_front), 256, 0, s>>>(
+        S.g->off, S.g->col, ws->visited, ws->pl, S.B, ws->bins, ws->goff, S.nb1, c);
+    G3_CHECK_LAUNCH();
+    td_bins<<<ws->grid_bins, 256, 0, s>>>(S.g->off, S.g->col, ws->visited, ws->pl, S.B,
+                                          ws->bins, ws->goff, S.nb1, c);
+    G3_CHECK_LAUNCH();
+  } else {
+    const int grid = cap_grid(ws->nwords, 16, ws->grid_bu);
+    if (S.o->bu_reverse)
+      bu_pull<1><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.B, S.g->off, S.g->col,
+                                      ws->pl, c);
+    else
+      bu_pull<0><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.B, S.g->off, S.g->col,
+                                      ws->pl, c);
+    G3_CHECK_LAUNCH();
+  }
   return G3_OK;
 }
 
-// Bottom-up expansion of F_L (bitmap) into fnext.
-static g3_status run_bu(Level& S, int64_t nf, int32_t lnext, cudaEvent_t ev_mid) {
-  g3_bfs_ws* ws = S.ws;
-  cudaStream_t s = S.s;
-  if (S.fmt_queue) {
-    G3_TRY_CUDA(cudaMemsetAsync(S.fcur, 0, (size_t)ws->nwords * 4, s));
-    q_to_bitmap<<<g3_grid_for(nf, 256), 256, 0, s>>>(S.qcur, nf, S.fcur);
-    G3_CHECK_LAUNCH();
-  }
-  if (ev_mid) G3_TRY_CUDA(cudaEventRecord(ev_mid, s));
-  const int grid = cap_grid(ws->nwords, 16, ws->grid_bu);
-  if (S.o->bu_reverse)
-    bu_pull<1><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.fcur, S.fnext, S.g->off,
-                                    S.g->col, ws->pl, lnext, ws->ctrl);
-  else
-    bu_pull<0><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.fcur, S.fnext, S.g->off,
-                                    S.g->col, ws->pl, lnext, ws->ctrl);
-  G3_CHECK_LAUNCH();
+// ------------------------------------------------------------ graph mode
+static g3_status add_kernel(cudaGraph_t gr, cudaGraphNode_t* node, cudaGraphNode_t* dep,
+                            void* func, int grid, int block, void** args) {
+  cudaKernelNodeParams p;
+  memset(&p, 0, sizeof(p));
+  p.func = func;
+  p.gridDim = dim3(grid);
+  p.blockDim = dim3(block);
+  p.kernelParams = args;
+  G3_TRY_CUDA(cudaGraphAddKernelNode(node, gr, dep, dep ? 1 : 0, &p));
   return G3_OK;
+}
+
+// Zero-filled storage for cudaGraphNodeParams (its union has no usable
+// default constructor).
+struct NodeParams {
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  NodeParams() { memset(raw, 0, sizeof(raw)); }
+  cudaGraphNodeParams& get() { return *reinterpret_cast<cudaGraphNodeParams*>(raw); }
+};
+
+static bool same_opts(const g3_bfs_opts& a, const g3_bfs_opts& b) {
+  return a.controller == b.controller && a.alpha == b.alpha && a.beta == b.beta &&
+         a.t1 == b.t1 && a.t2 == b.t2 && a.t3 == b.t3 && a.bu_reverse == b.bu_reverse &&
+         a.mlp_params == b.mlp_params;
+}
+
+// Builds the level loop: WHILE(h_loop) { bfs_select -> SWITCH(h_mode) {
+// TD_Q, TD_B, BU_B, BU_Q } -> bfs_control }. Kernel arguments are baked in;
+// everything that changes per search lives in the controller record.
+static g3_status build_graph(Launch& S) {
+  g3_bfs_ws* ws = S.ws;
+  cudaGraph_t top = nullptr;
+  g3_status st = G3_OK;
+  G3_TRY_CUDA(cudaGraphCreate(&top, 0));
+  cudaGraphConditionalHandle h_loop, h_mode;
+  cudaGraphNode_t wnode, sel, sw, ctl, n0, n1, n2;
+  cudaGraph_t body, br[4];
+  Ctrl* c = ws->ctrl;
+  int64_t nwords = ws->nwords;
+  int32_t nb = ws->nb;
+  int gconv = ws->grid_conv, gfront = ws->grid_front, gbins = ws->grid_bins;
+  int gbu = cap_grid(ws->nwords, 16, ws->grid_bu);
+  int gclear = g3_grid_for(ws->nwords, 256), gq2b = g3_grid_for(ws->nb, 256);
+  const int64_t* off = S.g->off;
+  const int32_t* col = S.g->col;
+  void* bu_fn = S.o->bu_reverse ? (void*)bu_pull<1> : (void*)bu_pull<0>;
+  void* a_conv[] = {&S.B, &nwords, &c};
+  void* a_clear[] = {&S.B, &nwords, &c};
+  void* a_q2b[] = {&S.B, &c};
+  void* a_td[] = {&off, &col, &ws->visited, &ws->pl, &S.B, &ws->bins, &ws->goff, &S.nb1, &c};
+  void* a_bu[] = {&nb, &nwords, &ws->visited, &S.B, &off, &col, &ws->pl, &c};
+  CtrlArgs ca;
+  void* a_ctl[] = {&c, &ca};
+  void* a_sel[] = {&c, &h_mode};
+  do {
+    if (cudaGraphConditionalHandleCreate(&h_loop, top, 1, cudaGraphCondAssignDefault) !=
+        cudaSuccess) { st = G3_ECUDA; break; }
+    NodeParams wbuf;
+    cudaGraphNodeParams& wp = wbuf.get();
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    if (cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp) != cudaSuccess) {
+      st = G3_ECUDA;
+      break;
+    }
+    body = wp.conditional.phGraph_out[0];
+    if (cudaGraphConditionalHandleCreate(&h_mode, body, 0, 0) != cudaSuccess) {
+      st = G3_ECUDA;
+      break;
+    }
+    if ((st = add_kernel(body, &sel, nullptr, (void*)bfs_select, 1, 1, a_sel)) != G3_OK) break;
+    NodeParams sbuf;
+    cudaGraphNodeParams& sp = sbuf.get();
+    sp.type = cudaGraphNodeTypeConditional;
+    sp.conditional.handle = h_mode;
+    sp.conditional.type = cudaGraphCondTypeSwitch;
+    sp.conditional.size = 4;
+    if (cudaGraphAddNode(&sw, body, &sel, nullptr, 1, &sp) != cudaSuccess) {
+      st = G3_ECUDA;
+      break;
+    }
+    for (int k = 0; k < 4; ++k) br[k] = sp.conditional.phGraph_out[k];
+    // MODE_TD_Q
+    if ((st = add_kernel(br[MODE_TD_Q], &n0, nullptr, (void*)td_front, gfront, 256, a_td))) break;
+    if ((st = add_kernel(br[MODE_TD_Q], &n1, &n0, (void*)td_bins, gbins, 256, a_td))) break;
+    // MODE_TD_B
+    if ((st = add_kernel(br[MODE_TD_B], &n0, nullptr, (void*)bitmap_to_q, gconv, 256, a_conv)))
+      break;
+    if ((st = add_kernel(br[MODE_TD_B], &n1, &n0, (void*)td_front, gfront, 256, a_td))) break;
+    if ((st = add_kernel(br[MODE_TD_B], &n2, &n1, (void*)td_bins, gbins, 256, a_td))) break;
+    // MODE_BU_B
+    if ((st = add_kernel(br[MODE_BU_B], &n0, nullptr, bu_fn, gbu, 256, a_bu))) break;
+    // MODE_BU_Q
+    if ((st = add_kernel(br[MODE_BU_Q], &n0, nullptr, (void*)bm_clear, gclear, 256, a_clear)))
+      break;
+    if ((st = add_kernel(br[MODE_BU_Q], &n1, &n0, (void*)q_to_bitmap, gq2b, 256, a_q2b))) break;
+    if ((st = add_kernel(br[MODE_BU_Q], &n2, &n1, bu_fn, gbu, 256, a_bu))) break;
+    ca = ctrl_args(S, 1, h_loop);
+    if ((st = add_kernel(body, &ctl, &sw, (void*)bfs_control, 1, 32, a_ctl))) break;
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, top, 0) != cudaSuccess) {
+      st = G3_ECUDA;
+      break;
+    }
+    if (ws->gexec) cudaGraphExecDestroy(ws->gexec);
+    ws->gexec = ex;
+    ws->gopts = *S.o;
+  } while (0);
+  if (st != G3_OK) {
+    cudaError_t e = cudaGetLastError();
+    g3_set_error("g3_bfs: building the level-loop graph failed: %s", cudaGetErrorString(e));
+  }
+  cudaGraphDestroy(top);
+  return st;
 }
 
 // Candidate top-down bin thresholds timed in record_both mode.
@@ -852,9 +1117,8 @@ static const int kSweep[5][3] = {
 // bottom-up one from the same state, restoring the visited bitmap and the
 // controller record after each trial. Fills r (times, best thresholds); the
 // state afterwards is the state before the trials.
-static g3_status record_trials(Level& S, int64_t nf, int32_t L, g3_level_stats* r) {
+static g3_status record_trials(const Launch& S, int64_t nf, g3_level_stats* r, cudaStream_t s) {
   g3_bfs_ws* ws = S.ws;
-  cudaStream_t s = S.s;
   const size_t vbytes = (size_t)ws->nwords * 4;
   G3_TRY_CUDA(cudaMemcpyAsync(ws->vis_save, ws->visited, vbytes, cudaMemcpyDeviceToDevice, s));
   Ctrl save;
@@ -864,17 +1128,17 @@ static g3_status record_trials(Level& S, int64_t nf, int32_t L, g3_level_stats* 
   for (int k = 0; k < 6; ++k) {
     Ctrl c = save;
     const bool td = k < 5;
+    c.dir = td ? G3_DIR_TD : G3_DIR_BU;
     if (td) {
       c.t1 = kSweep[k][0];
       c.t2 = kSweep[k][1];
       c.t3 = kSweep[k][2];
     }
+    const int mode = td ? (c.fmt_queue ? MODE_TD_Q : MODE_TD_B)
+                        : (c.fmt_queue ? MODE_BU_Q : MODE_BU_B);
     G3_TRY_CUDA(cudaMemcpyAsync(ws->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     G3_TRY_CUDA(cudaEventRecord(ws->ev[4], s));
-    if (td)
-      G3_TRY(run_td(S, nf, L + 1, nullptr));
-    else
-      G3_TRY(run_bu(S, nf, L + 1, nullptr));
+    G3_TRY(launch_level(S, mode, nf, nullptr, s));
     G3_TRY_CUDA(cudaEventRecord(ws->ev[5], s));
     G3_TRY_CUDA(cudaMemcpyAsync(ws->visited, ws->vis_save, vbytes, cudaMemcpyDeviceToDevice, s));
     G3_TRY_CUDA(cudaStreamSynchronize(s));
@@ -894,81 +1158,70 @@ static g3_status record_trials(Level& S, int64_t nf, int32_t L, g3_level_stats* 
   return G3_OK;
 }
 
+static void fill_record(g3_level_stats* r, int32_t L, const LevelLog& e) {
+  r->level = L;
+  r->dir = e.dir;
+  r->n_f = e.nf;
+  r->m_f = e.mf;
+  r->n_u = e.nu;
+  r->m_u = e.mu;
+  r->examined = e.examined;
+  r->n_next = e.n_next;
+  r->id_min = e.id_min;
+  r->id_max = e.id_max;
+  for (int k = 0; k < 4; ++k) {
+    r->hist[k] = e.hist[k];
+    r->mlp_out[k] = e.mlp_out[k];
+  }
+  r->t1 = e.t1;
+  r->t2 = e.t2;
+  r->t3 = e.t3;
+}
+
 static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32_t* parent,
                           int32_t* level, g3_level_stats* stats, int32_t max_stats,
                           int32_t* n_levels, cudaStream_t s) {
   if (!g->ws) G3_TRY(ws_create(g, &g->ws));
   g3_bfs_ws* ws = g->ws;
   const int32_t nb = ws->nb;
-  const int64_t nnz = g->nnz;
   Ctrl* h = ws->h_ctrl;
+  Launch S{g, ws, o, Bufs{{ws->qa, ws->qb}, {ws->fa, ws->fb}}, (int64_t)ws->nb + 4};
+  const bool host_driven = o->timing || o->record_both;
+  if (stats && max_stats > 0) memset(stats, 0, sizeof(g3_level_stats) * (size_t)max_stats);
 
   G3_TRY_CUDA(cudaMemsetAsync(ws->visited, 0, (size_t)(ws->nwords + 1) * 4, s));
-  bfs_root<<<1, 1, 0, s>>>(g->relabelled ? g->new_of_old : nullptr, root, nb, nnz, g->off,
-                           ws->visited, ws->pl, ws->qa, ws->ctrl, o->t1, o->t2, o->t3);
+  bfs_root<<<1, 1, 0, s>>>(g->relabelled ? g->new_of_old : nullptr, root, nb, g->nnz, g->off,
+                           ws->visited, ws->pl, ws->qa, ws->ctrl, ws->log, o->t1, o->t2, o->t3,
+                           host_driven ? 0x7fffffff : GRAPH_LEVEL_CAP);
   G3_CHECK_LAUNCH();
 
-  Level S{g, ws, o, s, ws->fa, ws->fb, ws->qa, ws->qb, true};
-  int nrec = 0;
-  for (int32_t L = 0;; ++L) {
+  if (!host_driven) {
+    if (!ws->gexec || !same_opts(ws->gopts, *o)) G3_TRY(build_graph(S));
+    G3_TRY_CUDA(cudaGraphLaunch(ws->gexec, s));
+  }
+  // Host-driven levels: everything in host-driven mode, and what a graph
+  // launch left over (searches deeper than its level cap).
+  for (;;) {
     G3_TRY_CUDA(cudaMemcpyAsync(h, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     G3_TRY_CUDA(cudaStreamSynchronize(s));
-    if (L > 0 && stats && nrec >= 1 && nrec - 1 < max_stats) {
-      // close the previous record: examined edges, next size, times
-      g3_level_stats& r = stats[nrec - 1];
-      r.n_next = h->nf;
-      if (r.dir == G3_DIR_BU) r.examined = h->exam_prev;
-      if (o->timing) {
-        cudaEventElapsedTime(&r.ms, ws->ev[0], ws->ev[3]);
-        cudaEventElapsedTime(&r.ms_expand, ws->ev[1], ws->ev[2]);
-      }
+    const int32_t L = h->level;
+    if (host_driven && o->timing && L > 0 && stats && L - 1 < max_stats) {
+      cudaEventElapsedTime(&stats[L - 1].ms, ws->ev[0], ws->ev[3]);
+      cudaEventElapsedTime(&stats[L - 1].ms_expand, ws->ev[1], ws->ev[2]);
     }
-    const int64_t nf = h->nf;
-    if (nf <= 0) break;
-    const int dir = h->dir;
-    g3_level_stats* rec = (stats && nrec < max_stats) ? &stats[nrec] : nullptr;
-    if (rec) {
-      memset(rec, 0, sizeof(*rec));
-      rec->level = L;
-      rec->dir = dir;
-      rec->n_f = h->nf;
-      rec->m_f = h->mf;
-      rec->n_u = h->nu;
-      rec->m_u = h->mu;
-      rec->examined = h->mf;
-      rec->id_min = h->id_min;
-      rec->id_max = h->id_max;
-      for (int k = 0; k < 4; ++k) rec->hist[k] = h->hist[k];
-      rec->t1 = h->t1;
-      rec->t2 = h->t2;
-      rec->t3 = h->t3;
-      for (int k = 0; k < 4; ++k) rec->mlp_out[k] = h->mlp_out[k];
-    }
-    ++nrec;
-    if (o->record_both && rec) G3_TRY(record_trials(S, nf, L, rec));
+    if (h->mode == MODE_DONE) break;
+    const int mode = h->mode;
+    if (o->record_both && stats && L < max_stats)
+      G3_TRY(record_trials(S, h->nf, &stats[L], s));
     if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[0], s));
-    if (dir == G3_DIR_TD) {
-      G3_TRY(run_td(S, nf, L + 1, o->timing ? ws->ev[1] : nullptr));
-    } else {
-      G3_TRY(run_bu(S, nf, L + 1, o->timing ? ws->ev[1] : nullptr));
-    }
+    G3_TRY(launch_level(S, mode, h->nf, o->timing ? ws->ev[1] : nullptr, s));
     if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[2], s));
-    bfs_control<<<1, 32, 0, s>>>(ws->ctrl, nb, nnz, o->controller, o->alpha, o->beta,
-                                 o->mlp_params, o->t1, o->t2, o->t3, dir == G3_DIR_TD);
+    CtrlArgs ca = ctrl_args(S, 0, 0);
+    bfs_control<<<1, 32, 0, s>>>(ws->ctrl, ca);
     G3_CHECK_LAUNCH();
     if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[3], s));
-    if (dir == G3_DIR_TD) {
-      int32_t* t = S.qcur;
-      S.qcur = S.qnext;
-      S.qnext = t;
-      S.fmt_queue = true;
-    } else {
-      uint32_t* t = S.fcur;
-      S.fcur = S.fnext;
-      S.fnext = t;
-      S.fmt_queue = false;
-    }
   }
+  const int32_t nrec = h->level;  // non-empty frontiers F_0 .. F_{nrec-1}
   if (n_levels) *n_levels = nrec;
 
   // outputs in original IDs
@@ -994,7 +1247,25 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
     G3_TRY_CUDA(cudaMemcpyAsync(parent, op, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
   if (!dev_l)
     G3_TRY_CUDA(cudaMemcpyAsync(level, ol, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
-  G3_TRY_CUDA(cudaStreamSynchronize(s));
+  // per-level records from the device log
+  const int32_t nlog = nrec < LOG_MAX ? nrec : LOG_MAX;
+  const int32_t ncopy = stats ? (nlog < max_stats ? nlog : max_stats) : 0;
+  LevelLog* hl = nullptr;
+  if (ncopy > 0) {
+    hl = (LevelLog*)malloc(sizeof(LevelLog) * (size_t)ncopy);
+    if (!hl) return G3_ENOMEM;
+    cudaError_t e =
+        cudaMemcpyAsync(hl, ws->log, sizeof(LevelLog) * (size_t)ncopy, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) {
+      free(hl);
+      G3_TRY_CUDA(e);
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess)
+    for (int32_t L = 0; L < ncopy; ++L) fill_record(&stats[L], L, hl[L]);
+  free(hl);
+  G3_TRY_CUDA(e);
   return G3_OK;
 }
 

@@ -260,3 +260,33 @@ def test_record_both_mode_keeps_results_exact(kron16):
         assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
         assert st and all(a["t_td_ms"] > 0 and a["t_bu_ms"] > 0 for a in st)
         assert all((a["best_t1"], a["best_t2"], a["best_t3"]) in sweep for a in st)
+
+
+def test_graph_mode_equals_host_driven_mode(kron16):
+    # default searches run the level loop as one CUDA graph; per-level timing
+    # switches to the host-driven loop. Both must give the same levels, the
+    # same per-level statistics and the same direction sequence.
+    K = kron16
+    for root in K["roots"][:16].tolist():
+        _, lg, sg = run_bfs(K["g"], root, K["n"], max_stats=64)
+        _, lh, sh = run_bfs(K["g"], root, K["n"], max_stats=64, timing=1)
+        assert np.array_equal(lg, lh)
+        keys = ["level", "dir", "n_f", "m_f", "n_u", "m_u", "examined", "n_next", "id_min",
+                "id_max", "hist"]
+        assert [[a[k] for k in keys] for a in sg] == [[a[k] for k in keys] for a in sh]
+        assert all(a["ms"] > 0 and a["ms_expand"] > 0 for a in sh)
+
+
+def test_deep_graph_beyond_graph_level_cap():
+    # a path longer than the 4096 levels one graph launch may run: the search
+    # continues on the host-driven loop and stays exact
+    n = 5000
+    src, dst = path_graph(n)
+    off, col = oracle.build_csr(src, dst, n)
+    for relabel in (True, False):
+        g = gpu_pipeline(src, dst, n, relabel)
+        parent, level, st = run_bfs(g, 0, n, max_stats=8)
+        assert level.tolist() == list(range(n))
+        assert oracle.validate(off, col, 0, parent, level) == 0
+        assert len(st) == 8 and st[7]["n_f"] == 1
+        g.free()
