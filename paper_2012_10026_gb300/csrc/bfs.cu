@@ -98,8 +98,10 @@ struct g3_bfs_ws {
   int32_t *qa, *qb, *bins;  // bins: 3 segments of nb entries (warp, CTA, grid)
   int64_t* goff;            // edge offset of each grid-bin vertex
   int2* pl;                 // (parent, level) per BFS-graph vertex
+  int2* nplus;              // (last row entry or -1, degree): Algorithm 6's neighbors+
   int32_t *out_parent, *out_level;  // staging for host outputs (n entries)
-  unsigned* bcount;                 // translation: entries per window
+  unsigned *wstart, *wend;          // translation: each window's slot range
+  unsigned* slot;                   // translation: each vertex's slot in its window
   unsigned long long* bucket;       // translation: TR_W slots per window
   int64_t nbuckets;
   Ctrl* ctrl;
@@ -117,7 +119,8 @@ void g3_bfs_ws_free(g3_bfs_ws* ws) {
   if (!ws) return;
   void* all[] = {ws->visited,    ws->fa,        ws->fb,   ws->vis_save, ws->qa,
                  ws->qb,         ws->bins,      ws->pl,   ws->out_parent,
-                 ws->out_level,  ws->ctrl,      ws->goff, ws->bcount,   ws->bucket,
+                 ws->out_level,  ws->ctrl,      ws->goff, ws->wstart,   ws->bucket, ws->slot,
+                 ws->wend,       ws->nplus,
                  ws->log};
   for (void* p : all)
     if (p) cudaFree(p);
@@ -493,9 +496,10 @@ __device__ __forceinline__ int32_t bu_scan_rest(const int32_t* __restrict__ col,
 }
 
 template <int REV>
-__global__ void __launch_bounds__(256) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
+__global__ void __launch_bounds__(256, 5) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
                                                Bufs B, const int64_t* __restrict__ off,
-                                               const int32_t* __restrict__ col, int2* pl,
+                                               const int32_t* __restrict__ col,
+                                               const int2* __restrict__ nplus, int2* pl,
                                                Ctrl* c) {
   if (c->dir != G3_DIR_BU) return;
   const uint32_t* __restrict__ fcur = (c->fsel ? B.f[1] : B.f[0]);
@@ -520,34 +524,64 @@ __global__ void __launch_bounds__(256) bu_pull(int32_t nb, int64_t nwords, uint3
       }
       continue;
     }
+    // first probes of both vertices, independent of each other. In the
+    // degree-aware order the first candidate is the row's last entry, read
+    // from the dense neighbors+ array together with the degree (8 coalesced
+    // bytes per vertex instead of two row bounds and a 32-byte sector).
     int64_t b0 = 0, e0 = 0, b1 = 0, e1 = 0;
-    if (c0) {
-      b0 = off[v0];
-      e0 = off[v0 + 1];
+    int32_t x0 = -1, x1 = -1, d0 = 0, d1 = 0;
+    if (REV) {
+      if (c0) {
+        const int2 t = nplus[v0];
+        x0 = t.x;
+        d0 = t.y;
+      }
+      if (c1) {
+        const int2 t = nplus[v1];
+        x1 = t.x;
+        d1 = t.y;
+      }
+    } else {
+      if (c0) {
+        b0 = off[v0];
+        e0 = off[v0 + 1];
+        d0 = (int32_t)(e0 - b0);
+        if (d0) x0 = col[b0];
+      }
+      if (c1) {
+        b1 = off[v1];
+        e1 = off[v1 + 1];
+        d1 = (int32_t)(e1 - b1);
+        if (d1) x1 = col[b1];
+      }
     }
-    if (c1) {
-      b1 = off[v1];
-      e1 = off[v1 + 1];
-    }
-    // first probes of both vertices, independent of each other
-    int32_t x0 = -1, x1 = -1;
-    if (e0 > b0) x0 = col[REV ? e0 - 1 : b0];
-    if (e1 > b1) x1 = col[REV ? e1 - 1 : b1];
     int32_t p0 = (x0 >= 0 && in_frontier(fcur, x0)) ? x0 : -1;
     int32_t p1 = (x1 >= 0 && in_frontier(fcur, x1)) ? x1 : -1;
-    int64_t k0 = e0 > b0 ? 1 : 0, k1 = e1 > b1 ? 1 : 0;
-    if (p0 < 0) p0 = bu_scan_rest<REV>(col, fcur, b0, e0, k0);
-    if (p1 < 0) p1 = bu_scan_rest<REV>(col, fcur, b1, e1, k1);
+    int64_t k0 = d0 > 0 ? 1 : 0, k1 = d1 > 0 ? 1 : 0;
+    if (p0 < 0 && d0 > 1) {
+      if (REV) {
+        e0 = off[v0 + 1];
+        b0 = e0 - d0;
+      }
+      p0 = bu_scan_rest<REV>(col, fcur, b0, e0, k0);
+    }
+    if (p1 < 0 && d1 > 1) {
+      if (REV) {
+        e1 = off[v1 + 1];
+        b1 = e1 - d1;
+      }
+      p1 = bu_scan_rest<REV>(col, fcur, b1, e1, k1);
+    }
     acc.ex += (unsigned)(k0 + k1);
     const uint32_t n0 = __ballot_sync(0xffffffffu, p0 >= 0);
     const uint32_t n1 = __ballot_sync(0xffffffffu, p1 >= 0);
     if (p0 >= 0) {
       pl[v0] = make_int2(p0, lnext);
-      acc.add_vertex((int32_t)v0, e0 - b0);
+      acc.add_vertex((int32_t)v0, d0);
     }
     if (p1 >= 0) {
       pl[v1] = make_int2(p1, lnext);
-      acc.add_vertex((int32_t)v1, e1 - b1);
+      acc.add_vertex((int32_t)v1, d1);
     }
     if (lane == 0) {
       fnext[w0] = n0;
@@ -783,34 +817,60 @@ __global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
 
 // Output translation of a relabelled graph in two streaming passes instead of
 // one random gather per vertex. The original IDs are cut into windows of
-// TR_W; pass 1 walks the BFS-graph labels in order (coalesced) and appends
-// each reached vertex to its window's bucket (one counter atomic, writes
-// that stay sequential per bucket); pass 2 gives each window to one block,
-// which assembles the window's parent[] and level[] in shared memory (-1 for
-// unreached) and writes them out coalesced.
+// TR_W. The permutation is fixed, so every BFS-graph vertex x has a fixed
+// slot in the bucket of its window, planned once per workspace (tr_plan).
+// Pass 1 walks the labels in order (coalesced reads) and writes x's
+// (window offset, level, parent) to its slot -- no atomics, and each bucket
+// fills roughly in order so its writes merge in L2; pass 2 gives each window
+// to one block, which assembles the window's parent[] and level[] in shared
+// memory (-1 for unreached and isolated vertices) and writes them coalesced.
 #define TR_SHIFT 12
 #define TR_W (1 << TR_SHIFT)
 #define TR_LEVEL_BITS 20
+#define TR_UNREACHED ((1u << TR_LEVEL_BITS) - 1u)
+
+// Plan: keys (window << 32 | x) sorted, so each window's vertices are in
+// label order; slot[x] = sorted position, window w occupies the positions
+// [wstart[w], wend[w]) (both zero for a window without BFS-graph vertices).
+__global__ void tr_plan_keys(int32_t nb, const int32_t* __restrict__ old_of_new,
+                             uint64_t* keys) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nb;
+       x += (int64_t)gridDim.x * blockDim.x)
+    keys[x] = ((uint64_t)(old_of_new[x] >> TR_SHIFT) << 32) | (uint64_t)x;
+}
+
+__global__ void tr_plan_slots(int32_t nb, const uint64_t* __restrict__ keys, unsigned* slot,
+                              unsigned* wstart, unsigned* wend) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    const unsigned w = (unsigned)(k >> 32);
+    slot[(uint32_t)k] = (unsigned)i;
+    if (i == 0 || (unsigned)(keys[i - 1] >> 32) != w) wstart[w] = (unsigned)i;
+    if (i == nb - 1 || (unsigned)(keys[i + 1] >> 32) != w) wend[w] = (unsigned)i + 1u;
+  }
+}
 
 __global__ void tr_bucket(int32_t nb, const uint32_t* __restrict__ visited,
                           const int2* __restrict__ pl, const int32_t* __restrict__ old_of_new,
-                          unsigned* bcount, unsigned long long* bucket) {
+                          const unsigned* __restrict__ slot, unsigned long long* bucket) {
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nb;
        x += (int64_t)gridDim.x * blockDim.x) {
-    if (!((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u)) continue;
-    const int2 t = pl[x];
     const int32_t o = old_of_new[x];
-    const int32_t po = __ldg(&old_of_new[t.x]);
-    const int64_t b = o >> TR_SHIFT;
-    const unsigned slot = atomicAdd(&bcount[b], 1u);
-    bucket[b * TR_W + slot] = ((unsigned long long)(o & (TR_W - 1)) << 52) |
-                              ((unsigned long long)(t.y & ((1 << TR_LEVEL_BITS) - 1)) << 32) |
-                              (unsigned)po;
+    unsigned lev = TR_UNREACHED, po = 0;
+    if ((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u) {
+      const int2 t = pl[x];
+      po = (unsigned)__ldg(&old_of_new[t.x]);
+      lev = (unsigned)t.y & TR_UNREACHED;
+    }
+    bucket[slot[x]] =
+        ((unsigned long long)(o & (TR_W - 1)) << 52) | ((unsigned long long)lev << 32) | po;
   }
 }
 
 __global__ void __launch_bounds__(256) tr_window(int32_t n, int32_t root,
-                                                 const unsigned* __restrict__ bcount,
+                                                 const unsigned* __restrict__ wstart,
+                                                 const unsigned* __restrict__ wend,
                                                  const unsigned long long* __restrict__ bucket,
                                                  int32_t* parent, int32_t* level) {
   __shared__ int32_t sp[TR_W], sl[TR_W];
@@ -822,12 +882,14 @@ __global__ void __launch_bounds__(256) tr_window(int32_t n, int32_t root,
       sl[i] = -1;
     }
     __syncthreads();
-    const unsigned cnt = bcount[b];
-    for (unsigned i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const unsigned long long e = bucket[base + i];
+    const unsigned e0 = wstart[b], e1 = wend[b];
+    for (unsigned i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+      const unsigned long long e = bucket[i];
+      const unsigned lev = (unsigned)(e >> 32) & TR_UNREACHED;
+      if (lev == TR_UNREACHED) continue;
       const int lo = (int)(e >> 52);
       sp[lo] = (int32_t)(unsigned)(e & 0xFFFFFFFFull);
-      sl[lo] = (int32_t)((e >> 32) & ((1u << TR_LEVEL_BITS) - 1));
+      sl[lo] = (int32_t)lev;
     }
     __syncthreads();
     if (threadIdx.x == 0 && root >= base && root < base + TR_W) {
@@ -840,6 +902,15 @@ __global__ void __launch_bounds__(256) tr_window(int32_t n, int32_t root,
       level[base + i] = sl[i];
     }
     __syncthreads();
+  }
+}
+
+__global__ void build_nplus(int32_t nb, const int64_t* __restrict__ off,
+                            const int32_t* __restrict__ col, int2* nplus) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nb;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = off[v], e = off[v + 1];
+    nplus[v] = make_int2(e > b ? col[e - 1] : -1, (int32_t)(e - b));
   }
 }
 
@@ -883,9 +954,12 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
       {(void**)&ws->fb, nw * 4},             {(void**)&ws->vis_save, nw * 4},
       {(void**)&ws->qa, nb1 * 4},            {(void**)&ws->qb, nb1 * 4},
       {(void**)&ws->bins, nb1 * 4 * 3},      {(void**)&ws->pl, nb1 * 8},
+      {(void**)&ws->nplus, nb1 * 8},
       {(void**)&ws->goff, nb1 * 8},          {(void**)&ws->out_parent, n1 * 4},
-      {(void**)&ws->out_level, n1 * 4},      {(void**)&ws->bcount, nbk * 4},
-      {(void**)&ws->bucket, nbk * TR_W * 8}, {(void**)&ws->ctrl, sizeof(Ctrl)},
+      {(void**)&ws->out_level, n1 * 4},      {(void**)&ws->wstart, nbk * 4},
+      {(void**)&ws->wend, nbk * 4},
+      {(void**)&ws->slot, nb1 * 4},
+      {(void**)&ws->bucket, nb1 * 8},        {(void**)&ws->ctrl, sizeof(Ctrl)},
       {(void**)&ws->log, sizeof(LevelLog) * LOG_MAX},
   };
   for (auto& r : req) {
@@ -908,6 +982,16 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
       g3_bfs_ws_free(ws);
       return G3_ECUDA;
     }
+  if (ws->nb > 0) {  // neighbors+ (Algorithm 6): last row entry and degree
+    build_nplus<<<g3_grid_for(ws->nb, 256), 256>>>(ws->nb, g->off, g->col, ws->nplus);
+    g3_count_launch();
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      g3_set_error("g3_bfs workspace: %s", cudaGetErrorString(e));
+      g3_bfs_ws_free(ws);
+      return G3_ECUDA;
+    }
+  }
   ws->grid_front = resident_grid(td_front, 256);
   ws->grid_bins = resident_grid(td_bins, 256);
   ws->grid_bu = resident_grid(bu_pull<1>, 256);
@@ -918,6 +1002,35 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
   ws->grid_trb = resident_grid(tr_bucket, 256);
   ws->grid_trw = resident_grid(tr_window, 256);
   ws->nbuckets = ((int64_t)g->n + TR_W - 1) >> TR_SHIFT;
+  if (g->relabelled) {  // plan each vertex's slot in its window's bucket
+    g3_status st = G3_OK;
+    cudaMemset(ws->wstart, 0, (size_t)(ws->nbuckets + 1) * 4);
+    cudaMemset(ws->wend, 0, (size_t)(ws->nbuckets + 1) * 4);
+    if (ws->nb > 0) {
+      uint64_t *ka = nullptr, *kb = nullptr, *sorted = nullptr;
+      st = g3_alloc(&ka, ws->nb, 0);
+      if (st == G3_OK) st = g3_alloc(&kb, ws->nb, 0);
+      if (st == G3_OK) {
+        tr_plan_keys<<<g3_grid_for(ws->nb, 256), 256>>>(ws->nb, g->old_of_new, ka);
+        g3_count_launch();
+        st = g3_radix_sort_u64(ka, kb, ws->nb, 32 + g3_bits_for(ws->nbuckets + 1), &sorted, 0);
+      }
+      if (st == G3_OK) {
+        tr_plan_slots<<<g3_grid_for(ws->nb, 256), 256>>>(ws->nb, sorted, ws->slot, ws->wstart,
+                                                         ws->wend);
+        g3_count_launch();
+      }
+      g3_free(ka, 0);
+      g3_free(kb, 0);
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (st != G3_OK || e != cudaSuccess) {
+      if (e != cudaSuccess)
+        g3_set_error("g3_bfs workspace: translation plan: %s", cudaGetErrorString(e));
+      g3_bfs_ws_free(ws);
+      return st != G3_OK ? st : G3_ECUDA;
+    }
+  }
   *out = ws;
   return G3_OK;
 }
@@ -981,10 +1094,10 @@ static g3_status launch_level(const Launch& S, int mode, int64_t nf, cudaEvent_t
     const int grid = cap_grid(ws->nwords, 16, ws->grid_bu);
     if (S.o->bu_reverse)
       bu_pull<1><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.B, S.g->off, S.g->col,
-                                      ws->pl, c);
+                                      ws->nplus, ws->pl, c);
     else
       bu_pull<0><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.B, S.g->off, S.g->col,
-                                      ws->pl, c);
+                                      ws->nplus, ws->pl, c);
     G3_CHECK_LAUNCH();
   }
   return G3_OK;
@@ -1041,7 +1154,7 @@ static g3_status build_graph(Launch& S) {
   void* a_clear[] = {&S.B, &nwords, &c};
   void* a_q2b[] = {&S.B, &c};
   void* a_td[] = {&off, &col, &ws->visited, &ws->pl, &S.B, &ws->bins, &ws->goff, &S.nb1, &c};
-  void* a_bu[] = {&nb, &nwords, &ws->visited, &S.B, &off, &col, &ws->pl, &c};
+  void* a_bu[] = {&nb, &nwords, &ws->visited, &S.B, &off, &col, &ws->nplus, &ws->pl, &c};
   CtrlArgs ca;
   void* a_ctl[] = {&c, &ca};
   void* a_sel[] = {&c, &h_mode};
@@ -1228,14 +1341,13 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   const bool dev_p = is_device_ptr(parent), dev_l = is_device_ptr(level);
   int32_t* op = dev_p ? parent : ws->out_parent;
   int32_t* ol = dev_l ? level : ws->out_level;
-  if (g->relabelled && nrec < (1 << TR_LEVEL_BITS)) {
-    G3_TRY_CUDA(cudaMemsetAsync(ws->bcount, 0, (size_t)ws->nbuckets * 4, s));
+  if (g->relabelled && nrec < (int32_t)TR_UNREACHED) {
     tr_bucket<<<cap_grid(nb, 256, ws->grid_trb), 256, 0, s>>>(nb, ws->visited, ws->pl,
-                                                               g->old_of_new, ws->bcount,
+                                                               g->old_of_new, ws->slot,
                                                                ws->bucket);
     G3_CHECK_LAUNCH();
     tr_window<<<cap_grid(ws->nbuckets, 1, ws->grid_trw), 256, 0, s>>>(
-        g->n, root, ws->bcount, ws->bucket, op, ol);
+        g->n, root, ws->wstart, ws->wend, ws->bucket, op, ol);
     G3_CHECK_LAUNCH();
   } else {  // labels are the original IDs, or levels too deep for the bucket format
     bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, s>>>(
