@@ -51,8 +51,9 @@ def parse_args():
     ap.add_argument("--roots", type=int, default=64)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--root-seed", type=int, default=2)
-    ap.add_argument("--controller", choices=["heuristic", "learned", "topdown", "bottomup"],
-                    default="heuristic")
+    ap.add_argument("--controller",
+                    choices=["auto", "heuristic", "learned", "topdown", "bottomup"],
+                    default="auto", help="auto: learned when trained parameters exist")
     ap.add_argument("--mlp", default=os.path.join(ROOT, "paper_2012_10026_gb300",
                                                   "mlp_params.json"))
     ap.add_argument("--cpu-baseline", type=int, default=1, help="run the oracle leg (rank 0)")
@@ -225,7 +226,8 @@ def workload_config(args):
     return {"workload": f"kronecker_scale{args.scale}_ef{args.edgefactor}_rcm_{args.roots}roots",
             "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
             "initiator": [0.57, 0.19, 0.19, 0.05], "gen_seed": args.seed,
-            "root_seed": args.root_seed, "controller": args.controller,
+            "root_seed": args.root_seed,
+            "controller": getattr(args, "controller_used", args.controller),
             "bu_reverse": args.bu_reverse,
             "l2": "256 MB write between roots (L2 flush); CSR larger than L2",
             "parallelism": "replicas"}
@@ -263,8 +265,13 @@ def gpu_arm(args, rank, world):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     info = g.info
+    use_learned = args.controller == "learned" or (args.controller == "auto" and
+                                                   os.path.exists(args.mlp))
+    name = "learned" if use_learned else ("heuristic" if args.controller == "auto"
+                                          else args.controller)
+    args.controller_used = name
     ctrl = {"heuristic": g3.G3_CTRL_HEURISTIC, "learned": g3.G3_CTRL_LEARNED,
-            "topdown": g3.G3_CTRL_TOPDOWN, "bottomup": g3.G3_CTRL_BOTTOMUP}[args.controller]
+            "topdown": g3.G3_CTRL_TOPDOWN, "bottomup": g3.G3_CTRL_BOTTOMUP}[name]
     kw = dict(controller=ctrl, bu_reverse=args.bu_reverse)
     mlp_t = None
     if ctrl == g3.G3_CTRL_LEARNED:
@@ -273,6 +280,7 @@ def gpu_arm(args, rank, world):
         kw["mlp_params"] = mlp_t
     opts = g3.opts(**kw)  # default path: the level loop runs as one CUDA graph
     opts_timed = g3.opts(timing=1, **kw)  # host-driven, CUDA events around each level
+    plain_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, bu_reverse=args.bu_reverse)
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
     level = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -323,6 +331,16 @@ def gpu_arm(args, rank, world):
     # instrumented step: the same kernels launched level by level with CUDA
     # events around each level's expansion, for the per-kernel roofline
     inst_t, all_st = one_step(opts_timed, 256)
+    # the plain heuristic BFS on the same graph and roots, when the headline
+    # is the learned controller
+    plain_t = None
+    if ctrl != g3.G3_CTRL_HEURISTIC:
+        for _ in range(args.warmup):
+            one_step(plain_opts, 0)
+        torch.cuda.synchronize()
+        plain_t = []
+        for _ in range(args.steps):
+            plain_t += one_step(plain_opts, 0)[0]
     if dist:
         dist.barrier()
     clocks = stop_clock_sampler(sampler, clk_path, local)
@@ -429,6 +447,9 @@ def gpu_arm(args, rank, world):
                             "max": max(all_t)},
             "levels": {"min": min(levels), "max": max(levels)},
             "hm_this_rank": hm,
+            "plain_heuristic": None if plain_t is None else {
+                "value": harmonic_gteps(ms, plain_t), "unit": "GTEPS",
+                "per_root_ms_median": statistics.median(plain_t)},
         }
         print(json.dumps(line), flush=True)
         if args.stats_out:

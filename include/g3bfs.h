@@ -197,6 +197,43 @@ g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, int32_t* pa
                  int32_t* level, g3_level_stats* stats, int32_t max_stats,
                  int32_t* n_levels, void* stream);
 
+/* --------------------------------------------------- learned controller */
+
+/* The learned direction / binning controller (the paper has no learned
+ * part; it tunes alpha and beta by grid search, Sec. 3.6): a multilayer
+ * perceptron with 12 inputs, 32 ReLU hidden units and 4 linear outputs.
+ *   params : G3_MLP_NPARAMS floats, layout W1[32][12], b1[32], W2[4][32], b2[4]
+ *   x      : B rows of 12 features (see g3_mlp_features), row-major
+ *   y      : B rows of 4 targets: ln(t_BU / t_TD) and log2 of the fastest
+ *            top-down bin thresholds t1, t2, t3
+ *   w      : 4 per-output loss weights, or NULL for all ones
+ * Loss L = 1/(2B) sum_b sum_k w_k (o_bk - y_bk)^2. All pointers are device
+ * pointers; calls are asynchronous on `stream` unless stated. */
+#define G3_MLP_NPARAMS 548
+
+/* out: B rows of 4 outputs. o0 < 0 selects bottom-up. */
+g3_status g3_mlp_forward(const float* params, const float* x, int32_t B, float* out,
+                         void* stream);
+
+/* loss (1 float) and grad (G3_MLP_NPARAMS floats) of the batch; computed by
+ * one block with a fixed summation order, so repeated calls agree bit for bit. */
+g3_status g3_mlp_loss_grad(const float* params, const float* x, const float* y,
+                           const float* w, int32_t B, float* loss, float* grad,
+                           void* stream);
+
+/* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8) at rate lr,
+ * updating params in place; losses (steps floats, or NULL) receives the loss
+ * before each step. One kernel launch. */
+g3_status g3_mlp_train(float* params, const float* x, const float* y, const float* w,
+                       int32_t B, int32_t steps, float lr, float* losses, void* stream);
+
+/* Feature rows x (count x 12 floats, device) of the level records `stats`
+ * (host array as g3_bfs returns them, consecutive records of one search in
+ * order), computed by the same device code the controller uses. n_bfs is the
+ * searched graph's vertex count. Synchronises `stream`. */
+g3_status g3_mlp_features(const g3_level_stats* stats, int32_t count, int32_t n_bfs, float* x,
+                          void* stream);
+
 /* ------------------------------------------------- allocation-free BFS */
 
 /* The paper has no counterpart to this entry point: it serves callers that

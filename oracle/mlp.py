@@ -12,7 +12,7 @@ ReLU derivative is taken as 0 at z == 0.
 Features of a level (inputs), computed from the frontier statistics:
     0 log2(1+n_f)   1 log2(1+m_f)   2 log2(1+n_u)   3 log2(1+m_u)
     4 (max_id - min_id) / n   (0 for an empty frontier)
-    5 log2((1+m_f)/(1+m_u))  6 level/32  7 previous direction (0 TD, 1 BU)
+    5 log2((1+m_f)/(1+m_u))  6 log2(1+n) (graph size)  7 previous direction (0 TD, 1 BU)
     8..11 fraction of frontier vertices with degree in
           [0,32), [32,1024), [1024,32768), [32768, inf)
 Outputs: o0 ~ ln(t_BU / t_TD) (bottom-up when o0 < 0), o1..o3 ~ log2 of the
@@ -101,6 +101,6 @@ def features(n_f, m_f, n_u, m_u, id_min, id_max, n, level, prev_dir, hist4):
     tot = max(n_f, 1)
     return np.array([
         np.log2(1.0 + n_f), np.log2(1.0 + m_f), np.log2(1.0 + n_u), np.log2(1.0 + m_u),
-        span, np.log2((1.0 + m_f) / (1.0 + m_u)), level / 32.0, float(prev_dir),
+        span, np.log2((1.0 + m_f) / (1.0 + m_u)), np.log2(1.0 + n), float(prev_dir),
         hist4[0] / tot, hist4[1] / tot, hist4[2] / tot, hist4[3] / tot,
     ], dtype=np.float64)

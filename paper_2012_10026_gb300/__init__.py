@@ -85,6 +85,12 @@ _SIGS = {
                               ctypes.POINTER(ctypes.c_int32), _vp]),
     "g3_bfs_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
                                       _vp]),
+    "g3_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp]),
+    "g3_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp]),
+    "g3_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_float, _vp, _vp]),
+    "g3_mlp_features": (ctypes.c_int, [ctypes.POINTER(g3_level_stats), ctypes.c_int32,
+                                       ctypes.c_int32, _vp, _vp]),
 }
 NOALLOC_MAX_N = 1 << 20
 
@@ -200,6 +206,55 @@ def g3_bfs_noalloc(off, col, n: int, root: int, parent, level, stream=None):
     device must not overlap on the GPU."""
     _check(lib().g3_bfs_noalloc(_ptr(off), _ptr(col), int(n), int(root), _ptr(parent),
                                 _ptr(level), _stream(stream)), "g3_bfs_noalloc")
+
+
+def _optr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def g3_mlp_forward(params, x, stream=None):
+    """MLP outputs (B x 4, float32 device tensor) for feature rows x (B x 12)."""
+    import torch
+    out = torch.empty((x.shape[0], 4), dtype=torch.float32, device=x.device)
+    _check(lib().g3_mlp_forward(_ptr(params), _ptr(x), x.shape[0], _ptr(out), _stream(stream)),
+           "g3_mlp_forward")
+    return out
+
+
+def g3_mlp_loss_grad(params, x, y, w=None, stream=None):
+    import torch
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    grad = torch.empty(MLP_NPARAMS, dtype=torch.float32, device=x.device)
+    _check(lib().g3_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(y), _optr(w), x.shape[0],
+                                  _ptr(loss), _ptr(grad), _stream(stream)), "g3_mlp_loss_grad")
+    return loss, grad
+
+
+def g3_mlp_train(params, x, y, steps: int, lr: float = 1e-2, w=None, stream=None):
+    """Full-batch Adam on the GPU, params updated in place; returns the losses."""
+    import torch
+    losses = torch.empty(max(steps, 1), dtype=torch.float32, device=x.device)
+    _check(lib().g3_mlp_train(_ptr(params), _ptr(x), _ptr(y), _optr(w), x.shape[0], int(steps),
+                              float(lr), _ptr(losses), _stream(stream)), "g3_mlp_train")
+    return losses[:steps]
+
+
+def g3_mlp_features(stats, n_bfs: int, device="cuda", stream=None):
+    """Feature rows (len(stats) x 12) of level records (dicts from g3_bfs)."""
+    import torch
+    arr = (g3_level_stats * max(len(stats), 1))()
+    for i, d in enumerate(stats):
+        for k, _ in g3_level_stats._fields_:
+            v = d[k]
+            if k in ("hist", "mlp_out"):
+                for j, e in enumerate(v):
+                    getattr(arr[i], k)[j] = e
+            else:
+                setattr(arr[i], k, v)
+    x = torch.empty((max(len(stats), 1), 12), dtype=torch.float32, device=device)
+    _check(lib().g3_mlp_features(arr, len(stats), int(n_bfs), _ptr(x), _stream(stream)),
+           "g3_mlp_features")
+    return x[:len(stats)]
 
 
 def g3_graph_free(graph: "Graph"):

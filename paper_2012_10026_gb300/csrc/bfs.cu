@@ -39,10 +39,12 @@
 // histogram, edges examined) are reduced per block and added with one atomic
 // per block; the controller logs them per level. (parent, level) of BFS-graph
 // vertices are kept packed as int2 and are only meaningful where the visited
-// bit is set, so nothing but the visited bitmap is cleared per search.
+// bit is set, so nothing but the visited bitmap is cleared per search. The
+// outputs in original IDs are then gathered in one pass (bfs_translate4).
 #include <math.h>
 #include <string.h>
 
+#include "g3_mlp.cuh"
 #include "g3_prims.cuh"
 
 #define LOG_MAX 4096           // per-level records kept on the device
@@ -100,16 +102,12 @@ struct g3_bfs_ws {
   int2* pl;                 // (parent, level) per BFS-graph vertex
   int2* nplus;              // (last row entry or -1, degree): Algorithm 6's neighbors+
   int32_t *out_parent, *out_level;  // staging for host outputs (n entries)
-  unsigned *wstart, *wend;          // translation: each window's slot range
-  unsigned* slot;                   // translation: each vertex's slot in its window
-  unsigned long long* bucket;       // translation: TR_W slots per window
-  int64_t nbuckets;
   Ctrl* ctrl;
   Ctrl* h_ctrl;  // pinned
   LevelLog* log;
   cudaEvent_t ev[6];
   // resident-grid sizes (SMs x blocks per SM) per kernel
-  int grid_front, grid_bins, grid_bu, grid_conv, grid_tr, grid_trb, grid_trw;
+  int grid_front, grid_bins, grid_bu, grid_conv, grid_tr, grid_tr4;
   // graph mode: instantiated level loop and the options it was built for
   cudaGraphExec_t gexec;
   g3_bfs_opts gopts;
@@ -119,8 +117,7 @@ void g3_bfs_ws_free(g3_bfs_ws* ws) {
   if (!ws) return;
   void* all[] = {ws->visited,    ws->fa,        ws->fb,   ws->vis_save, ws->qa,
                  ws->qb,         ws->bins,      ws->pl,   ws->out_parent,
-                 ws->out_level,  ws->ctrl,      ws->goff, ws->wstart,   ws->bucket, ws->slot,
-                 ws->wend,       ws->nplus,
+                 ws->out_level,  ws->ctrl,      ws->goff, ws->nplus,
                  ws->log};
   for (void* p : all)
     if (p) cudaFree(p);
@@ -651,39 +648,10 @@ __global__ void bitmap_to_q(Bufs B, int64_t nwords, Ctrl* c) {
 }
 
 // ------------------------------------------------------------- controller
-// Learned controller: 12-32-4 MLP (ReLU) evaluated by one warp, lane j =
-// hidden unit j. Parameter layout: W1[32][12], b1[32], W2[4][32], b2[4].
+// Learned controller: the 12-32-4 MLP of g3_mlp.cuh on the frontier record.
 __device__ void mlp_features(const Ctrl* c, int32_t nb, int prev_dir, float* f) {
-  const float nf = (float)c->nf, mf = (float)c->mf, nu = (float)c->nu, mu = (float)c->mu;
-  f[0] = log2f(1.f + nf);
-  f[1] = log2f(1.f + mf);
-  f[2] = log2f(1.f + nu);
-  f[3] = log2f(1.f + mu);
-  f[4] = (c->nf > 0 && nb > 0) ? (float)(c->id_max - c->id_min) / (float)nb : 0.f;
-  f[5] = log2f((1.f + mf) / (1.f + mu));
-  f[6] = (float)c->level / 32.f;
-  f[7] = (float)prev_dir;
-  const float tot = c->nf > 0 ? (float)c->nf : 1.f;
-  for (int k = 0; k < 4; ++k) f[8 + k] = (float)c->hist[k] / tot;
-}
-
-__device__ void mlp_eval_warp(const float* __restrict__ P, const float* f, float* out) {
-  const int j = threadIdx.x & 31;
-  const float* W1 = P;
-  const float* b1 = P + 32 * 12;
-  const float* W2 = b1 + 32;
-  const float* b2 = W2 + 4 * 32;
-  float z = b1[j];
-#pragma unroll
-  for (int i = 0; i < 12; ++i) z = fmaf(W1[j * 12 + i], f[i], z);
-  const float h = fmaxf(z, 0.f);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    float s = W2[k * 32 + j] * h;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    out[k] = s + b2[k];
-  }
+  mlp_features_raw(c->nf, c->mf, c->nu, c->mu, c->id_min, c->id_max, nb, c->level, prev_dir,
+                   c->hist, f);
 }
 
 __device__ __forceinline__ int clamp_thr(float lg, int lo, int hi) {
@@ -815,93 +783,67 @@ __global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
   }
 }
 
-// Output translation of a relabelled graph in two streaming passes instead of
-// one random gather per vertex. The original IDs are cut into windows of
-// TR_W. The permutation is fixed, so every BFS-graph vertex x has a fixed
-// slot in the bucket of its window, planned once per workspace (tr_plan).
-// Pass 1 walks the labels in order (coalesced reads) and writes x's
-// (window offset, level, parent) to its slot -- no atomics, and each bucket
-// fills roughly in order so its writes merge in L2; pass 2 gives each window
-// to one block, which assembles the window's parent[] and level[] in shared
-// memory (-1 for unreached and isolated vertices) and writes them coalesced.
-#define TR_SHIFT 12
-#define TR_W (1 << TR_SHIFT)
-#define TR_LEVEL_BITS 20
-#define TR_UNREACHED ((1u << TR_LEVEL_BITS) - 1u)
-
-// Plan: keys (window << 32 | x) sorted, so each window's vertices are in
-// label order; slot[x] = sorted position, window w occupies the positions
-// [wstart[w], wend[w]) (both zero for a window without BFS-graph vertices).
-__global__ void tr_plan_keys(int32_t nb, const int32_t* __restrict__ old_of_new,
-                             uint64_t* keys) {
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nb;
-       x += (int64_t)gridDim.x * blockDim.x)
-    keys[x] = ((uint64_t)(old_of_new[x] >> TR_SHIFT) << 32) | (uint64_t)x;
-}
-
-__global__ void tr_plan_slots(int32_t nb, const uint64_t* __restrict__ keys, unsigned* slot,
-                              unsigned* wstart, unsigned* wend) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb;
+// Same mapping, four consecutive original IDs per thread: one 128-bit load
+// of new_of_old, four independent gathers of (parent, level) and of the
+// parent's original ID in flight at once (the random gathers are what bounds
+// this pass, so their latency has to overlap), 128-bit stores. parent and
+// level must be 16-byte aligned.
+__global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int32_t root,
+                                                      const int32_t* __restrict__ new_of_old,
+                                                      const int32_t* __restrict__ old_of_new,
+                                                      const uint32_t* __restrict__ visited,
+                                                      const int2* __restrict__ pl,
+                                                      int32_t* parent, int32_t* level) {
+  const int64_t n4 = n >> 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = keys[i];
-    const unsigned w = (unsigned)(k >> 32);
-    slot[(uint32_t)k] = (unsigned)i;
-    if (i == 0 || (unsigned)(keys[i - 1] >> 32) != w) wstart[w] = (unsigned)i;
-    if (i == nb - 1 || (unsigned)(keys[i + 1] >> 32) != w) wend[w] = (unsigned)i + 1u;
+    int x[4];
+    if (new_of_old) {
+      const int4 xs = __ldg(reinterpret_cast<const int4*>(new_of_old) + i);
+      x[0] = xs.x;
+      x[1] = xs.y;
+      x[2] = xs.z;
+      x[3] = xs.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) x[k] = (int)(4 * i + k);
+    }
+    bool r[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      r[k] = x[k] < nb && ((__ldg(&visited[x[k] >> 5]) >> (x[k] & 31)) & 1u);
+    int2 t[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t[k] = r[k] ? __ldg(&pl[x[k]]) : make_int2(-1, -1);
+    int p[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      p[k] = r[k] ? (old_of_new ? __ldg(&old_of_new[t[k].x]) : t[k].x) : -1;
+      l[k] = t[k].y;
+    }
+    if ((root >> 2) == i) {
+      p[root & 3] = root;
+      l[root & 3] = 0;
+    }
+    reinterpret_cast<int4*>(parent)[i] = make_int4(p[0], p[1], p[2], p[3]);
+    reinterpret_cast<int4*>(level)[i] = make_int4(l[0], l[1], l[2], l[3]);
   }
-}
-
-__global__ void tr_bucket(int32_t nb, const uint32_t* __restrict__ visited,
-                          const int2* __restrict__ pl, const int32_t* __restrict__ old_of_new,
-                          const unsigned* __restrict__ slot, unsigned long long* bucket) {
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nb;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t o = old_of_new[x];
-    unsigned lev = TR_UNREACHED, po = 0;
-    if ((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u) {
-      const int2 t = pl[x];
-      po = (unsigned)__ldg(&old_of_new[t.x]);
-      lev = (unsigned)t.y & TR_UNREACHED;
+  // the last n % 4 IDs
+  const int64_t v = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v < n) {
+    int32_t p = -1, l = -1;
+    const int32_t xv = new_of_old ? new_of_old[v] : (int32_t)v;
+    if (xv < nb && ((__ldg(&visited[xv >> 5]) >> (xv & 31)) & 1u)) {
+      const int2 t = pl[xv];
+      p = old_of_new ? old_of_new[t.x] : t.x;
+      l = t.y;
     }
-    bucket[slot[x]] =
-        ((unsigned long long)(o & (TR_W - 1)) << 52) | ((unsigned long long)lev << 32) | po;
-  }
-}
-
-__global__ void __launch_bounds__(256) tr_window(int32_t n, int32_t root,
-                                                 const unsigned* __restrict__ wstart,
-                                                 const unsigned* __restrict__ wend,
-                                                 const unsigned long long* __restrict__ bucket,
-                                                 int32_t* parent, int32_t* level) {
-  __shared__ int32_t sp[TR_W], sl[TR_W];
-  const int64_t nbk = ((int64_t)n + TR_W - 1) >> TR_SHIFT;
-  for (int64_t b = blockIdx.x; b < nbk; b += gridDim.x) {
-    const int64_t base = b << TR_SHIFT;
-    for (int i = threadIdx.x; i < TR_W; i += blockDim.x) {
-      sp[i] = -1;
-      sl[i] = -1;
+    if (v == root) {
+      p = root;
+      l = 0;
     }
-    __syncthreads();
-    const unsigned e0 = wstart[b], e1 = wend[b];
-    for (unsigned i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
-      const unsigned long long e = bucket[i];
-      const unsigned lev = (unsigned)(e >> 32) & TR_UNREACHED;
-      if (lev == TR_UNREACHED) continue;
-      const int lo = (int)(e >> 52);
-      sp[lo] = (int32_t)(unsigned)(e & 0xFFFFFFFFull);
-      sl[lo] = (int32_t)lev;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && root >= base && root < base + TR_W) {
-      sp[root - base] = root;  // also an isolated root
-      sl[root - base] = 0;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < TR_W && base + i < n; i += blockDim.x) {
-      parent[base + i] = sp[i];
-      level[base + i] = sl[i];
-    }
-    __syncthreads();
+    parent[v] = p;
+    level[v] = l;
   }
 }
 
@@ -945,7 +887,6 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
   ws->nb = g->n_bfs;
   ws->nwords = ((int64_t)g->n_bfs + 31) / 32;
   const size_t nb1 = (size_t)g->n_bfs + 4, nw = (size_t)ws->nwords + 4, n1 = (size_t)g->n + 4;
-  const size_t nbk = (size_t)(g->n >> TR_SHIFT) + 2;
   struct {
     void** p;
     size_t bytes;
@@ -956,10 +897,8 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
       {(void**)&ws->bins, nb1 * 4 * 3},      {(void**)&ws->pl, nb1 * 8},
       {(void**)&ws->nplus, nb1 * 8},
       {(void**)&ws->goff, nb1 * 8},          {(void**)&ws->out_parent, n1 * 4},
-      {(void**)&ws->out_level, n1 * 4},      {(void**)&ws->wstart, nbk * 4},
-      {(void**)&ws->wend, nbk * 4},
-      {(void**)&ws->slot, nb1 * 4},
-      {(void**)&ws->bucket, nb1 * 8},        {(void**)&ws->ctrl, sizeof(Ctrl)},
+      {(void**)&ws->out_level, n1 * 4},
+      {(void**)&ws->ctrl, sizeof(Ctrl)},
       {(void**)&ws->log, sizeof(LevelLog) * LOG_MAX},
   };
   for (auto& r : req) {
@@ -999,38 +938,7 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
   if (g0 < ws->grid_bu) ws->grid_bu = g0;
   ws->grid_conv = resident_grid(bitmap_to_q, 256);
   ws->grid_tr = resident_grid(bfs_translate, 256);
-  ws->grid_trb = resident_grid(tr_bucket, 256);
-  ws->grid_trw = resident_grid(tr_window, 256);
-  ws->nbuckets = ((int64_t)g->n + TR_W - 1) >> TR_SHIFT;
-  if (g->relabelled) {  // plan each vertex's slot in its window's bucket
-    g3_status st = G3_OK;
-    cudaMemset(ws->wstart, 0, (size_t)(ws->nbuckets + 1) * 4);
-    cudaMemset(ws->wend, 0, (size_t)(ws->nbuckets + 1) * 4);
-    if (ws->nb > 0) {
-      uint64_t *ka = nullptr, *kb = nullptr, *sorted = nullptr;
-      st = g3_alloc(&ka, ws->nb, 0);
-      if (st == G3_OK) st = g3_alloc(&kb, ws->nb, 0);
-      if (st == G3_OK) {
-        tr_plan_keys<<<g3_grid_for(ws->nb, 256), 256>>>(ws->nb, g->old_of_new, ka);
-        g3_count_launch();
-        st = g3_radix_sort_u64(ka, kb, ws->nb, 32 + g3_bits_for(ws->nbuckets + 1), &sorted, 0);
-      }
-      if (st == G3_OK) {
-        tr_plan_slots<<<g3_grid_for(ws->nb, 256), 256>>>(ws->nb, sorted, ws->slot, ws->wstart,
-                                                         ws->wend);
-        g3_count_launch();
-      }
-      g3_free(ka, 0);
-      g3_free(kb, 0);
-    }
-    cudaError_t e = cudaDeviceSynchronize();
-    if (st != G3_OK || e != cudaSuccess) {
-      if (e != cudaSuccess)
-        g3_set_error("g3_bfs workspace: translation plan: %s", cudaGetErrorString(e));
-      g3_bfs_ws_free(ws);
-      return st != G3_OK ? st : G3_ECUDA;
-    }
-  }
+  ws->grid_tr4 = resident_grid(bfs_translate4, 256);
   *out = ws;
   return G3_OK;
 }
@@ -1341,15 +1249,12 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   const bool dev_p = is_device_ptr(parent), dev_l = is_device_ptr(level);
   int32_t* op = dev_p ? parent : ws->out_parent;
   int32_t* ol = dev_l ? level : ws->out_level;
-  if (g->relabelled && nrec < (int32_t)TR_UNREACHED) {
-    tr_bucket<<<cap_grid(nb, 256, ws->grid_trb), 256, 0, s>>>(nb, ws->visited, ws->pl,
-                                                               g->old_of_new, ws->slot,
-                                                               ws->bucket);
+  if ((((uintptr_t)op | (uintptr_t)ol) & 15) == 0) {
+    bfs_translate4<<<cap_grid((g->n + 3) / 4, 256, ws->grid_tr4), 256, 0, s>>>(
+        g->n, nb, root, g->relabelled ? g->new_of_old : nullptr,
+        g->relabelled ? g->old_of_new : nullptr, ws->visited, ws->pl, op, ol);
     G3_CHECK_LAUNCH();
-    tr_window<<<cap_grid(ws->nbuckets, 1, ws->grid_trw), 256, 0, s>>>(
-        g->n, root, ws->wstart, ws->wend, ws->bucket, op, ol);
-    G3_CHECK_LAUNCH();
-  } else {  // labels are the original IDs, or levels too deep for the bucket format
+  } else {  // outputs not 16-byte aligned
     bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, s>>>(
         g->n, nb, root, g->relabelled ? g->new_of_old : nullptr,
         g->relabelled ? g->old_of_new : nullptr, ws->visited, ws->pl, op, ol);

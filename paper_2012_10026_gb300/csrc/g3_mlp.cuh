@@ -1,0 +1,54 @@
+// The 12-32-4 MLP of the learned direction / binning controller: feature
+// extraction and one-warp inference, shared by the controller kernel (bfs.cu)
+// and the training kernels (mlp.cu) so training sees exactly the features the
+// controller computes.
+#pragma once
+#include "g3_internal.cuh"
+
+#define MLP_IN 12
+#define MLP_HID 32
+#define MLP_OUT 4
+#define MLP_NPARAMS (MLP_HID * MLP_IN + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT)  // 548
+// parameter layout: W1[32][12], b1[32], W2[4][32], b2[4]
+#define MLP_B1 (MLP_HID * MLP_IN)
+#define MLP_W2 (MLP_B1 + MLP_HID)
+#define MLP_B2 (MLP_W2 + MLP_OUT * MLP_HID)
+
+// Features of the frontier F_L (see the controller's documentation):
+//  0 log2(1+n_f) 1 log2(1+m_f) 2 log2(1+n_u) 3 log2(1+m_u)
+//  4 (id_max-id_min)/n  5 log2((1+m_f)/(1+m_u))  6 log2(1+n)  7 previous direction
+//  8..11 fraction of F_L in the degree buckets [0,32) [32,1024) [1024,32768) rest
+__device__ __forceinline__ void mlp_features_raw(long long nf, long long mf, long long nu,
+                                                 long long mu, int id_min, int id_max, int32_t nb,
+                                                 int level, int prev_dir, const long long* hist,
+                                                 float* f) {
+  const float fnf = (float)nf, fmf = (float)mf, fnu = (float)nu, fmu = (float)mu;
+  f[0] = log2f(1.f + fnf);
+  f[1] = log2f(1.f + fmf);
+  f[2] = log2f(1.f + fnu);
+  f[3] = log2f(1.f + fmu);
+  f[4] = (nf > 0 && nb > 0) ? (float)(id_max - id_min) / (float)nb : 0.f;
+  f[5] = log2f((1.f + fmf) / (1.f + fmu));
+  f[6] = log2f(1.f + (float)nb);  // graph size: the bottom-up scan cost grows with it
+  f[7] = (float)prev_dir;
+  const float tot = nf > 0 ? fnf : 1.f;
+  for (int k = 0; k < 4; ++k) f[8 + k] = (float)hist[k] / tot;
+}
+
+// One warp evaluates the network for one feature vector: lane j is hidden
+// unit j; the four outputs are warp reductions.
+__device__ __forceinline__ void mlp_eval_warp(const float* __restrict__ P, const float* f,
+                                              float* out) {
+  const int j = threadIdx.x & 31;
+  float z = P[MLP_B1 + j];
+#pragma unroll
+  for (int i = 0; i < MLP_IN; ++i) z = fmaf(P[j * MLP_IN + i], f[i], z);
+  const float h = fmaxf(z, 0.f);
+#pragma unroll
+  for (int k = 0; k < MLP_OUT; ++k) {
+    float s = P[MLP_W2 + k * MLP_HID + j] * h;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    out[k] = s + P[MLP_B2 + k];
+  }
+}

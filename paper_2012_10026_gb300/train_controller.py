@@ -1,0 +1,159 @@
+"""Trains the learned direction / binning controller on the GPU.
+
+Data: Kronecker graphs (edgefactor 16) at the given scales and seeds are
+built and RCM-relabelled by the library; for a sample of roots, g3_bfs runs in
+record_both mode, which expands every level both top-down (with five candidate
+bin-threshold triples) and bottom-up from the same state and times each with
+CUDA events. Each level L >= 1 (level 0 is always top-down) gives one sample:
+
+  x = the controller's 12 features of F_L (g3_mlp_features, the same device
+      code the controller runs),
+  y = [ln(t_BU / t_TD), log2 t1*, log2 t2*, log2 t3*]
+
+with t_TD the fastest top-down time over the candidates and t*'s its bin
+thresholds. The 12-32-4 network is trained by g3_mlp_train (full-batch Adam,
+one kernel), and the parameters are written as JSON.
+
+Usage:
+  python -m paper_2012_10026_gb300.train_controller --scales 20 21 22 23 24 \\
+      --seeds 11 12 13 14 15 --roots 12 --out paper_2012_10026_gb300/mlp_params.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+import paper_2012_10026_gb300 as g3  # noqa: E402
+
+LOSS_WEIGHTS = [1.0, 0.05, 0.05, 0.05]
+
+
+def init_params(seed: int) -> np.ndarray:
+    """He-uniform weights, zero biases (layout W1, b1, W2, b2)."""
+    rng = np.random.default_rng(seed)
+    w1 = rng.uniform(-1, 1, (32, 12)) * math.sqrt(6.0 / 12)
+    w2 = rng.uniform(-1, 1, (4, 32)) * math.sqrt(6.0 / 32)
+    return np.concatenate([w1.ravel(), np.zeros(32), w2.ravel(), np.zeros(4)]).astype(np.float32)
+
+
+def collect(scale: int, seed: int, nroots: int, root_seed: int, device="cuda"):
+    """Recorded levels of nroots searches on one graph -> (rows, n_bfs)."""
+    import torch
+    import graphgen
+    n = 1 << scale
+    src, dst = graphgen.kronecker_edges_dev(scale, 16, seed=seed, device=device)
+    flags = graphgen.nonisolated_flags_dev(src, dst, n).cpu().numpy()
+    roots = graphgen.pick_roots(flags, nroots, root_seed).tolist()
+    g = g3.g3_build_csr(src, dst, n)
+    del src, dst
+    g3.g3_rcm_relabel(g)
+    nb = g.info["n_bfs"]
+    parent = torch.empty(n, dtype=torch.int32, device=device)
+    level = torch.empty(n, dtype=torch.int32, device=device)
+    opts = g3.opts(record_both=1, timing=1)
+    rows = []
+    for r in roots:
+        st = g3.g3_bfs(g, r, parent, level, opts, max_stats=256)
+        rows.append(st)
+    g.free()
+    return rows, nb
+
+
+def dataset(runs):
+    """(X, Y, meta) from [(rows_of_one_search, n_bfs)]: one sample per level >= 1."""
+    xs, ys, meta = [], [], []
+    for st, nb in runs:
+        if not st:
+            continue
+        x = g3.g3_mlp_features(st, nb).cpu().numpy()
+        for a, row in zip(st, x):
+            if a["level"] == 0 or a["t_td_ms"] <= 0 or a["t_bu_ms"] <= 0:
+                continue
+            xs.append(row)
+            ys.append([math.log(a["t_bu_ms"] / a["t_td_ms"]), math.log2(a["best_t1"]),
+                       math.log2(a["best_t2"]), math.log2(a["best_t3"])])
+            meta.append((a["t_td_ms"], a["t_bu_ms"], a["dir"]))
+    return (np.array(xs, np.float32), np.array(ys, np.float32), meta)
+
+
+def regret(meta, choice_bu):
+    """sum over levels of t(chosen direction) - min(t_TD, t_BU), in ms."""
+    return float(sum((tb if c else tt) - min(tt, tb) for (tt, tb, _), c in zip(meta, choice_bu)))
+
+
+def train(X, Y, steps=3000, lr=1e-2, seed=0, device="cuda"):
+    import torch
+    p = torch.from_numpy(init_params(seed)).to(device)
+    w = torch.tensor(LOSS_WEIGHTS, dtype=torch.float32, device=device)
+    xt = torch.from_numpy(X).to(device)
+    yt = torch.from_numpy(Y).to(device)
+    losses = g3.g3_mlp_train(p, xt, yt, steps=steps, lr=lr, w=w).cpu().numpy()
+    return p, losses
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--scales", type=int, nargs="+", default=[20, 21, 22, 23, 24])
+    ap.add_argument("--seeds", type=int, nargs="+", default=[11, 12, 13, 14, 15])
+    ap.add_argument("--roots", type=int, default=12)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--lr", type=float, default=1e-2)
+    ap.add_argument("--out", default=os.path.join(HERE, "mlp_params.json"))
+    ap.add_argument("--eval-scale", type=int, default=0,
+                    help="held-out graph (seed 2) on which to compare the controllers")
+    ap.add_argument("--eval-roots", type=int, default=8)
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    runs = []
+    for scale, seed in zip(args.scales, args.seeds):
+        rows, nb = collect(scale, seed, args.roots, seed + 100)
+        runs += [(st, nb) for st in rows]
+    X, Y, meta = dataset(runs)
+    t1 = time.time()
+    p, losses = train(X, Y, args.steps, args.lr)
+    out = g3.g3_mlp_forward(p, torch.from_numpy(X).cuda()).cpu().numpy()
+    learned_bu = out[:, 0] < 0
+    heur_bu = np.array([d == 1 for (_, _, d) in meta])
+    best_bu = np.array([tb < tt for (tt, tb, _) in meta])
+    summary = {
+        "params": [float(v) for v in p.cpu().numpy()],
+        "layout": "W1[32][12], b1[32], W2[4][32], b2[4]",
+        "scales": args.scales, "seeds": args.seeds, "roots_per_graph": args.roots,
+        "samples": int(len(X)), "steps": args.steps, "lr": args.lr,
+        "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+        "direction_accuracy_learned": float(np.mean(learned_bu == best_bu)),
+        "direction_accuracy_heuristic": float(np.mean(heur_bu == best_bu)),
+        "train_regret_ms_learned": regret(meta, learned_bu),
+        "train_regret_ms_heuristic": regret(meta, heur_bu),
+        "collect_s": t1 - t0, "train_s": time.time() - t1,
+    }
+    if args.eval_scale:
+        # held-out graph: per-level times of both directions under the
+        # heuristic's path; regret of each controller's choices on it
+        rows, nb = collect(args.eval_scale, 1, args.eval_roots, 2)
+        Xe, Ye, me = dataset([(st, nb) for st in rows])
+        oe = g3.g3_mlp_forward(p, torch.from_numpy(Xe).cuda()).cpu().numpy()
+        summary["eval"] = {
+            "scale": args.eval_scale, "roots": args.eval_roots, "levels": int(len(Xe)),
+            "regret_ms_learned": regret(me, oe[:, 0] < 0),
+            "regret_ms_heuristic": regret(me, [d == 1 for (_, _, d) in me]),
+            "best_total_ms": float(sum(min(tt, tb) for (tt, tb, _) in me)),
+        }
+    with open(args.out, "w") as f:
+        json.dump(summary, f, indent=1)
+    print(json.dumps({k: v for k, v in summary.items() if k != "params"}))
+
+
+if __name__ == "__main__":
+    main()

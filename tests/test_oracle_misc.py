@@ -134,7 +134,7 @@ def test_adam_fits_linear_target():
 def test_features_closed_form():
     f = mlp.features(n_f=3, m_f=7, n_u=15, m_u=31, id_min=2, id_max=10, n=16, level=4,
                      prev_dir=1, hist4=[1, 2, 0, 0])
-    assert np.allclose(f, [2, 3, 4, 5, 0.5, -2, 0.125, 1, 1 / 3, 2 / 3, 0, 0])
+    assert np.allclose(f, [2, 3, 4, 5, 0.5, -2, np.log2(17), 1, 1 / 3, 2 / 3, 0, 0])
 
 
 # ---------------------------------------------------------------- metrics
