@@ -91,6 +91,7 @@ struct LevelLog {
 struct Bufs {
   int32_t* q[2];
   uint32_t* f[2];
+  const int32_t* o2n;  // old_of_new (parents are stored as original IDs), or NULL
 };
 
 struct g3_bfs_ws {
@@ -265,7 +266,7 @@ __global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, in
     return;
   }
   visited[r >> 5] |= 1u << (r & 31);
-  pl[r] = make_int2(r, 0);
+  pl[r] = make_int2(root, 0);  // parents are kept as original IDs
   q[0] = r;
   long long d = off[r + 1] - off[r];
   c->nf = 1;
@@ -289,7 +290,12 @@ struct TdArgs {
   int32_t lnext;
   int32_t* qnext;
   Ctrl* c;
+  const int32_t* o2n;
 };
+
+__device__ __forceinline__ int32_t orig_of(const int32_t* o2n, int32_t v) {
+  return o2n ? __ldg(&o2n[v]) : v;
+}
 
 // Per-warp staging of the next queue in shared memory: claimed vertices are
 // compacted into the warp's buffer with a ballot and written to the global
@@ -337,7 +343,7 @@ __device__ __forceinline__ void td_visit(const TdArgs& a, WarpQueue& q, StatAcc&
                                          int32_t w, int32_t v) {
   bool claim = has && td_claim(a.visited, w);
   if (claim) {
-    a.pl[w] = make_int2(v, a.lnext);
+    a.pl[w] = make_int2(v, a.lnext);  // v: the parent's original ID
     acc.add_vertex(w, a.off[w + 1] - a.off[w]);
   }
   wq_push(q, claim, w, a.qnext, &a.c->q_len);
@@ -350,14 +356,15 @@ __device__ __forceinline__ void td_row_vec4(const TdArgs& a, WarpQueue& q, StatA
                                             int32_t v, int64_t b, int64_t e, int64_t t,
                                             int64_t nthr, int64_t steps) {
   const int64_t a0 = b & ~3ll;
+  const int32_t vo = orig_of(a.o2n, v);
   for (int64_t s = 0; s < steps; ++s) {
     const int64_t j = a0 + 4 * (t + s * nthr);
     int4 x = make_int4(0, 0, 0, 0);
     if (j < e) x = *reinterpret_cast<const int4*>(a.col + j);
-    td_visit(a, q, acc, j + 0 >= b && j + 0 < e, x.x, v);
-    td_visit(a, q, acc, j + 1 >= b && j + 1 < e, x.y, v);
-    td_visit(a, q, acc, j + 2 >= b && j + 2 < e, x.z, v);
-    td_visit(a, q, acc, j + 3 >= b && j + 3 < e, x.w, v);
+    td_visit(a, q, acc, j + 0 >= b && j + 0 < e, x.x, vo);
+    td_visit(a, q, acc, j + 1 >= b && j + 1 < e, x.y, vo);
+    td_visit(a, q, acc, j + 2 >= b && j + 2 < e, x.z, vo);
+    td_visit(a, q, acc, j + 3 >= b && j + 3 < e, x.w, vo);
   }
 }
 
@@ -369,7 +376,7 @@ __device__ __forceinline__ void td_row_vec4(const TdArgs& a, WarpQueue& q, StatA
 
 __device__ __forceinline__ TdArgs td_args(const int64_t* off, const int32_t* col,
                                           uint32_t* visited, int2* pl, const Bufs& B, Ctrl* c) {
-  return TdArgs{off, col, visited, pl, c->level + 1, (c->qsel ? B.q[0] : B.q[1]), c};
+  return TdArgs{off, col, visited, pl, c->level + 1, (c->qsel ? B.q[0] : B.q[1]), c, B.o2n};
 }
 
 // Thread per frontier vertex: degree < t1 expanded here, larger degrees
@@ -406,10 +413,11 @@ __global__ void __launch_bounds__(256) td_front(const int64_t* __restrict__ off,
     }
     const int cnt = small ? (int)d : 0;
     const int maxc = __reduce_max_sync(0xffffffffu, cnt);
+    const int32_t vo = cnt ? orig_of(a.o2n, v) : 0;
     for (int k = 0; k < maxc; ++k) {
       bool has = k < cnt;
       int32_t w = has ? col[b + k] : 0;
-      td_visit(a, wq, acc, has, w, v);
+      td_visit(a, wq, acc, has, w, vo);
     }
   }
   wq_flush(wq, a.qnext, &c->q_len);
@@ -458,13 +466,14 @@ __global__ void __launch_bounds__(256) td_bins(const int64_t* __restrict__ off,
       for (int64_t base = j0; base < j1; base += 32) {
         const int64_t j = base + lane;
         const bool act = j < j1;
-        int32_t v = 0, w = 0;
+        int32_t vo = 0, w = 0;
         if (act) {
           while (h + 1 < nh && goff[h + 1] <= j) ++h;
-          v = gbin[h];
+          const int32_t v = gbin[h];
           w = col[off[v] + (j - goff[h])];
+          vo = orig_of(a.o2n, v);
         }
-        td_visit(a, wq, acc, act, w, v);
+        td_visit(a, wq, acc, act, w, vo);
       }
     }
   }
@@ -502,6 +511,7 @@ __global__ void __launch_bounds__(256, 5) bu_pull(int32_t nb, int64_t nwords, ui
   const uint32_t* __restrict__ fcur = (c->fsel ? B.f[1] : B.f[0]);
   uint32_t* __restrict__ fnext = (c->fsel ? B.f[0] : B.f[1]);
   const int32_t lnext = c->level + 1;
+  const int32_t* __restrict__ o2n = B.o2n;
   StatAcc acc;
   acc.init();
   const int lane = threadIdx.x & 31;
@@ -573,11 +583,11 @@ __global__ void __launch_bounds__(256, 5) bu_pull(int32_t nb, int64_t nwords, ui
     const uint32_t n0 = __ballot_sync(0xffffffffu, p0 >= 0);
     const uint32_t n1 = __ballot_sync(0xffffffffu, p1 >= 0);
     if (p0 >= 0) {
-      pl[v0] = make_int2(p0, lnext);
+      pl[v0] = make_int2(o2n ? __ldg(&o2n[p0]) : p0, lnext);
       acc.add_vertex((int32_t)v0, d0);
     }
     if (p1 >= 0) {
-      pl[v1] = make_int2(p1, lnext);
+      pl[v1] = make_int2(o2n ? __ldg(&o2n[p1]) : p1, lnext);
       acc.add_vertex((int32_t)v1, d1);
     }
     if (lane == 0) {
@@ -771,7 +781,7 @@ __global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
     const int32_t x = new_of_old ? new_of_old[v] : (int32_t)v;
     if (x < nb && ((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u)) {
       const int2 t = pl[x];
-      p = old_of_new ? old_of_new[t.x] : t.x;
+      p = t.x;
       l = t.y;
     }
     if (v == root) {
@@ -818,7 +828,7 @@ __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int
     int p[4], l[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      p[k] = r[k] ? (old_of_new ? __ldg(&old_of_new[t[k].x]) : t[k].x) : -1;
+      p[k] = r[k] ? t[k].x : -1;
       l[k] = t[k].y;
     }
     if ((root >> 2) == i) {
@@ -835,7 +845,7 @@ __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int
     const int32_t xv = new_of_old ? new_of_old[v] : (int32_t)v;
     if (xv < nb && ((__ldg(&visited[xv >> 5]) >> (xv & 31)) & 1u)) {
       const int2 t = pl[xv];
-      p = old_of_new ? old_of_new[t.x] : t.x;
+      p = t.x;
       l = t.y;
     }
     if (v == root) {
@@ -1206,7 +1216,9 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   g3_bfs_ws* ws = g->ws;
   const int32_t nb = ws->nb;
   Ctrl* h = ws->h_ctrl;
-  Launch S{g, ws, o, Bufs{{ws->qa, ws->qb}, {ws->fa, ws->fb}}, (int64_t)ws->nb + 4};
+  Launch S{g, ws, o,
+           Bufs{{ws->qa, ws->qb}, {ws->fa, ws->fb}, g->relabelled ? g->old_of_new : nullptr},
+           (int64_t)ws->nb + 4};
   const bool host_driven = o->timing || o->record_both;
   if (stats && max_stats > 0) memset(stats, 0, sizeof(g3_level_stats) * (size_t)max_stats);
 
