@@ -63,6 +63,14 @@ def parse_args():
     ap.add_argument("--bu-reverse", type=int, default=1,
                     help="bottom-up scans rows from the highest label (degree-aware order)")
     ap.add_argument("--stats-out", default="")
+    ap.add_argument("--workload", choices=["kron", "msbfs", "batch"], default="kron",
+                    help="kron: the single-root headline; msbfs: bit-sliced multi-source "
+                         "BFS on a Chung-Lu graph; batch: many small graphs in one launch")
+    ap.add_argument("--ms-log2n", type=int, default=24, help="msbfs: Chung-Lu 2^k vertices")
+    ap.add_argument("--ms-roots", type=int, default=256, help="msbfs: sources (64 per launch)")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--batch-warp-max-n", type=int, default=-1,
+                    help="batch: warp-per-graph size limit (-1: the library default)")
     return ap.parse_args()
 
 
@@ -461,10 +469,350 @@ def gpu_arm(args, rank, world):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------- secondary workloads
+def _common_line(args, world, metric, value, unit, times_ms, config):
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sum(times_ms) / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config}
+
+
+def _setup_dist(args):
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return local, world, dist
+
+
+def _max_over_ranks(dist, x):
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _ms_oracle_worker(log2n, roots, q):
+    try:
+        import numpy as np
+        import graphgen
+        import oracle
+        n = 1 << log2n
+        src, dst = graphgen.chunglu_edges(n)
+        off, col = oracle.build_csr(src, dst, n)
+        runs = []
+        for r in roots:
+            t0 = time.perf_counter()
+            _, lv = oracle.bfs(off, col, int(r))
+            dt = time.perf_counter() - t0
+            runs.append((int(r), int((lv[src] >= 0).sum()), dt))
+        q.put({"ok": True, "runs": runs})
+    except Exception as e:  # reported in the JSON line
+        q.put({"ok": False, "error": repr(e)})
+
+
+def msbfs_arm(args, rank, world):
+    """Bit-sliced multi-source BFS: Chung-Lu 2^24 (power law 2.1, mean degree
+    20, degree cap 2^16), RCM-relabelled, 256 sources run as 4 launches of 64.
+    Metric: aggregate GTEPS = sum over sources of m_s / sum of launch times."""
+    import numpy as np
+    import torch
+    import graphgen
+    import paper_2012_10026_gb300 as g3
+
+    local, world, dist = _setup_dist(args)
+    n = 1 << args.ms_log2n
+    src, dst = graphgen.chunglu_edges_dev(n)
+    flags = graphgen.nonisolated_flags_dev(src, dst, n).cpu().numpy()
+    roots = graphgen.pick_roots(flags, args.ms_roots, args.root_seed).tolist()
+    oracle_proc = None
+    if rank == 0 and args.cpu_baseline:
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        p = ctx.Process(target=_ms_oracle_worker, args=(args.ms_log2n, roots[:2], q))
+        p.start()
+        oracle_proc = (p, q)
+    g = g3.g3_build_csr(src, dst, n)
+    g3.g3_rcm_relabel(g)
+    info = g.info
+    cnt = torch.bincount(src.long(), minlength=n)  # generated tuples per first endpoint
+    del src, dst
+    torch.cuda.empty_cache()
+    batches = [roots[i:i + 64] for i in range(0, len(roots), 64)]
+    lv = torch.empty((64, n), dtype=torch.int8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # m_s per source (bookkeeping, untimed)
+    m_s = []
+    for b in batches:
+        g3.g3_msbfs(g, b, lv[:len(b)])
+        for i in range(len(b)):
+            m_s.append(int(cnt[lv[i] >= 0].sum().item()))
+    ev_s = torch.cuda.Event(enable_timing=True)
+    ev_e = torch.cuda.Event(enable_timing=True)
+
+    def step():
+        t = []
+        for b in batches:
+            flush.fill_(1)
+            ev_s.record()
+            g3.g3_msbfs(g, b, lv[:len(b)])
+            ev_e.record()
+            ev_e.synchronize()
+            t.append(ev_s.elapsed_time(ev_e))
+        return t
+
+    for _ in range(args.warmup):
+        step()
+    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_ms_rank{rank}.csv") \
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/g3_clocks_ms_{rank}.csv"
+    sampler = start_clock_sampler(clk_path)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = g3.kernel_launches()
+    times = []
+    for _ in range(args.steps):
+        times += step()
+    torch.cuda.synchronize()
+    launches = g3.kernel_launches() - l0
+    if dist:
+        dist.barrier()
+    clocks = stop_clock_sampler(sampler, clk_path, local)
+    tsum = _max_over_ranks(dist, sum(times))
+    value = world * args.steps * sum(m_s) / (tsum / 1e3) / 1e9
+    # the same sources, one plain g3_bfs each (heuristic controller)
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    plain_t = []
+    for r in roots:
+        flush.fill_(1)
+        ev_s.record()
+        g3.g3_bfs(g, r, parent, level)
+        ev_e.record()
+        ev_e.synchronize()
+        plain_t.append(ev_s.elapsed_time(ev_e))
+    # compulsory bytes per launch: the BFS-graph CSR read once, the per-vertex
+    # state words (vis, F, next: 3 x 8 B) written once, 64 B of levels per vertex
+    nb, nnz = info["n_bfs"], info["nnz"]
+    comp = 8 * (nb + 1) + 4 * nnz + 24 * nb + 64 * n
+    avg_ms = sum(times) / len(times)
+    peak, peak_kind = load_peaks()
+    cpu = None
+    if oracle_proc is not None:
+        d = finish_oracle_leg(*oracle_proc, timeout=args.cpu_timeout)
+        if d and d.get("ok"):
+            runs = d["runs"]
+            cpu = {"value": sum(x[1] for x in runs) / sum(x[2] for x in runs) / 1e9,
+                   "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "sample": f"{len(runs)} of the {len(roots)} sources, serial oracle BFS on "
+                             f"the oracle's CSR (generation and CSR untimed)"}
+        else:
+            cpu = {"value": None, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "sample": "oracle leg did not finish: " + (d or {}).get("error", "timeout")}
+    if rank == 0:
+        line = _common_line(args, world, f"aggregate GTEPS, bit-sliced MS-BFS, {len(roots)} "
+                            f"sources as {len(batches)} launches of 64, Chung-Lu 2^"
+                            f"{args.ms_log2n}", value, "GTEPS", times,
+                            {"workload": f"chunglu_2^{args.ms_log2n}_g2.1_d20_cap65536_rcm_"
+                                         f"{len(roots)}sources", "sources_per_launch": 64,
+                             "l2": "256 MB write between launches (L2 flush)",
+                             "parallelism": "replicas"})
+        line.update({
+            "roofline": {"bound": "hbm", "kernel": "g3_msbfs launch (all its kernels)",
+                         "achieved": comp / (avg_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": comp / (avg_ms / 1e3) / 1e9 / peak, "traffic": None,
+                         "peak_kind": peak_kind, "bytes_per_launch": comp,
+                         "bytes_model": "compulsory: CSR once + 3x8 B state + 64 B levels "
+                                        "per vertex (a lower bound; levels re-read state)"},
+            "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks,
+            "e2e": None,
+            "graph": {"n": info["n"], "n_plus": info["n_plus"], "nnz": info["nnz"],
+                      "max_degree": info["max_degree"]},
+            "per_launch_ms": {"min": min(times), "median": statistics.median(times),
+                              "max": max(times)},
+            "plain_g3_bfs_same_sources": {
+                "aggregate_gteps": sum(m_s) / (sum(plain_t) / 1e3) / 1e9,
+                "harmonic_gteps": harmonic_gteps(m_s, plain_t),
+                "total_ms": sum(plain_t)},
+        })
+        print(json.dumps(line), flush=True)
+    g.free()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _batch_oracle_worker(specs, q):
+    try:
+        import graphgen
+        import oracle
+        runs = []
+        for scale, gseed, root in specs:
+            src, dst = graphgen.kronecker_edges(scale, 16, seed=gseed)
+            off, col = oracle.build_csr(src, dst, 1 << scale)
+            t0 = time.perf_counter()
+            _, lv = oracle.bfs(off, col, int(root))
+            dt = time.perf_counter() - t0
+            runs.append((int((lv[src] >= 0).sum()), dt))
+        q.put({"ok": True, "runs": runs})
+    except Exception as e:
+        q.put({"ok": False, "error": repr(e)})
+
+
+def batch_arm(args, rank, world):
+    """Many small Kronecker graphs (SCALE ~ U{8..14}, edge factor 16, graph g
+    seeded 5*2^20+g), each RCM-relabelled with one random non-isolated root,
+    packed and searched in one captured persistent launch.
+    Metric: GTEPS = sum over graphs of m_g / launch time."""
+    import numpy as np
+    import torch
+    import graphgen
+    import paper_2012_10026_gb300 as g3
+
+    local, world, dist = _setup_dist(args)
+    specs = graphgen.small_graph_specs(args.batch_graphs, seed=5)
+    graphs, roots_u, m_g, voff, srcs = [], [], [], [0], []
+    t0 = time.perf_counter()
+    for i, (scale, gseed) in enumerate(specs):
+        n = 1 << scale
+        s, d = graphgen.kronecker_edges_dev(scale, 16, seed=gseed)
+        flags = graphgen.nonisolated_flags_dev(s, d, n).cpu().numpy()
+        r = int(graphgen.pick_roots(flags, 1, seed=gseed)[0])
+        g = g3.g3_build_csr(s, d, n)
+        g3.g3_rcm_relabel(g)
+        graphs.append(g)
+        roots_u.append(voff[-1] + r)
+        srcs.append(s.long() + voff[-1])
+        voff.append(voff[-1] + n)
+    b = g3.g3_batch_pack(graphs)
+    for g in graphs:
+        g.free()
+    setup_s = time.perf_counter() - t0
+    N = voff[-1]
+    oracle_proc = None
+    if rank == 0 and args.cpu_baseline:
+        sample = [(specs[i][0], specs[i][1], roots_u[i] - voff[i]) for i in range(0, len(specs), 16)]
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        p = ctx.Process(target=_batch_oracle_worker, args=(sample, q))
+        p.start()
+        oracle_proc = (p, q, len(sample))
+    roots = torch.tensor(roots_u, dtype=torch.int32, device="cuda")
+    parent = torch.empty(N, dtype=torch.int32, device="cuda")
+    level = torch.empty(N, dtype=torch.int32, device="cuda")
+    o = g3.batch_opts() if args.batch_warp_max_n < 0 else \
+        g3.batch_opts(warp_max_n=args.batch_warp_max_n)
+    g3.g3_bfs_batch(b, roots, parent, level, o)
+    src_all = torch.cat(srcs)
+    del srcs
+    m_total = int((level[src_all] >= 0).sum().item())
+    del src_all
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev_s = torch.cuda.Event(enable_timing=True)
+    ev_e = torch.cuda.Event(enable_timing=True)
+
+    def step():
+        flush.fill_(1)
+        ev_s.record()
+        g3.g3_bfs_batch(b, roots, parent, level, o, timed=False)
+        ev_e.record()
+        ev_e.synchronize()
+        return ev_s.elapsed_time(ev_e)
+
+    for _ in range(args.warmup):
+        step()
+    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv") \
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/g3_clocks_b_{rank}.csv"
+    sampler = start_clock_sampler(clk_path)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = g3.kernel_launches()
+    times = [step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    launches = g3.kernel_launches() - l0
+    if dist:
+        dist.barrier()
+    clocks = stop_clock_sampler(sampler, clk_path, local)
+    tsum = _max_over_ranks(dist, sum(times))
+    value = world * args.steps * m_total / (tsum / 1e3) / 1e9
+    # end to end: roots from pinned host memory in, parent/level to pinned host out
+    e2e = None
+    if not args.no_e2e:
+        h_roots = roots.cpu().pin_memory()
+        hp = torch.empty(N, dtype=torch.int32).pin_memory()
+        hl = torch.empty(N, dtype=torch.int32).pin_memory()
+        et = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            s0 = time.perf_counter()
+            roots.copy_(h_roots, non_blocking=True)
+            g3.g3_bfs_batch(b, roots, parent, level, o, timed=False)
+            hp.copy_(parent, non_blocking=True)
+            hl.copy_(level, non_blocking=True)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                et.append((time.perf_counter() - s0) * 1e3)
+        e2e = {"value": m_total / (sum(et) / len(et) / 1e3) / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": len(roots_u) * 4, "d2h_bytes_per_step": 2 * N * 4}
+    info = b.info
+    comp = 8 * (N + 1) + 4 * info["nnz"] + 8 * N + 4 * N
+    avg_ms = sum(times) / len(times)
+    peak, peak_kind = load_peaks()
+    cpu = None
+    if oracle_proc is not None:
+        p, q, ns = oracle_proc
+        d = finish_oracle_leg(p, q, timeout=args.cpu_timeout)
+        if d and d.get("ok"):
+            runs = d["runs"]
+            cpu = {"value": sum(x[0] for x in runs) / sum(x[1] for x in runs) / 1e9,
+                   "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "sample": f"{ns} of the {len(specs)} graphs (every 16th), serial oracle "
+                             f"BFS from the same root (generation and CSR untimed)"}
+        else:
+            cpu = {"value": None, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "sample": "oracle leg did not finish: " + (d or {}).get("error", "timeout")}
+    if rank == 0:
+        line = _common_line(args, world, f"GTEPS, {len(specs)} small Kronecker graphs "
+                            "(SCALE 8-14) in one captured launch", value, "GTEPS", times,
+                            {"workload": f"kronecker_batch{len(specs)}_scale8-14_ef16_rcm_1root",
+                             "warp_max_n": o.warp_max_n,
+                             "l2": "256 MB write between launches (L2 flush)",
+                             "parallelism": "replicas"})
+        line.update({
+            "roofline": {"bound": "hbm", "kernel": "batch_bfs (warp- and CTA-group launches)",
+                         "achieved": comp / (avg_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": comp / (avg_ms / 1e3) / 1e9 / peak, "traffic": None,
+                         "peak_kind": peak_kind, "bytes_per_launch": comp,
+                         "bytes_model": "compulsory: union CSR once + parent/level written + "
+                                        "label map read once"},
+            "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
+            "batch": {"graphs": len(specs), "N": N, "nnz": info["nnz"], "m_total": m_total,
+                      "setup_s": setup_s},
+            "per_launch_ms": {"min": min(times), "median": statistics.median(times),
+                              "max": max(times)},
+        })
+        print(json.dumps(line), flush=True)
+    b.free()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.workload == "msbfs" and args.impl != "reference":
+        return msbfs_arm(args, rank, world)
+    if args.workload == "batch" and args.impl != "reference":
+        return batch_arm(args, rank, world)
     if args.impl == "reference":
         reference_arm(args, rank, world)
     else:

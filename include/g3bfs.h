@@ -197,6 +197,75 @@ g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, int32_t* pa
                  int32_t* level, g3_level_stats* stats, int32_t max_stats,
                  int32_t* n_levels, void* stream);
 
+/* --------------------------------------------------- multi-source BFS */
+
+/* Up to 64 searches in one pass, one bit per source in a uint64 per vertex
+ * (the paper runs its 64 evaluation roots one after the other, Sec. 4; this
+ * batched form has no counterpart there). Per level the frontier is either
+ * pushed (every frontier vertex ORs its source bits into its neighbours,
+ * the top-down analogue of Algorithm 1) or pulled (every vertex not reached
+ * by all sources ORs its neighbours' frontier words, with an early exit once
+ * all missing sources are found, the bottom-up analogue of Algorithm 2). */
+typedef struct {
+  int32_t push_alpha;     /* pull a level when (sum of frontier degrees) *
+                             push_alpha > nnz, else push (14) */
+  int32_t pull_warp_deg;  /* pull: vertices of at least this degree are scanned
+                             by a whole warp, smaller ones by one thread (256) */
+  int32_t reserved[6];
+} g3_msbfs_opts;
+
+void g3_msbfs_opts_default(g3_msbfs_opts* o);
+
+/* BFS from roots[0..k) (host array, original IDs, 1 <= k <= 64; repeats
+ * allowed) on the graph's current CSR.
+ *   level    : device pointer, k x n int8, row s = hop distances from roots[s]
+ *              in original IDs, -1 where unreachable (isolated roots reach
+ *              only themselves).
+ *   n_levels : (nullable) number of levels run.
+ *   ms       : (nullable) time of the call on the device, CUDA events.
+ * The first call on a graph allocates its workspace (about 100 bytes per
+ * vertex). Synchronises `stream` once per level and before returning.
+ * Errors: G3_EINVAL, G3_ERANGE (a level above 126 does not fit int8),
+ * G3_ENOMEM, G3_ECUDA. */
+g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k, const g3_msbfs_opts* opts,
+                   int8_t* level, int32_t* n_levels, float* ms, void* stream);
+
+/* ------------------------------------------------- batched small graphs */
+
+/* Many small graphs searched in one persistent, CUDA-graph-captured launch
+ * (no counterpart in the paper). */
+typedef struct g3_batch g3_batch;
+
+typedef struct {
+  int32_t warp_max_n;  /* graphs with at most this many BFS vertices are searched
+                          by one warp, larger ones by a whole CTA (1024; at most
+                          2048 are ever given to a warp) */
+  int32_t reserved[7];
+} g3_batch_opts;
+
+void g3_batch_opts_default(g3_batch_opts* o);
+
+/* Packs G graphs, each built by g3_build_csr and relabelled by g3_rcm_relabel,
+ * into one union: graph g keeps the contiguous ID range [voff[g], voff[g+1])
+ * (voff = prefix sums of the graphs' n in the given order) for original IDs and
+ * labels alike. The graphs are read, not taken over: the caller may free them
+ * afterwards. Each graph may have at most 16384 non-isolated vertices.
+ * Synchronises. Errors: G3_EINVAL, G3_ENOMEM, G3_ECUDA. */
+g3_status g3_batch_pack(g3_graph* const* graphs, int32_t G, void* stream, g3_batch** out);
+
+g3_status g3_batch_info_get(const g3_batch* b, int32_t* G, int64_t* N, int64_t* nnz);
+
+/* One BFS per graph: roots (device, G entries, union original IDs, root g in
+ * graph g's range), parent and level (device, N entries each, union original
+ * IDs; a root outside its graph's range leaves that graph all -1). The first
+ * call with a given (roots, parent, level, warp_max_n) captures the launch into
+ * a CUDA graph; later calls only launch it. ms (nullable): device time of the
+ * launch, which then synchronises; otherwise the call is asynchronous. */
+g3_status g3_bfs_batch(g3_batch* b, const int32_t* roots, const g3_batch_opts* opts,
+                       int32_t* parent, int32_t* level, float* ms, void* stream);
+
+void g3_batch_free(g3_batch* b);
+
 /* --------------------------------------------------- learned controller */
 
 /* The learned direction / binning controller (the paper has no learned

@@ -63,6 +63,15 @@ class g3_level_stats(ctypes.Structure):
         return d
 
 
+class g3_msbfs_opts(ctypes.Structure):
+    _fields_ = [("push_alpha", ctypes.c_int32), ("pull_warp_deg", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class g3_batch_opts(ctypes.Structure):
+    _fields_ = [("warp_max_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 
@@ -85,6 +94,20 @@ _SIGS = {
                               ctypes.POINTER(ctypes.c_int32), _vp]),
     "g3_bfs_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
                                       _vp]),
+    "g3_msbfs_opts_default": (None, [ctypes.POINTER(g3_msbfs_opts)]),
+    "g3_msbfs": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                ctypes.POINTER(g3_msbfs_opts), _vp,
+                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
+                                _vp]),
+    "g3_batch_opts_default": (None, [ctypes.POINTER(g3_batch_opts)]),
+    "g3_batch_pack": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, _vp,
+                                     ctypes.POINTER(_vp)]),
+    "g3_batch_info_get": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int64)]),
+    "g3_bfs_batch": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(g3_batch_opts), _vp, _vp,
+                                    ctypes.POINTER(ctypes.c_float), _vp]),
+    "g3_batch_free": (None, [_vp]),
     "g3_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp]),
     "g3_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp]),
     "g3_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
@@ -116,6 +139,11 @@ def declared_symbols():
     import re
     txt = open(HEADER).read()
     return sorted(set(re.findall(r"\b(g3_[a-z0-9_]+)\s*\(", txt)) - {"g3_graph"})
+
+
+def kernel_launches() -> int:
+    """Kernels this library has launched so far (graph nodes included)."""
+    return int(lib().g3_kernel_launches())
 
 
 def _check(st, where):
@@ -206,6 +234,85 @@ def g3_bfs_noalloc(off, col, n: int, root: int, parent, level, stream=None):
     device must not overlap on the GPU."""
     _check(lib().g3_bfs_noalloc(_ptr(off), _ptr(col), int(n), int(root), _ptr(parent),
                                 _ptr(level), _stream(stream)), "g3_bfs_noalloc")
+
+
+def msbfs_opts(**kw) -> g3_msbfs_opts:
+    o = g3_msbfs_opts()
+    lib().g3_msbfs_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def g3_msbfs(graph: "Graph", roots, level, options: g3_msbfs_opts | None = None, stream=None):
+    """Bit-sliced BFS from up to 64 roots (original IDs) into level, a k x n
+    int8 device tensor. Returns (levels run, device ms)."""
+    roots = [int(r) for r in roots]
+    arr = (ctypes.c_int32 * len(roots))(*roots)
+    nl = ctypes.c_int32(0)
+    ms = ctypes.c_float(0.0)
+    _check(lib().g3_msbfs(graph.handle, arr, len(roots),
+                          ctypes.byref(options) if options is not None else None,
+                          _ptr(level), ctypes.byref(nl), ctypes.byref(ms), _stream(stream)),
+           "g3_msbfs")
+    return nl.value, ms.value
+
+
+class Batch:
+    """Owner of a g3_batch* (many small relabelled graphs packed together)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def free(self):
+        if self.handle and self.handle.value:
+            import torch
+            torch.cuda.synchronize()
+            lib().g3_batch_free(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self.handle and self.handle.value:
+                lib().g3_batch_free(self.handle)
+        except Exception:
+            pass
+
+    @property
+    def info(self):
+        G = ctypes.c_int32()
+        N = ctypes.c_int64()
+        E = ctypes.c_int64()
+        _check(lib().g3_batch_info_get(self.handle, ctypes.byref(G), ctypes.byref(N),
+                                       ctypes.byref(E)), "g3_batch_info_get")
+        return {"G": G.value, "N": N.value, "nnz": E.value}
+
+
+def batch_opts(**kw) -> g3_batch_opts:
+    o = g3_batch_opts()
+    lib().g3_batch_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def g3_batch_pack(graphs, stream=None) -> Batch:
+    arr = (_vp * len(graphs))(*[g.handle.value for g in graphs])
+    b = ctypes.c_void_p()
+    _check(lib().g3_batch_pack(arr, len(graphs), _stream(stream), ctypes.byref(b)),
+           "g3_batch_pack")
+    return Batch(b)
+
+
+def g3_bfs_batch(batch: Batch, roots, parent, level, options: g3_batch_opts | None = None,
+                 timed: bool = True, stream=None):
+    """One BFS per packed graph; returns the device ms of the launch (timed)."""
+    ms = ctypes.c_float(0.0)
+    _check(lib().g3_bfs_batch(batch.handle, _ptr(roots),
+                              ctypes.byref(options) if options is not None else None,
+                              _ptr(parent), _ptr(level), ctypes.byref(ms) if timed else None,
+                              _stream(stream)), "g3_bfs_batch")
+    return ms.value
 
 
 def _optr(t):

@@ -71,6 +71,7 @@ g3_status g3_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cuda
 
 // ---------------------------------------------------------------- graph
 struct g3_bfs_ws;  // BFS workspace (bfs.cu)
+struct g3_ms_ws;   // multi-source BFS workspace (msbfs.cu)
 
 struct g3_graph {
   int32_t n;            // vertices of the input
@@ -84,9 +85,11 @@ struct g3_graph {
   int32_t* old_of_new;  // [n] after relabel
   int32_t* new_of_old;  // [n] after relabel
   g3_bfs_ws* ws;
+  g3_ms_ws* ms;
 };
 
 void g3_bfs_ws_free(g3_bfs_ws* ws);
+void g3_ms_ws_free(g3_ms_ws* ws);
 
 // ----------------------------------------------------------- device utils
 __device__ __forceinline__ unsigned g3_lanemask_lt() {

@@ -1,0 +1,416 @@
+// Bit-sliced multi-source BFS: up to 64 searches at once, one bit per source
+// in a uint64 per vertex (the paper's method has no multi-source form; this
+// batches the roots of Sec. 4's 64-root evaluation into one pass).
+//
+// State per BFS-graph vertex v: vis[v] (sources that reached v), F[v] (sources
+// whose frontier contains v). Level L -> L+1 runs one of two kernels:
+//   push (small frontiers, the top-down analogue): every frontier vertex u
+//     ORs F[u] & ~vis[w] into N[w] of each neighbour w; the first toucher of w
+//     queues it; a finalize pass over the touched vertices keeps the new bits.
+//   pull (large frontiers, the bottom-up analogue): every vertex not yet
+//     reached by all sources ORs the frontier words of its neighbours, with an
+//     early exit once every missing source is found; vertices with degree >=
+//     pull_warp_deg are pulled by a whole warp (degree binning).
+// Levels are stored per vertex as a 64-byte row in label order and written to
+// level[s][original ID] (int8) by a shared-memory transpose at the end.
+#include <string.h>
+
+#include "g3_prims.cuh"
+
+struct g3_ms_ws {
+  int32_t nb;
+  uint64_t *vis, *fa, *fb, *nx;
+  int8_t* lv;        // [nb][64]
+  int32_t *qa, *qb;  // frontier queues
+  int32_t* heavy;    // pull: vertices pulled by a warp
+  unsigned long long* ctr;  // [0] next queue len, [1] next sum of degrees, [2] heavy len
+  unsigned long long* h_ctr;
+  int32_t* d_roots;
+  cudaEvent_t ev[2];
+};
+
+void g3_ms_ws_free(g3_ms_ws* w) {
+  if (!w) return;
+  void* all[] = {w->vis, w->fa, w->fb, w->nx, w->lv, w->qa, w->qb, w->heavy, w->ctr, w->d_roots};
+  for (void* p : all)
+    if (p) cudaFree(p);
+  if (w->h_ctr) cudaFreeHost(w->h_ctr);
+  for (int i = 0; i < 2; ++i)
+    if (w->ev[i]) cudaEventDestroy(w->ev[i]);
+  free(w);
+}
+
+static g3_status ms_ws_create(g3_graph* g, g3_ms_ws** out) {
+  g3_ms_ws* w = (g3_ms_ws*)calloc(1, sizeof(g3_ms_ws));
+  if (!w) return G3_ENOMEM;
+  w->nb = g->n_bfs;
+  const size_t nb1 = (size_t)g->n_bfs + 4;
+  struct {
+    void** p;
+    size_t bytes;
+  } req[] = {{(void**)&w->vis, nb1 * 8}, {(void**)&w->fa, nb1 * 8},   {(void**)&w->fb, nb1 * 8},
+             {(void**)&w->nx, nb1 * 8},  {(void**)&w->lv, nb1 * 64},  {(void**)&w->qa, nb1 * 4},
+             {(void**)&w->qb, nb1 * 4},  {(void**)&w->heavy, nb1 * 4}, {(void**)&w->ctr, 64},
+             {(void**)&w->d_roots, 64 * 4}};
+  for (auto& r : req) {
+    cudaError_t e = cudaMalloc(r.p, r.bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g3_set_error("g3_msbfs workspace: cudaMalloc(%zu): %s", r.bytes, cudaGetErrorString(e));
+      g3_ms_ws_free(w);
+      return G3_ENOMEM;
+    }
+  }
+  if (cudaMallocHost((void**)&w->h_ctr, 64) != cudaSuccess ||
+      cudaEventCreate(&w->ev[0]) != cudaSuccess || cudaEventCreate(&w->ev[1]) != cudaSuccess) {
+    cudaGetLastError();
+    g3_ms_ws_free(w);
+    return G3_ENOMEM;
+  }
+  *out = w;
+  return G3_OK;
+}
+
+// ---------------------------------------------------------------- kernels
+// Seeds F and vis with the roots (BFS-graph labels) and queues each seed
+// vertex once.
+__global__ void ms_seed(const int32_t* roots, int k, const int32_t* new_of_old, int32_t nb,
+                        uint64_t* vis, uint64_t* F, int8_t* lv, int32_t* q,
+                        unsigned long long* ctr, const int64_t* off) {
+  const int s = threadIdx.x;
+  if (s >= k) return;
+  const int32_t x = new_of_old ? new_of_old[roots[s]] : roots[s];
+  if (x < 0 || x >= nb) return;
+  const uint64_t old = atomicOr((unsigned long long*)&F[x], 1ull << s);
+  atomicOr((unsigned long long*)&vis[x], 1ull << s);
+  lv[(int64_t)x * 64 + s] = 0;
+  if (old == 0) {
+    const unsigned long long slot = atomicAdd(&ctr[0], 1ull);
+    q[slot] = x;
+    atomicAdd(&ctr[1], (unsigned long long)(off[x + 1] - off[x]));
+  }
+}
+
+// Push: N[w] |= F[u] & ~vis[w] for the edges of frontier vertices u, one warp
+// per frontier vertex; first touchers of w are queued in `touched`.
+__global__ void __launch_bounds__(256) ms_push(const int32_t* __restrict__ q, int64_t qlen,
+                                               const int64_t* __restrict__ off,
+                                               const int32_t* __restrict__ col,
+                                               const uint64_t* __restrict__ F,
+                                               const uint64_t* __restrict__ vis, uint64_t* N,
+                                               int32_t* touched, unsigned long long* tlen) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < qlen; i += nwarps) {
+    const int32_t u = q[i];
+    const uint64_t fu = F[u];
+    const int64_t b = off[u], e = off[u + 1];
+    for (int64_t j0 = b; j0 < e; j0 += 32) {
+      const int64_t j = j0 + lane;
+      bool first = false;
+      int32_t w = 0;
+      if (j < e) {
+        w = col[j];
+        const uint64_t m = fu & ~__ldcg((const unsigned long long*)&vis[w]);
+        if (m) {
+          const uint64_t o = atomicOr((unsigned long long*)&N[w], m);
+          first = (o == 0);
+        }
+      }
+      g3_warp_append(0xffffffffu, first, w, touched, tlen);
+    }
+  }
+}
+
+// Finalize after a push: keep N[w]'s bits not yet in vis[w] as the new
+// frontier word, record their levels, queue w when anything is new, clear N.
+__global__ void ms_push_finalize(const int32_t* __restrict__ touched, int64_t len,
+                                 uint64_t* N, uint64_t* vis, uint64_t* Fn, int8_t* lv,
+                                 int8_t lnext, int32_t* qn, const int64_t* __restrict__ off,
+                                 unsigned long long* ctr) {
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < len;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool want = false;
+    int32_t w = 0;
+    unsigned long long d = 0;
+    if (i < len) {
+      w = touched[i];
+      const uint64_t nw = N[w];
+      N[w] = 0;
+      const uint64_t nv = nw & ~vis[w];
+      Fn[w] = nv;
+      if (nv) {
+        vis[w] |= nv;
+        uint64_t bits = nv;
+        while (bits) {
+          const int s = __ffsll((long long)bits) - 1;
+          lv[(int64_t)w * 64 + s] = lnext;
+          bits &= bits - 1;
+        }
+        want = true;
+        d = (unsigned long long)(off[w + 1] - off[w]);
+      }
+    }
+    g3_warp_append(0xffffffffu, want, w, qn, &ctr[0]);
+    for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if ((threadIdx.x & 31) == 0 && d) atomicAdd(&ctr[1], d);
+  }
+}
+
+// Records v's new source bits at level lnext.
+__device__ __forceinline__ void ms_take(int32_t v, uint64_t nv, uint64_t* vis, uint64_t vv,
+                                        int8_t* lv, int8_t lnext) {
+  vis[v] = vv | nv;
+  uint64_t bits = nv;
+  while (bits) {
+    const int s = __ffsll((long long)bits) - 1;
+    lv[(int64_t)v * 64 + s] = lnext;
+    bits &= bits - 1;
+  }
+}
+
+// Pull: thread per vertex for degree < heavy_deg, else queued for ms_pull_heavy.
+__global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __restrict__ off,
+                                               const int32_t* __restrict__ col,
+                                               const uint64_t* __restrict__ F, uint64_t* vis,
+                                               uint64_t* Fn, int8_t* lv, int8_t lnext,
+                                               uint64_t full, int64_t heavy_deg,
+                                               int32_t* heavy, int32_t* qn,
+                                               unsigned long long* ctr) {
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nb;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    bool want = false, big = false;
+    unsigned long long d = 0;
+    if (v < nb) {
+      const uint64_t vv = vis[v];
+      uint64_t nv = 0;
+      if (vv != full) {
+        const int64_t b = off[v], e = off[v + 1];
+        if (e - b >= heavy_deg) {
+          big = true;
+        } else {
+          uint64_t acc = 0;
+          for (int64_t j = b; j < e && (acc | vv) != full; ++j) acc |= __ldg(&F[col[j]]);
+          nv = acc & ~vv;
+          if (nv) {
+            ms_take((int32_t)v, nv, vis, vv, lv, lnext);
+            want = true;
+            d = (unsigned long long)(e - b);
+          }
+        }
+      }
+      if (!big) Fn[v] = nv;
+    }
+    g3_warp_append(0xffffffffu, big, (int32_t)v, heavy, &ctr[2]);
+    g3_warp_append(0xffffffffu, want, (int32_t)v, qn, &ctr[0]);
+    for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if ((threadIdx.x & 31) == 0 && d) atomicAdd(&ctr[1], d);
+  }
+}
+
+// Pull for high-degree vertices: one warp per vertex, warp-OR of 32 frontier
+// words per step, early exit once every missing source is found.
+__global__ void __launch_bounds__(256) ms_pull_heavy(const int32_t* __restrict__ heavy,
+                                                     const unsigned long long* hlen,
+                                                     const int64_t* __restrict__ off,
+                                                     const int32_t* __restrict__ col,
+                                                     const uint64_t* __restrict__ F,
+                                                     uint64_t* vis, uint64_t* Fn, int8_t* lv,
+                                                     int8_t lnext, uint64_t full, int32_t* qn,
+                                                     unsigned long long* ctr) {
+  const int64_t len = (int64_t)*hlen;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < len; i += nwarps) {
+    const int32_t v = heavy[i];
+    const uint64_t vv = vis[v];
+    const int64_t b = off[v], e = off[v + 1];
+    uint64_t acc = 0;
+    for (int64_t j0 = b; j0 < e; j0 += 32) {
+      const int64_t j = j0 + lane;
+      uint64_t x = j < e ? __ldg(&F[col[j]]) : 0ull;
+      for (int o = 16; o; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
+      acc |= x;
+      if ((acc | vv) == full) break;
+    }
+    const uint64_t nv = acc & ~vv;
+    if (lane == 0) {
+      Fn[v] = nv;
+      if (nv) {
+        ms_take(v, nv, vis, vv, lv, lnext);
+        const unsigned long long slot = atomicAdd(&ctr[0], 1ull);
+        qn[slot] = v;
+        atomicAdd(&ctr[1], (unsigned long long)(e - b));
+      }
+    }
+  }
+}
+
+// level[s][o] for s < k and a tile of 64 original IDs: gather the 64-byte rows
+// of the tile's vertices into shared memory (valid where the source's bit is
+// set in vis), then write each source's 64 bytes contiguously.
+__global__ void __launch_bounds__(256) ms_out(int32_t n, int32_t nb, int k,
+                                              const int32_t* __restrict__ new_of_old,
+                                              const uint64_t* __restrict__ vis,
+                                              const int8_t* __restrict__ lv, int8_t* level) {
+  __shared__ int8_t tile[64][64 + 4];
+  __shared__ int32_t xs[64];
+  __shared__ uint64_t vm[64];
+  const int64_t ntiles = ((int64_t)n + 63) / 64;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t o0 = t * 64;
+    if (threadIdx.x < 64) {
+      const int64_t o = o0 + threadIdx.x;
+      int32_t x = -1;
+      if (o < n) x = new_of_old ? new_of_old[o] : (int32_t)o;
+      if (x >= nb) x = -1;
+      xs[threadIdx.x] = x;
+      vm[threadIdx.x] = x >= 0 ? vis[x] : 0ull;
+    }
+    __syncthreads();
+    {  // 256 threads x 16 bytes = the 64 x 64 tile
+      const int r = threadIdx.x >> 2, qd = threadIdx.x & 3;
+      const int32_t x = xs[r];
+      int4 val = make_int4(-1, -1, -1, -1);
+      if (x >= 0) val = *reinterpret_cast<const int4*>(lv + (int64_t)x * 64 + qd * 16);
+      const int8_t* vb = reinterpret_cast<const int8_t*>(&val);
+      const uint64_t m = vm[r];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int s = qd * 16 + j;
+        tile[r][s] = ((m >> s) & 1ull) ? vb[j] : (int8_t)-1;
+      }
+    }
+    __syncthreads();
+    // each (source, 4 consecutive IDs) pair is one 32-bit store
+    for (int idx = threadIdx.x; idx < k * 16; idx += blockDim.x) {
+      const int s = idx >> 4, c = idx & 15;
+      const int64_t o = o0 + 4 * c;
+      if (o + 3 < n) {
+        const uint32_t w = (uint32_t)(uint8_t)tile[4 * c][s] |
+                           ((uint32_t)(uint8_t)tile[4 * c + 1][s] << 8) |
+                           ((uint32_t)(uint8_t)tile[4 * c + 2][s] << 16) |
+                           ((uint32_t)(uint8_t)tile[4 * c + 3][s] << 24);
+        if (((uintptr_t)(level + (int64_t)s * n + o) & 3) == 0) {
+          *reinterpret_cast<uint32_t*>(level + (int64_t)s * n + o) = w;
+        } else {
+          for (int j = 0; j < 4; ++j) level[(int64_t)s * n + o + j] = tile[4 * c + j][s];
+        }
+      } else {
+        for (int j = 0; j < 4 && o + j < n; ++j) level[(int64_t)s * n + o + j] = tile[4 * c + j][s];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The roots themselves (also isolated roots, which are not in the BFS graph).
+__global__ void ms_roots_out(const int32_t* roots, int k, int32_t n, int8_t* level) {
+  const int s = threadIdx.x;
+  if (s < k) level[(int64_t)s * n + roots[s]] = 0;
+}
+
+// ------------------------------------------------------------------ host
+extern "C" void g3_msbfs_opts_default(g3_msbfs_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->push_alpha = 14;
+  o->pull_warp_deg = 256;
+}
+
+extern "C" g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k,
+                              const g3_msbfs_opts* opts, int8_t* level, int32_t* n_levels,
+                              float* ms, void* stream) {
+  if (!g || !roots || !level || k < 1 || k > 64) {
+    g3_set_error("g3_msbfs: bad arguments (k must be 1..64)");
+    return G3_EINVAL;
+  }
+  for (int s = 0; s < k; ++s)
+    if (roots[s] < 0 || roots[s] >= g->n) {
+      g3_set_error("g3_msbfs: root %d outside [0, %d)", roots[s], g->n);
+      return G3_EINVAL;
+    }
+  g3_msbfs_opts o;
+  if (opts) o = *opts; else g3_msbfs_opts_default(&o);
+  if (o.push_alpha <= 0 || o.pull_warp_deg < 1) {
+    g3_set_error("g3_msbfs: bad options");
+    return G3_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!g->ms) G3_TRY(ms_ws_create(g, &g->ms));
+  g3_ms_ws* w = g->ms;
+  const int32_t nb = w->nb;
+  const uint64_t full = k == 64 ? ~0ull : ((1ull << k) - 1ull);
+  const int32_t* n2o = g->relabelled ? g->new_of_old : nullptr;
+  unsigned long long* h = w->h_ctr;
+  const int grid = G3_NUM_SMS * 8;
+
+  G3_TRY_CUDA(cudaEventRecord(w->ev[0], s));
+  G3_TRY_CUDA(cudaMemcpyAsync(w->d_roots, roots, (size_t)k * 4, cudaMemcpyHostToDevice, s));
+  G3_TRY_CUDA(cudaMemsetAsync(w->vis, 0, (size_t)nb * 8 + 8, s));
+  G3_TRY_CUDA(cudaMemsetAsync(w->fa, 0, (size_t)nb * 8 + 8, s));
+  G3_TRY_CUDA(cudaMemsetAsync(w->nx, 0, (size_t)nb * 8 + 8, s));
+  G3_TRY_CUDA(cudaMemsetAsync(w->ctr, 0, 64, s));
+  ms_seed<<<1, 64, 0, s>>>(w->d_roots, k, n2o, nb, w->vis, w->fa, w->lv, w->qa, w->ctr, g->off);
+  G3_CHECK_LAUNCH();
+  uint64_t *F = w->fa, *Fn = w->fb;
+  int32_t *q = w->qa, *qn = w->qb;
+  int32_t L = 0;
+  for (;; ++L) {
+    G3_TRY_CUDA(cudaMemcpyAsync(h, w->ctr, 24, cudaMemcpyDeviceToHost, s));
+    G3_TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t qlen = (int64_t)h[0], mf = (int64_t)h[1];
+    if (qlen == 0) break;
+    // expanding level L writes L + 1 (127 still fits int8); a non-empty
+    // frontier at level 127 means a level above 126 exists
+    if (L >= 127) {
+      g3_set_error("g3_msbfs: a level exceeds 126, the int8 range of the output");
+      return G3_ERANGE;
+    }
+    G3_TRY_CUDA(cudaMemsetAsync(w->ctr, 0, 24, s));
+    const bool pull = mf * (int64_t)o.push_alpha > g->nnz;
+    const int8_t lnext = (int8_t)(L + 1);
+    if (pull) {
+      ms_pull<<<grid, 256, 0, s>>>(nb, g->off, g->col, F, w->vis, Fn, w->lv, lnext, full,
+                                   o.pull_warp_deg, w->heavy, qn, w->ctr);
+      G3_CHECK_LAUNCH();
+      ms_pull_heavy<<<grid, 256, 0, s>>>(w->heavy, w->ctr + 2, g->off, g->col, F, w->vis, Fn,
+                                         w->lv, lnext, full, qn, w->ctr);
+      G3_CHECK_LAUNCH();
+    } else {
+      // Fn must be zero outside the new frontier: after a pull it is fully
+      // written, so clear it; after a push only the old frontier two levels
+      // back is set there, and clearing all of it is as cheap.
+      G3_TRY_CUDA(cudaMemsetAsync(Fn, 0, (size_t)nb * 8 + 8, s));
+      // touched vertices are collected in the heavy buffer
+      ms_push<<<g3_grid_for(qlen, 8, grid), 256, 0, s>>>(q, qlen, g->off, g->col, F, w->vis,
+                                                         w->nx, w->heavy, w->ctr + 2);
+      G3_CHECK_LAUNCH();
+      G3_TRY_CUDA(cudaMemcpyAsync(h + 2, w->ctr + 2, 8, cudaMemcpyDeviceToHost, s));
+      G3_TRY_CUDA(cudaStreamSynchronize(s));
+      const int64_t tl = (int64_t)h[2];
+      if (tl > 0) {
+        ms_push_finalize<<<g3_grid_for(tl, 256, grid), 256, 0, s>>>(
+            w->heavy, tl, w->nx, w->vis, Fn, w->lv, lnext, qn, g->off, w->ctr);
+        G3_CHECK_LAUNCH();
+      }
+    }
+    uint64_t* tf = F;
+    F = Fn;
+    Fn = tf;
+    int32_t* tq = q;
+    q = qn;
+    qn = tq;
+  }
+  if (n_levels) *n_levels = L;
+  ms_out<<<grid, 256, 0, s>>>(g->n, nb, k, n2o, w->vis, w->lv, level);
+  G3_CHECK_LAUNCH();
+  ms_roots_out<<<1, 64, 0, s>>>(w->d_roots, k, g->n, level);
+  G3_CHECK_LAUNCH();
+  G3_TRY_CUDA(cudaEventRecord(w->ev[1], s));
+  G3_TRY_CUDA(cudaStreamSynchronize(s));
+  if (ms) cudaEventElapsedTime(ms, w->ev[0], w->ev[1]);
+  return G3_OK;
+}

@@ -448,10 +448,12 @@ extern "C" g3_status g3_rcm_relabel(g3_graph* g, void* stream) {
     return G3_ESTATE;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if (g->ws) {
+  if (g->ws || g->ms) {
     cudaStreamSynchronize(s);
     g3_bfs_ws_free(g->ws);
+    g3_ms_ws_free(g->ms);
     g->ws = nullptr;
+    g->ms = nullptr;
   }
   RcmBufs B;
   g3_status st = rcm_impl(g, s, B);
