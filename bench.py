@@ -67,10 +67,19 @@ def parse_args():
                     help="kron: the single-root headline; msbfs: bit-sliced multi-source "
                          "BFS on a Chung-Lu graph; batch: many small graphs in one launch")
     ap.add_argument("--ms-log2n", type=int, default=24, help="msbfs: Chung-Lu 2^k vertices")
+    ap.add_argument("--msbfs-compare", type=int, default=1,
+                    help="kron: also time the roots as one bit-sliced multi-source pass")
     ap.add_argument("--ms-roots", type=int, default=256, help="msbfs: sources (64 per launch)")
+    ap.add_argument("--ms-push-alpha", type=int, default=-1,
+                    help="msbfs: fixed push/pull split (-1: autotuned)")
+    ap.add_argument("--ms-pull-warp-deg", type=int, default=-1,
+                    help="msbfs: fixed warp-pull degree (-1: autotuned)")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--batch-warp-max-n", type=int, default=-1,
-                    help="batch: warp-per-graph size limit (-1: the library default)")
+                    help="batch: warp-per-graph size limit (-1: autotuned)")
+    ap.add_argument("--tune-cache", default=os.path.join(ROOT, "paper_2012_10026_gb300",
+                                                         "tune_cache.txt"),
+                    help="msbfs/batch: autotuner cache ('' = tune afresh, no cache)")
     return ap.parse_args()
 
 
@@ -284,8 +293,10 @@ def gpu_arm(args, rank, world):
     mlp_t = None
     if ctrl == g3.G3_CTRL_LEARNED:
         with open(args.mlp) as f:
-            mlp_t = torch.tensor(json.load(f)["params"], dtype=torch.float32, device="cuda")
+            mj = json.load(f)
+        mlp_t = torch.tensor(mj["params"], dtype=torch.float32, device="cuda")
         kw["mlp_params"] = mlp_t
+        kw["mlp_margin"] = int(mj.get("mlp_margin", 0))
     opts = g3.opts(**kw)  # default path: the level loop runs as one CUDA graph
     opts_timed = g3.opts(timing=1, **kw)  # host-driven, CUDA events around each level
     plain_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, bu_reverse=args.bu_reverse)
@@ -349,6 +360,36 @@ def gpu_arm(args, rank, world):
         plain_t = []
         for _ in range(args.steps):
             plain_t += one_step(plain_opts, 0)[0]
+    # the same 64 roots as one bit-sliced multi-source pass (after the timed
+    # region; autotuned push/pull split and warp binning)
+    msb = None
+    if len(roots) <= 64 and args.msbfs_compare:
+        lv8 = torch.empty((len(roots), n), dtype=torch.int8, device="cuda")
+        t_tune = time.perf_counter()
+        mopts, mrec = g3.autotune_msbfs(g, roots, lv8, args.tune_cache or None)
+        t_tune = time.perf_counter() - t_tune
+        mt = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1)
+            ev_s.record()
+            g3.g3_msbfs(g, roots, lv8, mopts)
+            ev_e.record()
+            ev_e.synchronize()
+            if i >= args.warmup:
+                mt.append(ev_s.elapsed_time(ev_e))
+        # every source's levels equal the single-root search's (spot check)
+        g3.g3_bfs(g, roots[0], parent, level, plain_opts)
+        same = bool(torch.equal(lv8[0].to(torch.int32), level))
+        del lv8
+        torch.cuda.empty_cache()
+        m_sum = sum(m_r[r] for r in roots)
+        single = sum(all_t[:len(roots)])
+        msb = {"aggregate_gteps": m_sum / (statistics.median(mt) / 1e3) / 1e9,
+               "ms_per_launch_median": statistics.median(mt),
+               "single_root_aggregate_gteps": m_sum / (single / 1e3) / 1e9,
+               "single_root_total_ms": single, "levels_equal_single_root": same,
+               "push_alpha": mopts.push_alpha, "pull_warp_deg": mopts.pull_warp_deg,
+               "autotune": dict(mrec.to_dict(), seconds=t_tune)}
     if dist:
         dist.barrier()
     clocks = stop_clock_sampler(sampler, clk_path, local)
@@ -455,6 +496,7 @@ def gpu_arm(args, rank, world):
                             "max": max(all_t)},
             "levels": {"min": min(levels), "max": max(levels)},
             "hm_this_rank": hm,
+            "msbfs_same_roots": msb,
             "plain_heuristic": None if plain_t is None else {
                 "value": harmonic_gteps(ms, plain_t), "unit": "GTEPS",
                 "per_root_ms_median": statistics.median(plain_t)},
@@ -548,10 +590,19 @@ def msbfs_arm(args, rank, world):
     batches = [roots[i:i + 64] for i in range(0, len(roots), 64)]
     lv = torch.empty((64, n), dtype=torch.int8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # autotuned push/pull split and warp binning (untimed; cached per size class)
+    t_tune = time.perf_counter()
+    if args.ms_push_alpha > 0 and args.ms_pull_warp_deg > 0:
+        mopts, tune_rec = g3.msbfs_opts(push_alpha=args.ms_push_alpha,
+                                        pull_warp_deg=args.ms_pull_warp_deg), None
+    else:
+        mopts, tune_rec = g3.autotune_msbfs(g, batches[0], lv[:len(batches[0])],
+                                            args.tune_cache or None)
+    t_tune = time.perf_counter() - t_tune
     # m_s per source (bookkeeping, untimed)
     m_s = []
     for b in batches:
-        g3.g3_msbfs(g, b, lv[:len(b)])
+        g3.g3_msbfs(g, b, lv[:len(b)], mopts)
         for i in range(len(b)):
             m_s.append(int(cnt[lv[i] >= 0].sum().item()))
     ev_s = torch.cuda.Event(enable_timing=True)
@@ -562,7 +613,7 @@ def msbfs_arm(args, rank, world):
         for b in batches:
             flush.fill_(1)
             ev_s.record()
-            g3.g3_msbfs(g, b, lv[:len(b)])
+            g3.g3_msbfs(g, b, lv[:len(b)], mopts)
             ev_e.record()
             ev_e.synchronize()
             t.append(ev_s.elapsed_time(ev_e))
@@ -622,6 +673,8 @@ def msbfs_arm(args, rank, world):
                             f"{args.ms_log2n}", value, "GTEPS", times,
                             {"workload": f"chunglu_2^{args.ms_log2n}_g2.1_d20_cap65536_rcm_"
                                          f"{len(roots)}sources", "sources_per_launch": 64,
+                             "push_alpha": mopts.push_alpha,
+                             "pull_warp_deg": mopts.pull_warp_deg,
                              "l2": "256 MB write between launches (L2 flush)",
                              "parallelism": "replicas"})
         line.update({
@@ -637,6 +690,7 @@ def msbfs_arm(args, rank, world):
                       "max_degree": info["max_degree"]},
             "per_launch_ms": {"min": min(times), "median": statistics.median(times),
                               "max": max(times)},
+            "autotune": None if tune_rec is None else dict(tune_rec.to_dict(), seconds=t_tune),
             "plain_g3_bfs_same_sources": {
                 "aggregate_gteps": sum(m_s) / (sum(plain_t) / 1e3) / 1e9,
                 "harmonic_gteps": harmonic_gteps(m_s, plain_t),
@@ -706,8 +760,13 @@ def batch_arm(args, rank, world):
     roots = torch.tensor(roots_u, dtype=torch.int32, device="cuda")
     parent = torch.empty(N, dtype=torch.int32, device="cuda")
     level = torch.empty(N, dtype=torch.int32, device="cuda")
-    o = g3.batch_opts() if args.batch_warp_max_n < 0 else \
-        g3.batch_opts(warp_max_n=args.batch_warp_max_n)
+    tune_rec, t_tune = None, 0.0
+    if args.batch_warp_max_n < 0:
+        t_tune = time.perf_counter()
+        o, tune_rec = g3.autotune_batch(b, roots, parent, level, args.tune_cache or None)
+        t_tune = time.perf_counter() - t_tune
+    else:
+        o = g3.batch_opts(warp_max_n=args.batch_warp_max_n)
     g3.g3_bfs_batch(b, roots, parent, level, o)
     src_all = torch.cat(srcs)
     del srcs
@@ -796,6 +855,7 @@ def batch_arm(args, rank, world):
             "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
             "batch": {"graphs": len(specs), "N": N, "nnz": info["nnz"], "m_total": m_total,
                       "setup_s": setup_s},
+            "autotune": None if tune_rec is None else dict(tune_rec.to_dict(), seconds=t_tune),
             "per_launch_ms": {"min": min(times), "median": statistics.median(times),
                               "max": max(times)},
         })

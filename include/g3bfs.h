@@ -141,7 +141,11 @@ typedef struct {
   int32_t record_both;      /* training-data mode: every level is run both
                                top-down and bottom-up from the same state and
                                both are timed (stats t_td_ms, t_bu_ms) */
-  int32_t reserved[7];
+  int32_t mlp_margin;       /* learned controller: the network overrides the
+                               alpha/beta rule's direction only when its
+                               predicted |ln(t_BU / t_TD)| exceeds
+                               mlp_margin / 1000 (0, the default: always) */
+  int32_t reserved[6];
 } g3_bfs_opts;
 
 /* Fills the defaults listed above. */
@@ -265,6 +269,65 @@ g3_status g3_bfs_batch(g3_batch* b, const int32_t* roots, const g3_batch_opts* o
                        int32_t* parent, int32_t* level, float* ms, void* stream);
 
 void g3_batch_free(g3_batch* b);
+
+/* ------------------------------------------------------------ autotuner */
+
+/* Device-timed search over launch parameters with a per-size-class cache
+ * file. The paper picks its switching parameters by a grid search over
+ * measured runs (Sec. 4); these calls extend that search to the parameters
+ * of this library's kernels. Each candidate is timed as the minimum of three
+ * runs, each after a 256 MB write that evicts L2. */
+enum { G3_TUNE_BFS = 1, G3_TUNE_MSBFS = 2, G3_TUNE_BATCH = 3 };
+
+typedef struct {
+  int32_t kind;        /* G3_TUNE_* */
+  int32_t size_class;  /* floor(log2(BFS vertices per graph)) */
+  int32_t deg_class;   /* floor(log2(CSR entries per BFS vertex)) */
+  int32_t p[6];        /* chosen values: BFS (alpha, beta, t1, t2, t3, bu_reverse);
+                          MS-BFS (push_alpha, pull_warp_deg); batch (warp_max_n);
+                          unused slots 0 */
+  int32_t points;      /* candidates timed; 0 when the entry came from the cache */
+  float ms;            /* device ms of the chosen point (BFS: summed over roots) */
+  float ms_default;    /* device ms of the options passed in */
+} g3_tune_entry;
+
+/* Size class of a graph (graphs = 1) or of a batch (graphs = G, vertices and
+ * nnz the batch totals). Host only. Errors: G3_EINVAL. */
+g3_status g3_tune_key(int32_t kind, int64_t vertices, int64_t nnz, int32_t graphs,
+                      int32_t* size_class, int32_t* deg_class);
+
+/* Cache file access, host only. A missing or unreadable file holds no entries
+ * (lookup sets *found = 0); malformed lines are skipped; the last line with a
+ * key wins. Store rewrites the file (through path.tmp and a rename) with the
+ * entry replacing any of the same key. Errors: G3_EINVAL (null argument, bad
+ * kind, file not writable). */
+g3_status g3_tune_cache_lookup(const char* path, int32_t kind, int32_t size_class,
+                               int32_t deg_class, g3_tune_entry* out, int32_t* found);
+g3_status g3_tune_cache_store(const char* path, const g3_tune_entry* e);
+
+/* Each autotune call first looks up its key in cache_path (nullable: no
+ * cache) and, on a hit, only copies the cached values into *opts. Otherwise it
+ * times the candidates on the device, writes the fastest into *opts (which
+ * on entry holds the starting point and every option not searched), stores it
+ * in the cache and fills *rec (nullable). Outputs of the timed runs are left
+ * in the caller's buffers. Synchronises.
+ *   g3_autotune_bfs   : roots host (nroots original IDs), parent/level as for
+ *                       g3_bfs; coordinate search, two passes, over alpha,
+ *                       beta, (t1, t2, t3) and bu_reverse; the controller stays.
+ *   g3_autotune_msbfs : roots host (k <= 64), level as for g3_msbfs; full grid
+ *                       over push_alpha x pull_warp_deg.
+ *   g3_autotune_batch : roots/parent/level as for g3_bfs_batch; warp_max_n
+ *                       over {0, 64, ..., 2048}.
+ * Errors: those of the timed call, G3_EINVAL, G3_ENOMEM. */
+g3_status g3_autotune_bfs(g3_graph* g, const int32_t* roots, int32_t nroots, int32_t* parent,
+                          int32_t* level, const char* cache_path, g3_bfs_opts* opts,
+                          g3_tune_entry* rec, void* stream);
+g3_status g3_autotune_msbfs(g3_graph* g, const int32_t* roots, int32_t k, int8_t* level,
+                            const char* cache_path, g3_msbfs_opts* opts, g3_tune_entry* rec,
+                            void* stream);
+g3_status g3_autotune_batch(g3_batch* b, const int32_t* roots, int32_t* parent, int32_t* level,
+                            const char* cache_path, g3_batch_opts* opts, g3_tune_entry* rec,
+                            void* stream);
 
 /* --------------------------------------------------- learned controller */
 

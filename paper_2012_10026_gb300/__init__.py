@@ -42,7 +42,8 @@ class g3_bfs_opts(ctypes.Structure):
                 ("beta", ctypes.c_int32), ("t1", ctypes.c_int32), ("t2", ctypes.c_int32),
                 ("t3", ctypes.c_int32), ("bu_reverse", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
-                ("record_both", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("record_both", ctypes.c_int32), ("mlp_margin", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class g3_level_stats(ctypes.Structure):
@@ -71,6 +72,20 @@ class g3_msbfs_opts(ctypes.Structure):
 class g3_batch_opts(ctypes.Structure):
     _fields_ = [("warp_max_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
+
+class g3_tune_entry(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("size_class", ctypes.c_int32),
+                ("deg_class", ctypes.c_int32), ("p", ctypes.c_int32 * 6),
+                ("points", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("ms_default", ctypes.c_float)]
+
+    def to_dict(self):
+        return {"kind": self.kind, "size_class": self.size_class, "deg_class": self.deg_class,
+                "p": list(self.p), "points": self.points, "ms": self.ms,
+                "ms_default": self.ms_default}
+
+
+G3_TUNE_BFS, G3_TUNE_MSBFS, G3_TUNE_BATCH = 1, 2, 3
 
 _lib = None
 _vp = ctypes.c_void_p
@@ -108,6 +123,22 @@ _SIGS = {
     "g3_bfs_batch": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(g3_batch_opts), _vp, _vp,
                                     ctypes.POINTER(ctypes.c_float), _vp]),
     "g3_batch_free": (None, [_vp]),
+    "g3_tune_key": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32)]),
+    "g3_tune_cache_lookup": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.POINTER(g3_tune_entry),
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "g3_tune_cache_store": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(g3_tune_entry)]),
+    "g3_autotune_bfs": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_char_p,
+                                       ctypes.POINTER(g3_bfs_opts),
+                                       ctypes.POINTER(g3_tune_entry), _vp]),
+    "g3_autotune_msbfs": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, ctypes.c_char_p,
+                                         ctypes.POINTER(g3_msbfs_opts),
+                                         ctypes.POINTER(g3_tune_entry), _vp]),
+    "g3_autotune_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_char_p,
+                                         ctypes.POINTER(g3_batch_opts),
+                                         ctypes.POINTER(g3_tune_entry), _vp]),
     "g3_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp]),
     "g3_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp]),
     "g3_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
@@ -313,6 +344,65 @@ def g3_bfs_batch(batch: Batch, roots, parent, level, options: g3_batch_opts | No
                               _ptr(parent), _ptr(level), ctypes.byref(ms) if timed else None,
                               _stream(stream)), "g3_bfs_batch")
     return ms.value
+
+
+def _path(p):
+    return None if p is None else os.fsencode(p)
+
+
+def tune_key(kind: int, vertices: int, nnz: int, graphs: int = 1):
+    sc, dc = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().g3_tune_key(kind, vertices, nnz, graphs, ctypes.byref(sc), ctypes.byref(dc)),
+           "g3_tune_key")
+    return sc.value, dc.value
+
+
+def tune_cache_lookup(path, kind: int, size_class: int, deg_class: int):
+    """The cached g3_tune_entry for the key, or None."""
+    e = g3_tune_entry()
+    found = ctypes.c_int32()
+    _check(lib().g3_tune_cache_lookup(_path(path), kind, size_class, deg_class, ctypes.byref(e),
+                                      ctypes.byref(found)), "g3_tune_cache_lookup")
+    return e if found.value else None
+
+
+def tune_cache_store(path, entry: g3_tune_entry):
+    _check(lib().g3_tune_cache_store(_path(path), ctypes.byref(entry)), "g3_tune_cache_store")
+
+
+def autotune_bfs(graph: "Graph", roots, parent, level, cache_path=None,
+                 start: g3_bfs_opts | None = None, stream=None):
+    """Returns (tuned g3_bfs_opts, g3_tune_entry)."""
+    roots = [int(r) for r in roots]
+    arr = (ctypes.c_int32 * len(roots))(*roots)
+    o = start if start is not None else opts()
+    rec = g3_tune_entry()
+    _check(lib().g3_autotune_bfs(graph.handle, arr, len(roots), _ptr(parent), _ptr(level),
+                                 _path(cache_path), ctypes.byref(o), ctypes.byref(rec),
+                                 _stream(stream)), "g3_autotune_bfs")
+    return o, rec
+
+
+def autotune_msbfs(graph: "Graph", roots, level, cache_path=None,
+                   start: g3_msbfs_opts | None = None, stream=None):
+    roots = [int(r) for r in roots]
+    arr = (ctypes.c_int32 * len(roots))(*roots)
+    o = start if start is not None else msbfs_opts()
+    rec = g3_tune_entry()
+    _check(lib().g3_autotune_msbfs(graph.handle, arr, len(roots), _ptr(level),
+                                   _path(cache_path), ctypes.byref(o), ctypes.byref(rec),
+                                   _stream(stream)), "g3_autotune_msbfs")
+    return o, rec
+
+
+def autotune_batch(batch: Batch, roots, parent, level, cache_path=None,
+                   start: g3_batch_opts | None = None, stream=None):
+    o = start if start is not None else batch_opts()
+    rec = g3_tune_entry()
+    _check(lib().g3_autotune_batch(batch.handle, _ptr(roots), _ptr(parent), _ptr(level),
+                                   _path(cache_path), ctypes.byref(o), ctypes.byref(rec),
+                                   _stream(stream)), "g3_autotune_batch")
+    return o, rec
 
 
 def _optr(t):

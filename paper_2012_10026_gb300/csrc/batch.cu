@@ -65,146 +65,168 @@ __device__ __forceinline__ void group_sync() {
   if (GT == 32) __syncwarp(); else __syncthreads();
 }
 
+// One BFS of graph g by a group of GT threads (a warp or the whole CTA) with
+// the graph's bitmaps in shared memory: bm = visited, current and next
+// frontier, MAXW words each; s_cnt = two group-shared counters.
 template <int GT, int MAXW>
-__global__ void __launch_bounds__(256) batch_bfs(BatchArgs A, const int32_t* __restrict__ order,
-                                                 int32_t count, unsigned* counter) {
-  constexpr int NG = 256 / GT;   // groups per block
-  constexpr int WPG = GT / 32;   // warps per group
-  __shared__ uint32_t bm[NG][3][MAXW];
-  __shared__ int s_gi[NG];
-  __shared__ unsigned long long s_nf[NG], s_mf[NG];
-  const int grp = threadIdx.x / GT, t = threadIdx.x % GT;
+__device__ __forceinline__ void batch_search(const BatchArgs& A, int32_t g, uint32_t* bm,
+                                             unsigned long long* s_cnt, int t) {
+  constexpr int WPG = GT / 32;  // warps per group
   const int lane = threadIdx.x & 31, wig = t >> 5;
-  uint32_t* vis = bm[grp][0];
+  uint32_t* vis = bm;
+  uint32_t* cur = bm + MAXW;
+  uint32_t* nxt = bm + 2 * MAXW;
+  const int32_t vb = A.voff[g], ng = A.voff[g + 1] - vb, npg = A.np[g];
+  const int32_t words = (npg + 31) >> 5;
+  const int32_t root_o = A.roots[g];
+  // a root outside its own graph's ID range leaves the graph unreached
+  const bool root_ok = root_o >= vb && root_o < vb + ng;
+  const int32_t r = root_ok ? A.label_of[root_o] - vb : npg;
+  for (int32_t i = t; i < ng; i += GT) {
+    A.parent[vb + i] = -1;
+    A.level[vb + i] = -1;
+  }
+  for (int32_t w = t; w < words; w += GT) {
+    vis[w] = 0u;
+    cur[w] = 0u;
+  }
+  group_sync<GT>();
+  if (t == 0 && root_ok) {
+    A.parent[root_o] = root_o;
+    A.level[root_o] = 0;
+    if (r >= 0 && r < npg) {
+      vis[r >> 5] |= 1u << (r & 31);
+      cur[r >> 5] |= 1u << (r & 31);
+    }
+  }
+  group_sync<GT>();
+  if (r < 0 || r >= npg) return;  // isolated root: nothing else is reached
+  const int64_t mtot = A.off[vb + npg] - A.off[vb];
+  int64_t mvis = A.off[vb + r + 1] - A.off[vb + r];
+  int64_t mf = mvis, prev_nf = 0, nf = 1;
+  bool bu = false;
+  for (int32_t L = 0;; ++L) {
+    // direction for this level (Algorithm 2 starts top-down; alpha/beta rule)
+    if (L > 0) {
+      const int64_t mu = mtot - mvis;
+      bu = bu ? !(nf < prev_nf && nf * 24 < npg) : (mf * 14 > mu);
+    }
+    for (int32_t w = t; w < words; w += GT) nxt[w] = 0u;
+    if (t == 0) {
+      s_cnt[0] = 0;
+      s_cnt[1] = 0;
+    }
+    group_sync<GT>();
+    unsigned long long cnt = 0, dsum = 0;
+    if (!bu) {
+      // top-down: each warp takes frontier words, the whole warp expands
+      // each frontier vertex of the word
+      for (int32_t w = wig; w < words; w += WPG) {
+        uint32_t bits = cur[w];
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const int32_t V = vb + w * 32 + b;
+          const int32_t vo = A.orig_of[V];
+          const int64_t e = A.off[V + 1];
+          for (int64_t j = A.off[V] + lane; j < e; j += 32) {
+            const int32_t u = A.col[j] - vb;
+            const uint32_t bit = 1u << (u & 31);
+            if (!(vis[u >> 5] & bit) && !(atomicOr(&vis[u >> 5], bit) & bit)) {
+              atomicOr(&nxt[u >> 5], bit);
+              const int32_t uo = A.orig_of[vb + u];
+              A.parent[uo] = vo;
+              A.level[uo] = L + 1;
+              cnt++;
+              dsum += (unsigned long long)(A.off[vb + u + 1] - A.off[vb + u]);
+            }
+          }
+        }
+      }
+    } else {
+      // bottom-up: lane per vertex, scan from the row's end (highest label
+      // first), stop at the first neighbour in the current frontier
+      for (int32_t w = wig; w < words; w += WPG) {
+        const int32_t v = w * 32 + lane;
+        const bool cand = v < npg && !((vis[w] >> lane) & 1u);
+        int32_t p = -1;
+        int64_t d = 0;
+        if (cand) {
+          const int64_t b0 = A.off[vb + v], e0 = A.off[vb + v + 1];
+          d = e0 - b0;
+          for (int64_t j = e0 - 1; j >= b0; --j) {
+            const int32_t u = A.col[j] - vb;
+            if ((cur[u >> 5] >> (u & 31)) & 1u) {
+              p = u;
+              break;
+            }
+          }
+        }
+        const uint32_t found = __ballot_sync(0xffffffffu, p >= 0);
+        if (lane == 0 && found) {
+          nxt[w] = found;
+          vis[w] |= found;
+        }
+        if (p >= 0) {
+          const int32_t vo = A.orig_of[vb + v];
+          A.parent[vo] = A.orig_of[vb + p];
+          A.level[vo] = L + 1;
+          cnt++;
+          dsum += (unsigned long long)d;
+        }
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    }
+    if (lane == 0 && cnt) {
+      atomicAdd(&s_cnt[0], cnt);
+      atomicAdd(&s_cnt[1], dsum);
+    }
+    group_sync<GT>();
+    prev_nf = nf;
+    nf = (int64_t)s_cnt[0];
+    mf = (int64_t)s_cnt[1];
+    mvis += mf;
+    uint32_t* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    group_sync<GT>();
+    if (nf == 0) break;
+  }
+}
+
+// Persistent kernel over all graphs: first every CTA takes graphs of the
+// CTA list (largest first) as a whole, then, once that list is drained, each
+// warp takes graphs of the warp list on its own; the tail of the big graphs
+// overlaps the small ones. counters[0] / [1] are the two lists' cursors.
+__global__ void __launch_bounds__(256) batch_bfs(BatchArgs A, const int32_t* __restrict__ order_cta,
+                                                 int32_t n_cta,
+                                                 const int32_t* __restrict__ order_warp,
+                                                 int32_t n_warp, unsigned* counters) {
+  static_assert(3 * BT_CTA_WORDS == 8 * 3 * BT_WARP_WORDS, "shared layouts must coincide");
+  __shared__ uint32_t bm[3 * BT_CTA_WORDS];
+  __shared__ unsigned long long s_cnt[8][2];
+  __shared__ int s_gi[8];
   for (;;) {
-    if (t == 0) s_gi[grp] = (int)atomicAdd(counter, 1u);
-    group_sync<GT>();
-    const int gi = s_gi[grp];
-    group_sync<GT>();
-    if (gi >= count) break;
-    const int32_t g = order[gi];
-    const int32_t vb = A.voff[g], ng = A.voff[g + 1] - vb, npg = A.np[g];
-    const int32_t words = (npg + 31) >> 5;
-    const int32_t root_o = A.roots[g];
-    // a root outside its own graph's ID range leaves the graph unreached
-    const bool root_ok = root_o >= vb && root_o < vb + ng;
-    const int32_t r = root_ok ? A.label_of[root_o] - vb : npg;
-    uint32_t* cur = bm[grp][1];
-    uint32_t* nxt = bm[grp][2];
-    for (int32_t i = t; i < ng; i += GT) {
-      A.parent[vb + i] = -1;
-      A.level[vb + i] = -1;
-    }
-    for (int32_t w = t; w < words; w += GT) {
-      vis[w] = 0u;
-      cur[w] = 0u;
-    }
-    group_sync<GT>();
-    if (t == 0 && root_ok) {
-      A.parent[root_o] = root_o;
-      A.level[root_o] = 0;
-      if (r >= 0 && r < npg) {
-        vis[r >> 5] |= 1u << (r & 31);
-        cur[r >> 5] |= 1u << (r & 31);
-      }
-    }
-    group_sync<GT>();
-    if (r < 0 || r >= npg) continue;  // isolated root: nothing else is reached
-    const int64_t eb = A.off[vb];
-    const int64_t mtot = A.off[vb + npg] - eb;
-    int64_t mvis = A.off[vb + r + 1] - A.off[vb + r];
-    int64_t mf = mvis, prev_nf = 0, nf = 1;
-    bool bu = false;
-    for (int32_t L = 0;; ++L) {
-      // direction for this level (Algorithm 2 starts top-down; alpha/beta rule)
-      if (L > 0) {
-        const int64_t mu = mtot - mvis;
-        bu = bu ? !(nf < prev_nf && nf * 24 < npg) : (mf * 14 > mu);
-      }
-      for (int32_t w = t; w < words; w += GT) nxt[w] = 0u;
-      if (t == 0) {
-        s_nf[grp] = 0;
-        s_mf[grp] = 0;
-      }
-      group_sync<GT>();
-      unsigned long long cnt = 0, dsum = 0;
-      if (!bu) {
-        // top-down: each warp takes frontier words, the whole warp expands
-        // each frontier vertex of the word
-        for (int32_t w = wig; w < words; w += WPG) {
-          uint32_t bits = cur[w];
-          while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1u;
-            const int32_t V = vb + w * 32 + b;
-            const int32_t vo = A.orig_of[V];
-            const int64_t e = A.off[V + 1];
-            for (int64_t j = A.off[V] + lane; j < e; j += 32) {
-              const int32_t u = A.col[j] - vb;
-              const uint32_t bit = 1u << (u & 31);
-              if (!(vis[u >> 5] & bit) && !(atomicOr(&vis[u >> 5], bit) & bit)) {
-                atomicOr(&nxt[u >> 5], bit);
-                const int32_t uo = A.orig_of[vb + u];
-                A.parent[uo] = vo;
-                A.level[uo] = L + 1;
-                cnt++;
-                dsum += (unsigned long long)(A.off[vb + u + 1] - A.off[vb + u]);
-              }
-            }
-          }
-        }
-      } else {
-        // bottom-up: lane per vertex, scan from the row's end (highest label
-        // first), stop at the first neighbour in the current frontier
-        for (int32_t w = wig; w < words; w += WPG) {
-          const int32_t v = w * 32 + lane;
-          const bool cand = v < npg && !((vis[w] >> lane) & 1u);
-          int32_t p = -1;
-          int64_t d = 0;
-          if (cand) {
-            const int64_t b0 = A.off[vb + v], e0 = A.off[vb + v + 1];
-            d = e0 - b0;
-            for (int64_t j = e0 - 1; j >= b0; --j) {
-              const int32_t u = A.col[j] - vb;
-              if ((cur[u >> 5] >> (u & 31)) & 1u) {
-                p = u;
-                break;
-              }
-            }
-          }
-          const uint32_t found = __ballot_sync(0xffffffffu, p >= 0);
-          if (lane == 0 && found) {
-            nxt[w] = found;
-            vis[w] |= found;
-          }
-          if (p >= 0) {
-            const int32_t vo = A.orig_of[vb + v];
-            A.parent[vo] = A.orig_of[vb + p];
-            A.level[vo] = L + 1;
-            cnt++;
-            dsum += (unsigned long long)d;
-          }
-        }
-      }
-      for (int o = 16; o; o >>= 1) {
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-      }
-      if (lane == 0 && cnt) {
-        atomicAdd(&s_nf[grp], cnt);
-        atomicAdd(&s_mf[grp], dsum);
-      }
-      group_sync<GT>();
-      prev_nf = nf;
-      nf = (int64_t)s_nf[grp];
-      mf = (int64_t)s_mf[grp];
-      mvis += mf;
-      uint32_t* tmp = cur;
-      cur = nxt;
-      nxt = tmp;
-      group_sync<GT>();
-      if (nf == 0) break;
-    }
+    if (threadIdx.x == 0) s_gi[0] = (int)atomicAdd(&counters[0], 1u);
+    __syncthreads();
+    const int gi = s_gi[0];
+    __syncthreads();
+    if (gi >= n_cta) break;
+    batch_search<256, BT_CTA_WORDS>(A, order_cta[gi], bm, s_cnt[0], threadIdx.x);
+    __syncthreads();
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* wbm = bm + wid * 3 * BT_WARP_WORDS;
+  for (;;) {
+    int gi = 0;
+    if (lane == 0) gi = (int)atomicAdd(&counters[1], 1u);
+    gi = __shfl_sync(0xffffffffu, gi, 0);
+    if (gi >= n_warp) break;
+    batch_search<32, BT_WARP_WORDS>(A, order_warp[gi], wbm, s_cnt[wid], lane);
+    __syncwarp();
   }
 }
 
@@ -382,13 +404,12 @@ static g3_status batch_capture(g3_batch* b, const int32_t* roots, int32_t* paren
                            cudaMemcpyHostToDevice));
   b->n_warp = (int32_t)warp_list.size();
   b->n_cta = (int32_t)cta_list.size();
-  int dev = 0, sms = 0, per_w = 0, per_c = 0;
+  int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_w, batch_bfs<32, BT_WARP_WORDS>, 256, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_c, batch_bfs<256, BT_CTA_WORDS>, 256, 0);
-  const int grid_w = std::max(1, std::min(sms * std::max(per_w, 1), (b->n_warp + 7) / 8));
-  const int grid_c = std::max(1, std::min(sms * std::max(per_c, 1), b->n_cta));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_bfs, 256, 0);
+  const int grid =
+      std::max(1, std::min(sms * std::max(per, 1), std::max(b->n_cta, (b->n_warp + 7) / 8)));
   BatchArgs A{b->N, b->off, b->col, b->orig_of, b->label_of, b->voff, b->np, roots, parent, level};
   cudaStream_t cs;
   G3_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -396,13 +417,9 @@ static g3_status batch_capture(g3_batch* b, const int32_t* roots, int32_t* paren
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(b->counters, 0, 16, cs);
-    if (b->n_warp)
-      batch_bfs<32, BT_WARP_WORDS><<<grid_w, 256, 0, cs>>>(A, b->order_warp, b->n_warp,
-                                                           b->counters);
-    if (b->n_cta)
-      batch_bfs<256, BT_CTA_WORDS><<<grid_c, 256, 0, cs>>>(A, b->order_cta, b->n_cta,
-                                                           b->counters + 1);
-    e = cudaStreamEndCapture(cs, &graph);
+    batch_bfs<<<grid, 256, 0, cs>>>(A, b->order_cta, b->n_cta, b->order_warp, b->n_warp,
+                                    b->counters);
+  e = cudaStreamEndCapture(cs, &graph);
   }
   cudaStreamDestroy(cs);
   if (e != cudaSuccess) {
@@ -447,8 +464,7 @@ extern "C" g3_status g3_bfs_batch(g3_batch* b, const int32_t* roots, const g3_ba
   }
   G3_TRY_CUDA(cudaEventRecord(b->ev[0], s));
   G3_TRY_CUDA(cudaGraphLaunch(b->gexec, s));
-  if (b->n_warp) g3_count_launch();
-  if (b->n_cta) g3_count_launch();
+  g3_count_launch();
   G3_TRY_CUDA(cudaEventRecord(b->ev[1], s));
   if (ms) {
     G3_TRY_CUDA(cudaEventSynchronize(b->ev[1]));

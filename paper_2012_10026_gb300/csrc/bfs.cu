@@ -674,6 +674,7 @@ struct CtrlArgs {
   int64_t nnz;
   int controller, alpha, beta;
   const float* mlp;
+  float mlp_margin;
   int t1, t2, t3;
   LevelLog* log;
   int graph_mode;
@@ -740,7 +741,8 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
     mlp_eval_warp(A.mlp, feat, out);
     if (lane == 0) {
       for (int k = 0; k < 4; ++k) c->mlp_out[k] = out[k];
-      decide = out[0] < 0.f ? G3_DIR_BU : G3_DIR_TD;
+      // inside the margin the alpha/beta rule's direction stands
+      if (fabsf(out[0]) > A.mlp_margin) decide = out[0] < 0.f ? G3_DIR_BU : G3_DIR_TD;
       int a1 = clamp_thr(out[1], 2, 12), a2 = clamp_thr(out[2], 6, 18),
           a3 = clamp_thr(out[3], 10, 26);
       if (a2 <= a1) a2 = a1 * 2;
@@ -978,9 +980,11 @@ struct Launch {
 };
 
 static CtrlArgs ctrl_args(const Launch& S, int graph_mode, cudaGraphConditionalHandle h_loop) {
-  return CtrlArgs{S.ws->nb,     S.g->nnz,     S.o->controller, S.o->alpha,
-                  S.o->beta,    S.o->mlp_params, S.o->t1,     S.o->t2,
-                  S.o->t3,      S.ws->log,    graph_mode,      h_loop};
+  return CtrlArgs{S.ws->nb,     S.g->nnz,        S.o->controller,
+                  S.o->alpha,   S.o->beta,       S.o->mlp_params,
+                  S.o->mlp_margin * 1e-3f,       S.o->t1,
+                  S.o->t2,      S.o->t3,         S.ws->log,
+                  graph_mode,   h_loop};
 }
 
 // Host-driven launch of the kernels of one level of the given mode. Every
@@ -1045,7 +1049,7 @@ struct NodeParams {
 static bool same_opts(const g3_bfs_opts& a, const g3_bfs_opts& b) {
   return a.controller == b.controller && a.alpha == b.alpha && a.beta == b.beta &&
          a.t1 == b.t1 && a.t2 == b.t2 && a.t3 == b.t3 && a.bu_reverse == b.bu_reverse &&
-         a.mlp_params == b.mlp_params;
+         a.mlp_params == b.mlp_params && a.mlp_margin == b.mlp_margin;
 }
 
 // Builds the level loop: WHILE(h_loop) { bfs_select -> SWITCH(h_mode) {
@@ -1312,7 +1316,7 @@ extern "C" g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, 
   g3_bfs_opts o;
   if (opts) o = *opts; else g3_bfs_opts_default(&o);
   if (o.controller < 0 || o.controller > 3 || o.alpha <= 0 || o.beta <= 0 || o.t1 < 1 ||
-      o.t2 <= o.t1 || o.t3 <= o.t2) {
+      o.t2 <= o.t1 || o.t3 <= o.t2 || o.mlp_margin < 0) {
     g3_set_error("g3_bfs: bad options");
     return G3_EINVAL;
   }

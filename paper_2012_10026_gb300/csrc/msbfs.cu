@@ -11,11 +11,17 @@
 //     reached by all sources ORs the frontier words of its neighbours, with an
 //     early exit once every missing source is found; vertices with degree >=
 //     pull_warp_deg are pulled by a whole warp (degree binning).
+// Rows longer than MS_CHUNK entries (the hubs of a power-law graph) are split
+// in both directions: the warp that meets such a row takes its first chunk
+// and queues the others as (vertex, chunk) items for a follow-up kernel with
+// one warp per item, so no single warp walks a million-entry row.
 // Levels are stored per vertex as a 64-byte row in label order and written to
 // level[s][original ID] (int8) by a shared-memory transpose at the end.
 #include <string.h>
 
 #include "g3_prims.cuh"
+
+#define MS_CHUNK 2048  // row entries per warp work item
 
 struct g3_ms_ws {
   int32_t nb;
@@ -23,7 +29,12 @@ struct g3_ms_ws {
   int8_t* lv;        // [nb][64]
   int32_t *qa, *qb;  // frontier queues
   int32_t* heavy;    // pull: vertices pulled by a warp
-  unsigned long long* ctr;  // [0] next queue len, [1] next sum of degrees, [2] heavy len
+  int32_t* pend;     // pull: heavy vertices whose rows were split into chunks
+  int2* items;       // (vertex, chunk index >= 1) of split rows
+  int64_t items_cap;
+  // [0] next queue len, [1] next sum of degrees, [2] heavy len, [3] items,
+  // [4] pending heavy vertices
+  unsigned long long* ctr;
   unsigned long long* h_ctr;
   int32_t* d_roots;
   cudaEvent_t ev[2];
@@ -31,7 +42,8 @@ struct g3_ms_ws {
 
 void g3_ms_ws_free(g3_ms_ws* w) {
   if (!w) return;
-  void* all[] = {w->vis, w->fa, w->fb, w->nx, w->lv, w->qa, w->qb, w->heavy, w->ctr, w->d_roots};
+  void* all[] = {w->vis,   w->fa,   w->fb,    w->nx,  w->lv,     w->qa,
+                 w->qb,    w->heavy, w->pend, w->items, w->ctr, w->d_roots};
   for (void* p : all)
     if (p) cudaFree(p);
   if (w->h_ctr) cudaFreeHost(w->h_ctr);
@@ -45,12 +57,15 @@ static g3_status ms_ws_create(g3_graph* g, g3_ms_ws** out) {
   if (!w) return G3_ENOMEM;
   w->nb = g->n_bfs;
   const size_t nb1 = (size_t)g->n_bfs + 4;
+  // a row of d entries yields at most d / MS_CHUNK items
+  w->items_cap = g->nnz / MS_CHUNK + 4;
   struct {
     void** p;
     size_t bytes;
   } req[] = {{(void**)&w->vis, nb1 * 8}, {(void**)&w->fa, nb1 * 8},   {(void**)&w->fb, nb1 * 8},
              {(void**)&w->nx, nb1 * 8},  {(void**)&w->lv, nb1 * 64},  {(void**)&w->qa, nb1 * 4},
              {(void**)&w->qb, nb1 * 4},  {(void**)&w->heavy, nb1 * 4}, {(void**)&w->ctr, 64},
+             {(void**)&w->pend, nb1 * 4}, {(void**)&w->items, (size_t)w->items_cap * 8},
              {(void**)&w->d_roots, 64 * 4}};
   for (auto& r : req) {
     cudaError_t e = cudaMalloc(r.p, r.bytes);
@@ -91,34 +106,75 @@ __global__ void ms_seed(const int32_t* roots, int k, const int32_t* new_of_old, 
   }
 }
 
-// Push: N[w] |= F[u] & ~vis[w] for the edges of frontier vertices u, one warp
-// per frontier vertex; first touchers of w are queued in `touched`.
+// Queues chunks 1 .. of a row longer than MS_CHUNK (warp-wide call).
+__device__ __forceinline__ void ms_queue_chunks(int32_t v, int64_t deg, int2* items,
+                                                unsigned long long* nitems, int lane) {
+  const int64_t nch = (deg + MS_CHUNK - 1) / MS_CHUNK;
+  if (nch <= 1) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(nitems, (unsigned long long)(nch - 1));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int64_t c = 1 + lane; c < nch; c += 32) items[base + c - 1] = make_int2(v, (int32_t)c);
+}
+
+// Push of row entries [b, e) of frontier vertex u (warp-wide call):
+// N[w] |= F[u] & ~vis[w]; first touchers of w queue it in `touched`.
+__device__ __forceinline__ void ms_push_range(int64_t b, int64_t e, uint64_t fu,
+                                              const int32_t* __restrict__ col,
+                                              const uint64_t* __restrict__ vis, uint64_t* N,
+                                              int32_t* touched, unsigned long long* tlen,
+                                              int lane) {
+  for (int64_t j0 = b; j0 < e; j0 += 32) {
+    const int64_t j = j0 + lane;
+    bool first = false;
+    int32_t w = 0;
+    if (j < e) {
+      w = col[j];
+      const uint64_t m = fu & ~__ldcg((const unsigned long long*)&vis[w]);
+      if (m) {
+        const uint64_t o = atomicOr((unsigned long long*)&N[w], m);
+        first = (o == 0);
+      }
+    }
+    g3_warp_append(0xffffffffu, first, w, touched, tlen);
+  }
+}
+
+// Push, one warp per frontier vertex (first chunk of long rows).
 __global__ void __launch_bounds__(256) ms_push(const int32_t* __restrict__ q, int64_t qlen,
                                                const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
                                                const uint64_t* __restrict__ F,
                                                const uint64_t* __restrict__ vis, uint64_t* N,
-                                               int32_t* touched, unsigned long long* tlen) {
+                                               int32_t* touched, unsigned long long* ctr,
+                                               int2* items) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < qlen; i += nwarps) {
     const int32_t u = q[i];
     const uint64_t fu = F[u];
     const int64_t b = off[u], e = off[u + 1];
-    for (int64_t j0 = b; j0 < e; j0 += 32) {
-      const int64_t j = j0 + lane;
-      bool first = false;
-      int32_t w = 0;
-      if (j < e) {
-        w = col[j];
-        const uint64_t m = fu & ~__ldcg((const unsigned long long*)&vis[w]);
-        if (m) {
-          const uint64_t o = atomicOr((unsigned long long*)&N[w], m);
-          first = (o == 0);
-        }
-      }
-      g3_warp_append(0xffffffffu, first, w, touched, tlen);
-    }
+    ms_queue_chunks(u, e - b, items, &ctr[3], lane);
+    ms_push_range(b, min(e, b + MS_CHUNK), fu, col, vis, N, touched, &ctr[2], lane);
+  }
+}
+
+// Push of the queued chunks, one warp per (vertex, chunk) item.
+__global__ void __launch_bounds__(256) ms_push_chunks(const int2* __restrict__ items,
+                                                      const int64_t* __restrict__ off,
+                                                      const int32_t* __restrict__ col,
+                                                      const uint64_t* __restrict__ F,
+                                                      const uint64_t* __restrict__ vis,
+                                                      uint64_t* N, int32_t* touched,
+                                                      unsigned long long* ctr) {
+  const int64_t len = (int64_t)ctr[3];
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < len; i += nwarps) {
+    const int2 it = items[i];
+    const int64_t b = off[it.x] + (int64_t)it.y * MS_CHUNK;
+    ms_push_range(b, min(off[it.x + 1], b + MS_CHUNK), F[it.x], col, vis, N, touched, &ctr[2],
+                  lane);
   }
 }
 
@@ -191,8 +247,14 @@ __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __rest
         if (e - b >= heavy_deg) {
           big = true;
         } else {
+          // four independent gathers per step; the exit test runs per step
           uint64_t acc = 0;
-          for (int64_t j = b; j < e && (acc | vv) != full; ++j) acc |= __ldg(&F[col[j]]);
+          int64_t j = b;
+          for (; j + 4 <= e && (acc | vv) != full; j += 4) {
+            const int32_t c0 = col[j], c1 = col[j + 1], c2 = col[j + 2], c3 = col[j + 3];
+            acc |= (__ldg(&F[c0]) | __ldg(&F[c1])) | (__ldg(&F[c2]) | __ldg(&F[c3]));
+          }
+          for (; j < e && (acc | vv) != full; ++j) acc |= __ldg(&F[col[j]]);
           nv = acc & ~vv;
           if (nv) {
             ms_take((int32_t)v, nv, vis, vv, lv, lnext);
@@ -210,58 +272,119 @@ __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __rest
   }
 }
 
-// Pull for high-degree vertices: one warp per vertex, warp-OR of 32 frontier
-// words per step, early exit once every missing source is found.
+// Frontier sources among row entries [b, e) (warp-wide call): the OR of
+// F over the entries, cut short once `have` | the OR covers every source.
+__device__ __forceinline__ uint64_t ms_pull_range(int64_t b, int64_t e, uint64_t have,
+                                                  uint64_t full,
+                                                  const int32_t* __restrict__ col,
+                                                  const uint64_t* __restrict__ F, int lane) {
+  uint64_t acc = 0;
+  for (int64_t j0 = b; j0 < e; j0 += 32) {
+    const int64_t j = j0 + lane;
+    uint64_t x = j < e ? __ldg(&F[col[j]]) : 0ull;
+    for (int o = 16; o; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
+    acc |= x;
+    if ((acc | have) == full) break;
+  }
+  return acc;
+}
+
+// Queues a vertex that found new sources for the next level.
+__device__ __forceinline__ void ms_emit(int32_t v, uint64_t nv, uint64_t vv, uint64_t* vis,
+                                        uint64_t* Fn, int8_t* lv, int8_t lnext, int32_t* qn,
+                                        int64_t deg, unsigned long long* ctr) {
+  Fn[v] = nv;
+  if (nv) {
+    ms_take(v, nv, vis, vv, lv, lnext);
+    const unsigned long long slot = atomicAdd(&ctr[0], 1ull);
+    qn[slot] = v;
+    atomicAdd(&ctr[1], (unsigned long long)deg);
+  }
+}
+
+// Pull for high-degree vertices: one warp per vertex over the row's first
+// chunk; a row longer than that, still missing sources, has its other
+// chunks queued and its partial OR parked in N[v] for ms_pull_pending.
 __global__ void __launch_bounds__(256) ms_pull_heavy(const int32_t* __restrict__ heavy,
-                                                     const unsigned long long* hlen,
                                                      const int64_t* __restrict__ off,
                                                      const int32_t* __restrict__ col,
                                                      const uint64_t* __restrict__ F,
-                                                     uint64_t* vis, uint64_t* Fn, int8_t* lv,
-                                                     int8_t lnext, uint64_t full, int32_t* qn,
+                                                     uint64_t* vis, uint64_t* Fn, uint64_t* N,
+                                                     int8_t* lv, int8_t lnext, uint64_t full,
+                                                     int32_t* qn, int32_t* pend, int2* items,
                                                      unsigned long long* ctr) {
-  const int64_t len = (int64_t)*hlen;
+  const int64_t len = (int64_t)ctr[2];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < len; i += nwarps) {
     const int32_t v = heavy[i];
     const uint64_t vv = vis[v];
     const int64_t b = off[v], e = off[v + 1];
-    uint64_t acc = 0;
-    for (int64_t j0 = b; j0 < e; j0 += 32) {
-      const int64_t j = j0 + lane;
-      uint64_t x = j < e ? __ldg(&F[col[j]]) : 0ull;
-      for (int o = 16; o; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
-      acc |= x;
-      if ((acc | vv) == full) break;
-    }
-    const uint64_t nv = acc & ~vv;
-    if (lane == 0) {
-      Fn[v] = nv;
-      if (nv) {
-        ms_take(v, nv, vis, vv, lv, lnext);
-        const unsigned long long slot = atomicAdd(&ctr[0], 1ull);
-        qn[slot] = v;
-        atomicAdd(&ctr[1], (unsigned long long)(e - b));
+    const uint64_t acc = ms_pull_range(b, min(e, b + MS_CHUNK), vv, full, col, F, lane);
+    if (e - b > MS_CHUNK && (acc | vv) != full) {
+      ms_queue_chunks(v, e - b, items, &ctr[3], lane);
+      if (lane == 0) {
+        N[v] = acc;
+        pend[atomicAdd(&ctr[4], 1ull)] = v;
       }
+    } else if (lane == 0) {
+      ms_emit(v, acc & ~vv, vv, vis, Fn, lv, lnext, qn, e - b, ctr);
     }
   }
 }
 
-// level[s][o] for s < k and a tile of 64 original IDs: gather the 64-byte rows
-// of the tile's vertices into shared memory (valid where the source's bit is
-// set in vis), then write each source's 64 bytes contiguously.
+// Pull of the queued chunks, one warp per item; partial ORs meet in N[v].
+__global__ void __launch_bounds__(256) ms_pull_chunks(const int2* __restrict__ items,
+                                                      const int64_t* __restrict__ off,
+                                                      const int32_t* __restrict__ col,
+                                                      const uint64_t* __restrict__ F,
+                                                      const uint64_t* __restrict__ vis,
+                                                      uint64_t* N, uint64_t full,
+                                                      const unsigned long long* ctr) {
+  const int64_t len = (int64_t)ctr[3];
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < len; i += nwarps) {
+    const int2 it = items[i];
+    const int64_t b = off[it.x] + (int64_t)it.y * MS_CHUNK;
+    const uint64_t acc =
+        ms_pull_range(b, min(off[it.x + 1], b + MS_CHUNK), vis[it.x], full, col, F, lane);
+    if (lane == 0 && acc) atomicOr((unsigned long long*)&N[it.x], acc);
+  }
+}
+
+// Finishes the split heavy vertices: new sources = N[v] & ~vis[v]; N cleared.
+__global__ void ms_pull_pending(const int32_t* __restrict__ pend, const int64_t* __restrict__ off,
+                                uint64_t* vis, uint64_t* Fn, uint64_t* N, int8_t* lv,
+                                int8_t lnext, int32_t* qn, unsigned long long* ctr) {
+  const int64_t len = (int64_t)ctr[4];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = pend[i];
+    const uint64_t vv = vis[v];
+    const uint64_t acc = N[v];
+    N[v] = 0;
+    ms_emit(v, acc & ~vv, vv, vis, Fn, lv, lnext, qn, off[v + 1] - off[v], ctr);
+  }
+}
+
+// level[s][o] for s < k over tiles of MS_OUT_TILE original IDs: gather the
+// 64-byte rows of the tile's vertices into shared memory (a level is valid
+// where the source's bit is set in vis), then write each source's slice of
+// the tile as 32-bit words, one 128-byte run per warp store.
+#define MS_OUT_TILE 128
 __global__ void __launch_bounds__(256) ms_out(int32_t n, int32_t nb, int k,
                                               const int32_t* __restrict__ new_of_old,
                                               const uint64_t* __restrict__ vis,
                                               const int8_t* __restrict__ lv, int8_t* level) {
-  __shared__ int8_t tile[64][64 + 4];
-  __shared__ int32_t xs[64];
-  __shared__ uint64_t vm[64];
-  const int64_t ntiles = ((int64_t)n + 63) / 64;
+  __shared__ __align__(16) int8_t tile[MS_OUT_TILE][64 + 4];
+  __shared__ int32_t xs[MS_OUT_TILE];
+  __shared__ uint64_t vm[MS_OUT_TILE];
+  const int64_t ntiles = ((int64_t)n + MS_OUT_TILE - 1) / MS_OUT_TILE;
+  const bool aligned = ((uintptr_t)level & 3) == 0 && (n & 3) == 0;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t o0 = t * 64;
-    if (threadIdx.x < 64) {
+    const int64_t o0 = t * MS_OUT_TILE;
+    if (threadIdx.x < MS_OUT_TILE) {
       const int64_t o = o0 + threadIdx.x;
       int32_t x = -1;
       if (o < n) x = new_of_old ? new_of_old[o] : (int32_t)o;
@@ -270,8 +393,11 @@ __global__ void __launch_bounds__(256) ms_out(int32_t n, int32_t nb, int k,
       vm[threadIdx.x] = x >= 0 ? vis[x] : 0ull;
     }
     __syncthreads();
-    {  // 256 threads x 16 bytes = the 64 x 64 tile
-      const int r = threadIdx.x >> 2, qd = threadIdx.x & 3;
+    // MS_OUT_TILE rows x 4 quarters of 16 bytes, two per thread
+#pragma unroll
+    for (int h = 0; h < (MS_OUT_TILE * 4) / 256; ++h) {
+      const int idx = threadIdx.x + h * 256;
+      const int r = idx >> 2, qd = idx & 3;
       const int32_t x = xs[r];
       int4 val = make_int4(-1, -1, -1, -1);
       if (x >= 0) val = *reinterpret_cast<const int4*>(lv + (int64_t)x * 64 + qd * 16);
@@ -279,27 +405,24 @@ __global__ void __launch_bounds__(256) ms_out(int32_t n, int32_t nb, int k,
       const uint64_t m = vm[r];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const int s = qd * 16 + j;
-        tile[r][s] = ((m >> s) & 1ull) ? vb[j] : (int8_t)-1;
+        const int sidx = qd * 16 + j;
+        tile[r][sidx] = ((m >> sidx) & 1ull) ? vb[j] : (int8_t)-1;
       }
     }
     __syncthreads();
-    // each (source, 4 consecutive IDs) pair is one 32-bit store
-    for (int idx = threadIdx.x; idx < k * 16; idx += blockDim.x) {
-      const int s = idx >> 4, c = idx & 15;
+    constexpr int WPT = MS_OUT_TILE / 4;  // 32-bit words per source per tile
+    for (int idx = threadIdx.x; idx < k * WPT; idx += blockDim.x) {
+      const int sidx = idx / WPT, c = idx % WPT;
       const int64_t o = o0 + 4 * c;
-      if (o + 3 < n) {
-        const uint32_t w = (uint32_t)(uint8_t)tile[4 * c][s] |
-                           ((uint32_t)(uint8_t)tile[4 * c + 1][s] << 8) |
-                           ((uint32_t)(uint8_t)tile[4 * c + 2][s] << 16) |
-                           ((uint32_t)(uint8_t)tile[4 * c + 3][s] << 24);
-        if (((uintptr_t)(level + (int64_t)s * n + o) & 3) == 0) {
-          *reinterpret_cast<uint32_t*>(level + (int64_t)s * n + o) = w;
-        } else {
-          for (int j = 0; j < 4; ++j) level[(int64_t)s * n + o + j] = tile[4 * c + j][s];
-        }
+      int8_t* dst = level + (int64_t)sidx * n + o;
+      if (aligned && o + 3 < n) {
+        const uint32_t w = (uint32_t)(uint8_t)tile[4 * c][sidx] |
+                           ((uint32_t)(uint8_t)tile[4 * c + 1][sidx] << 8) |
+                           ((uint32_t)(uint8_t)tile[4 * c + 2][sidx] << 16) |
+                           ((uint32_t)(uint8_t)tile[4 * c + 3][sidx] << 24);
+        *reinterpret_cast<uint32_t*>(dst) = w;
       } else {
-        for (int j = 0; j < 4 && o + j < n; ++j) level[(int64_t)s * n + o + j] = tile[4 * c + j][s];
+        for (int j = 0; j < 4 && o + j < n; ++j) dst[j] = tile[4 * c + j][sidx];
       }
     }
     __syncthreads();
@@ -353,6 +476,10 @@ extern "C" g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k,
   G3_TRY_CUDA(cudaMemsetAsync(w->fa, 0, (size_t)nb * 8 + 8, s));
   G3_TRY_CUDA(cudaMemsetAsync(w->nx, 0, (size_t)nb * 8 + 8, s));
   G3_TRY_CUDA(cudaMemsetAsync(w->ctr, 0, 64, s));
+  if (w->items_cap < g->nnz / MS_CHUNK + 4) {
+    g3_set_error("g3_msbfs: workspace does not fit the graph");
+    return G3_ESTATE;
+  }
   ms_seed<<<1, 64, 0, s>>>(w->d_roots, k, n2o, nb, w->vis, w->fa, w->lv, w->qa, w->ctr, g->off);
   G3_CHECK_LAUNCH();
   uint64_t *F = w->fa, *Fn = w->fb;
@@ -369,15 +496,21 @@ extern "C" g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k,
       g3_set_error("g3_msbfs: a level exceeds 126, the int8 range of the output");
       return G3_ERANGE;
     }
-    G3_TRY_CUDA(cudaMemsetAsync(w->ctr, 0, 24, s));
+    G3_TRY_CUDA(cudaMemsetAsync(w->ctr, 0, 40, s));
     const bool pull = mf * (int64_t)o.push_alpha > g->nnz;
     const int8_t lnext = (int8_t)(L + 1);
     if (pull) {
       ms_pull<<<grid, 256, 0, s>>>(nb, g->off, g->col, F, w->vis, Fn, w->lv, lnext, full,
                                    o.pull_warp_deg, w->heavy, qn, w->ctr);
       G3_CHECK_LAUNCH();
-      ms_pull_heavy<<<grid, 256, 0, s>>>(w->heavy, w->ctr + 2, g->off, g->col, F, w->vis, Fn,
-                                         w->lv, lnext, full, qn, w->ctr);
+      ms_pull_heavy<<<grid, 256, 0, s>>>(w->heavy, g->off, g->col, F, w->vis, Fn, w->nx, w->lv,
+                                         lnext, full, qn, w->pend, w->items, w->ctr);
+      G3_CHECK_LAUNCH();
+      ms_pull_chunks<<<grid, 256, 0, s>>>(w->items, g->off, g->col, F, w->vis, w->nx, full,
+                                          w->ctr);
+      G3_CHECK_LAUNCH();
+      ms_pull_pending<<<G3_NUM_SMS, 256, 0, s>>>(w->pend, g->off, w->vis, Fn, w->nx, w->lv,
+                                                 lnext, qn, w->ctr);
       G3_CHECK_LAUNCH();
     } else {
       // Fn must be zero outside the new frontier: after a pull it is fully
@@ -386,7 +519,10 @@ extern "C" g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k,
       G3_TRY_CUDA(cudaMemsetAsync(Fn, 0, (size_t)nb * 8 + 8, s));
       // touched vertices are collected in the heavy buffer
       ms_push<<<g3_grid_for(qlen, 8, grid), 256, 0, s>>>(q, qlen, g->off, g->col, F, w->vis,
-                                                         w->nx, w->heavy, w->ctr + 2);
+                                                         w->nx, w->heavy, w->ctr, w->items);
+      G3_CHECK_LAUNCH();
+      ms_push_chunks<<<grid, 256, 0, s>>>(w->items, g->off, g->col, F, w->vis, w->nx, w->heavy,
+                                          w->ctr);
       G3_CHECK_LAUNCH();
       G3_TRY_CUDA(cudaMemcpyAsync(h + 2, w->ctr + 2, 8, cudaMemcpyDeviceToHost, s));
       G3_TRY_CUDA(cudaStreamSynchronize(s));

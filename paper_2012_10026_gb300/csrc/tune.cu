@@ -1,0 +1,417 @@
+// Autotuner: times candidate launch parameters on the device and keeps the
+// fastest per graph-size class in a small text cache. The paper tunes its
+// direction-switch parameters by a grid search over measured runs (Sec. 4);
+// this generalises that to the degree-bin thresholds, the scan direction of
+// the bottom-up step, the multi-source push/pull split and warp binning, and
+// the warp- vs CTA-per-graph split of the batched search.
+//
+// Cache file: one entry per line,
+//   g3tune1 <kind> <size_class> <deg_class> <p0> .. <p5> <points> <ms> <ms_default>
+// Lines that do not parse are ignored; a store rewrites the file through a
+// temporary file and a rename, replacing the entry with the same key.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "g3_internal.cuh"
+
+namespace {
+
+int32_t ilog2_floor(double x) {
+  if (!(x >= 1.0)) return 0;
+  return (int32_t)floor(log2(x));
+}
+
+bool parse_line(const char* line, g3_tune_entry* e) {
+  g3_tune_entry t;
+  memset(&t, 0, sizeof(t));
+  char tag[16] = {0};
+  const int got = sscanf(line, "%15s %d %d %d %d %d %d %d %d %d %d %f %f", tag, &t.kind,
+                         &t.size_class, &t.deg_class, &t.p[0], &t.p[1], &t.p[2], &t.p[3],
+                         &t.p[4], &t.p[5], &t.points, &t.ms, &t.ms_default);
+  if (got != 13 || strcmp(tag, "g3tune1") != 0) return false;
+  *e = t;
+  return true;
+}
+
+std::vector<g3_tune_entry> read_all(const char* path) {
+  std::vector<g3_tune_entry> out;
+  FILE* f = fopen(path, "r");
+  if (!f) return out;
+  char line[512];
+  while (fgets(line, sizeof(line), f)) {
+    g3_tune_entry e;
+    if (parse_line(line, &e)) out.push_back(e);
+  }
+  fclose(f);
+  return out;
+}
+
+bool same_key(const g3_tune_entry& a, const g3_tune_entry& b) {
+  return a.kind == b.kind && a.size_class == b.size_class && a.deg_class == b.deg_class;
+}
+
+// 256 MB written between timed runs so that no candidate starts with the
+// graph warm in the 129 MB L2.
+struct Flush {
+  void* p = nullptr;
+  size_t bytes = 256u << 20;
+  ~Flush() {
+    if (p) cudaFree(p);
+  }
+  g3_status init() {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      g3_set_error("autotune: cudaMalloc of the L2 flush buffer failed");
+      return G3_ENOMEM;
+    }
+    return G3_OK;
+  }
+  g3_status run(cudaStream_t s) {
+    G3_TRY_CUDA(cudaMemsetAsync(p, 1, bytes, s));
+    return G3_OK;
+  }
+};
+
+struct Events {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~Events() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  g3_status init() {
+    G3_TRY_CUDA(cudaEventCreate(&a));
+    G3_TRY_CUDA(cudaEventCreate(&b));
+    return G3_OK;
+  }
+};
+
+constexpr int kReps = 3;  // each candidate: the minimum of three timed runs
+
+g3_status cache_hit(const char* path, g3_tune_entry* key, bool* hit) {
+  *hit = false;
+  if (!path) return G3_OK;
+  int32_t found = 0;
+  G3_TRY(g3_tune_cache_lookup(path, key->kind, key->size_class, key->deg_class, key, &found));
+  if (found) {
+    key->points = 0;
+    *hit = true;
+  }
+  return G3_OK;
+}
+
+}  // namespace
+
+extern "C" g3_status g3_tune_cache_lookup(const char* path, int32_t kind, int32_t size_class,
+                                          int32_t deg_class, g3_tune_entry* out,
+                                          int32_t* found) {
+  if (!path || !out || !found) {
+    g3_set_error("g3_tune_cache_lookup: null argument");
+    return G3_EINVAL;
+  }
+  *found = 0;
+  g3_tune_entry key;
+  memset(&key, 0, sizeof(key));
+  key.kind = kind;
+  key.size_class = size_class;
+  key.deg_class = deg_class;
+  for (const g3_tune_entry& e : read_all(path)) {
+    if (same_key(e, key)) {  // the last matching line wins
+      *out = e;
+      *found = 1;
+    }
+  }
+  return G3_OK;
+}
+
+extern "C" g3_status g3_tune_cache_store(const char* path, const g3_tune_entry* e) {
+  if (!path || !e || e->kind < G3_TUNE_BFS || e->kind > G3_TUNE_BATCH) {
+    g3_set_error("g3_tune_cache_store: bad argument");
+    return G3_EINVAL;
+  }
+  // one line per key, the last one read winning, then the new entry
+  std::vector<g3_tune_entry> all;
+  for (const g3_tune_entry& x : read_all(path)) {
+    if (same_key(x, *e)) continue;
+    bool dup = false;
+    for (g3_tune_entry& y : all)
+      if (same_key(x, y)) {
+        y = x;
+        dup = true;
+      }
+    if (!dup) all.push_back(x);
+  }
+  all.push_back(*e);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) {
+    g3_set_error("g3_tune_cache_store: cannot write %s", tmp.c_str());
+    return G3_EINVAL;
+  }
+  bool ok = true;
+  for (const g3_tune_entry& x : all)
+    ok = ok && fprintf(f, "g3tune1 %d %d %d %d %d %d %d %d %d %d %.6g %.6g\n", x.kind,
+                       x.size_class, x.deg_class, x.p[0], x.p[1], x.p[2], x.p[3], x.p[4],
+                       x.p[5], x.points, x.ms, x.ms_default) > 0;
+  ok = (fclose(f) == 0) && ok;
+  if (!ok || rename(tmp.c_str(), path) != 0) {
+    remove(tmp.c_str());
+    g3_set_error("g3_tune_cache_store: cannot write %s", path);
+    return G3_EINVAL;
+  }
+  return G3_OK;
+}
+
+extern "C" g3_status g3_tune_key(int32_t kind, int64_t vertices, int64_t nnz, int32_t graphs,
+                                 int32_t* size_class, int32_t* deg_class) {
+  if (!size_class || !deg_class || vertices < 0 || nnz < 0 || graphs < 1) {
+    g3_set_error("g3_tune_key: bad argument");
+    return G3_EINVAL;
+  }
+  (void)kind;
+  const double v = (double)std::max<int64_t>(vertices, 1);
+  *size_class = ilog2_floor(v / graphs);
+  *deg_class = ilog2_floor((double)nnz / v);
+  return G3_OK;
+}
+
+// ------------------------------------------------------------------ BFS
+namespace {
+
+g3_status time_bfs(g3_graph* g, const int32_t* roots, int32_t nroots, const g3_bfs_opts& o,
+                   int32_t* parent, int32_t* level, Flush& fl, Events& ev, cudaStream_t s,
+                   float* best) {
+  *best = 1e30f;
+  for (int rep = 0; rep < kReps; ++rep) {
+    float tot = 0.f;
+    for (int32_t i = 0; i < nroots; ++i) {
+      G3_TRY(fl.run(s));
+      G3_TRY_CUDA(cudaEventRecord(ev.a, s));
+      G3_TRY(g3_bfs(g, roots[i], &o, parent, level, nullptr, 0, nullptr, s));
+      G3_TRY_CUDA(cudaEventRecord(ev.b, s));
+      G3_TRY_CUDA(cudaEventSynchronize(ev.b));
+      float ms = 0.f;
+      G3_TRY_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+      tot += ms;
+    }
+    *best = std::min(*best, tot);
+  }
+  return G3_OK;
+}
+
+void bfs_to_entry(const g3_bfs_opts& o, g3_tune_entry* e) {
+  e->p[0] = o.alpha;
+  e->p[1] = o.beta;
+  e->p[2] = o.t1;
+  e->p[3] = o.t2;
+  e->p[4] = o.t3;
+  e->p[5] = o.bu_reverse;
+}
+
+void entry_to_bfs(const g3_tune_entry& e, g3_bfs_opts* o) {
+  o->alpha = e.p[0];
+  o->beta = e.p[1];
+  o->t1 = e.p[2];
+  o->t2 = e.p[3];
+  o->t3 = e.p[4];
+  o->bu_reverse = e.p[5];
+}
+
+}  // namespace
+
+extern "C" g3_status g3_autotune_bfs(g3_graph* g, const int32_t* roots, int32_t nroots,
+                                     int32_t* parent, int32_t* level, const char* cache_path,
+                                     g3_bfs_opts* opts, g3_tune_entry* rec, void* stream) {
+  if (!g || !roots || nroots <= 0 || !parent || !level || !opts) {
+    g3_set_error("g3_autotune_bfs: bad argument");
+    return G3_EINVAL;
+  }
+  g3_tune_entry e;
+  memset(&e, 0, sizeof(e));
+  e.kind = G3_TUNE_BFS;
+  G3_TRY(g3_tune_key(e.kind, g->n_bfs, g->nnz, 1, &e.size_class, &e.deg_class));
+  bool hit = false;
+  G3_TRY(cache_hit(cache_path, &e, &hit));
+  if (hit) {
+    entry_to_bfs(e, opts);
+    if (rec) *rec = e;
+    return G3_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Flush fl;
+  Events ev;
+  G3_TRY(fl.init());
+  G3_TRY(ev.init());
+  // the controller the caller chose stays; the heuristic's parameters and
+  // the expansion parameters are searched one coordinate at a time, twice
+  g3_bfs_opts best = *opts;
+  float best_ms = 0.f;
+  G3_TRY(time_bfs(g, roots, nroots, best, parent, level, fl, ev, s, &best_ms));
+  e.ms_default = best_ms;
+  int points = 1;
+  static const int32_t alphas[] = {6, 10, 14, 20, 28, 40};
+  static const int32_t betas[] = {12, 18, 24, 36, 48};
+  static const int32_t bins[][3] = {{32, 1024, 32768}, {16, 512, 16384}, {64, 2048, 65536},
+                                    {32, 256, 8192},   {8, 256, 32768},   {32, 2048, 262144}};
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int c = 0; c < 4; ++c) {
+      const int count = c == 0 ? 6 : c == 1 ? 5 : c == 2 ? 6 : 2;
+      for (int i = 0; i < count; ++i) {
+        g3_bfs_opts o = best;
+        if (c == 0) o.alpha = alphas[i];
+        if (c == 1) o.beta = betas[i];
+        if (c == 2) {
+          o.t1 = bins[i][0];
+          o.t2 = bins[i][1];
+          o.t3 = bins[i][2];
+        }
+        if (c == 3) o.bu_reverse = i;
+        if (!memcmp(&o, &best, sizeof(o))) continue;
+        float ms = 0.f;
+        G3_TRY(time_bfs(g, roots, nroots, o, parent, level, fl, ev, s, &ms));
+        ++points;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = o;
+        }
+      }
+    }
+  }
+  *opts = best;
+  bfs_to_entry(best, &e);
+  e.points = points;
+  e.ms = best_ms;
+  if (cache_path) G3_TRY(g3_tune_cache_store(cache_path, &e));
+  if (rec) *rec = e;
+  return G3_OK;
+}
+
+// -------------------------------------------------------------- MS-BFS
+extern "C" g3_status g3_autotune_msbfs(g3_graph* g, const int32_t* roots, int32_t k,
+                                       int8_t* level, const char* cache_path,
+                                       g3_msbfs_opts* opts, g3_tune_entry* rec, void* stream) {
+  if (!g || !roots || k <= 0 || k > 64 || !level || !opts) {
+    g3_set_error("g3_autotune_msbfs: bad argument");
+    return G3_EINVAL;
+  }
+  g3_tune_entry e;
+  memset(&e, 0, sizeof(e));
+  e.kind = G3_TUNE_MSBFS;
+  G3_TRY(g3_tune_key(e.kind, g->n_bfs, g->nnz, 1, &e.size_class, &e.deg_class));
+  bool hit = false;
+  G3_TRY(cache_hit(cache_path, &e, &hit));
+  if (hit) {
+    opts->push_alpha = e.p[0];
+    opts->pull_warp_deg = e.p[1];
+    if (rec) *rec = e;
+    return G3_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Flush fl;
+  G3_TRY(fl.init());
+  auto time_one = [&](const g3_msbfs_opts& o, float* best) -> g3_status {
+    *best = 1e30f;
+    for (int rep = 0; rep < kReps; ++rep) {
+      G3_TRY(fl.run(s));
+      float ms = 0.f;
+      G3_TRY(g3_msbfs(g, roots, k, &o, level, nullptr, &ms, s));
+      *best = std::min(*best, ms);
+    }
+    return G3_OK;
+  };
+  g3_msbfs_opts best = *opts;
+  float best_ms = 0.f;
+  G3_TRY(time_one(best, &best_ms));
+  e.ms_default = best_ms;
+  int points = 1;
+  static const int32_t alphas[] = {2, 4, 8, 14, 24, 48, 1 << 30};
+  static const int32_t warp_degs[] = {16, 32, 64, 128, 256, 512, 1024, 1 << 30};
+  for (int32_t a : alphas)
+    for (int32_t d : warp_degs) {
+      g3_msbfs_opts o = *opts;
+      o.push_alpha = a;
+      o.pull_warp_deg = d;
+      if (!memcmp(&o, opts, sizeof(o))) continue;
+      float ms = 0.f;
+      G3_TRY(time_one(o, &ms));
+      ++points;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = o;
+      }
+    }
+  *opts = best;
+  e.p[0] = best.push_alpha;
+  e.p[1] = best.pull_warp_deg;
+  e.points = points;
+  e.ms = best_ms;
+  if (cache_path) G3_TRY(g3_tune_cache_store(cache_path, &e));
+  if (rec) *rec = e;
+  return G3_OK;
+}
+
+// --------------------------------------------------------------- batch
+extern "C" g3_status g3_autotune_batch(g3_batch* b, const int32_t* roots, int32_t* parent,
+                                       int32_t* level, const char* cache_path,
+                                       g3_batch_opts* opts, g3_tune_entry* rec, void* stream) {
+  if (!b || !roots || !parent || !level || !opts) {
+    g3_set_error("g3_autotune_batch: bad argument");
+    return G3_EINVAL;
+  }
+  int32_t G = 0;
+  int64_t N = 0, nnz = 0;
+  G3_TRY(g3_batch_info_get(b, &G, &N, &nnz));
+  g3_tune_entry e;
+  memset(&e, 0, sizeof(e));
+  e.kind = G3_TUNE_BATCH;
+  G3_TRY(g3_tune_key(e.kind, N, nnz, G, &e.size_class, &e.deg_class));
+  bool hit = false;
+  G3_TRY(cache_hit(cache_path, &e, &hit));
+  if (hit) {
+    opts->warp_max_n = e.p[0];
+    if (rec) *rec = e;
+    return G3_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Flush fl;
+  G3_TRY(fl.init());
+  auto time_one = [&](const g3_batch_opts& o, float* best) -> g3_status {
+    *best = 1e30f;
+    for (int rep = 0; rep < kReps + 1; ++rep) {  // the first run of a new value captures
+      G3_TRY(fl.run(s));
+      float ms = 0.f;
+      G3_TRY(g3_bfs_batch(b, roots, &o, parent, level, &ms, s));
+      if (rep > 0) *best = std::min(*best, ms);
+    }
+    return G3_OK;
+  };
+  g3_batch_opts best = *opts;
+  float best_ms = 0.f;
+  G3_TRY(time_one(best, &best_ms));
+  e.ms_default = best_ms;
+  int points = 1;
+  static const int32_t limits[] = {0, 64, 128, 256, 512, 1024, 2048};
+  for (int32_t w : limits) {
+    g3_batch_opts o = *opts;
+    o.warp_max_n = w;
+    if (!memcmp(&o, opts, sizeof(o))) continue;
+    float ms = 0.f;
+    G3_TRY(time_one(o, &ms));
+    ++points;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = o;
+    }
+  }
+  *opts = best;
+  e.p[0] = best.warp_max_n;
+  e.points = points;
+  e.ms = best_ms;
+  if (cache_path) G3_TRY(g3_tune_cache_store(cache_path, &e));
+  if (rec) *rec = e;
+  return G3_OK;
+}

@@ -90,6 +90,15 @@ def regret(meta, choice_bu):
     return float(sum((tb if c else tt) - min(tt, tb) for (tt, tb, _), c in zip(meta, choice_bu)))
 
 
+MARGINS = [0.0, 0.05, 0.1, 0.15, 0.2, 0.3, 0.5, 0.75, 1.0, 1e9]
+
+
+def gated(o0, meta, margin):
+    """Direction choices when the network decides only outside the margin
+    (|predicted ln(t_BU/t_TD)| > margin) and the alpha/beta rule otherwise."""
+    return [(x < 0) if abs(x) > margin else (d == 1) for x, (_, _, d) in zip(o0, meta)]
+
+
 def train(X, Y, steps=3000, lr=1e-2, seed=0, device="cuda"):
     import torch
     p = torch.from_numpy(init_params(seed)).to(device)
@@ -138,6 +147,16 @@ def main():
         "train_regret_ms_heuristic": regret(meta, heur_bu),
         "collect_s": t1 - t0, "train_s": time.time() - t1,
     }
+    # margin chosen on a held-out graph of the largest training scale (a new
+    # seed and new roots), never on the evaluation scale
+    rows, nb = collect(max(args.scales), 97, args.roots, 98)
+    Xh, _, mh = dataset([(st, nb) for st in rows])
+    oh = g3.g3_mlp_forward(p, torch.from_numpy(Xh).cuda()).cpu().numpy()[:, 0]
+    table = {str(m): regret(mh, gated(oh, mh, m)) for m in MARGINS}
+    best_m = min(MARGINS, key=lambda m: (table[str(m)], m))
+    summary["holdout"] = {"scale": max(args.scales), "levels": int(len(Xh)),
+                          "regret_ms_by_margin": table}
+    summary["mlp_margin"] = int(round(min(best_m, 1e6) * 1000))
     if args.eval_scale:
         # held-out graph: per-level times of both directions under the
         # heuristic's path; regret of each controller's choices on it
@@ -147,6 +166,7 @@ def main():
         summary["eval"] = {
             "scale": args.eval_scale, "roots": args.eval_roots, "levels": int(len(Xe)),
             "regret_ms_learned": regret(me, oe[:, 0] < 0),
+            "regret_ms_learned_gated": regret(me, gated(oe[:, 0], me, best_m)),
             "regret_ms_heuristic": regret(me, [d == 1 for (_, _, d) in me]),
             "best_total_ms": float(sum(min(tt, tb) for (tt, tb, _) in me)),
         }

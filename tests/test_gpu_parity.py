@@ -224,6 +224,40 @@ def test_learned_controller_random_params_stays_exact(kron16):
                 assert a["dir"] == (g3.G3_DIR_BU if o[0] < 0 else g3.G3_DIR_TD)
 
 
+@pytest.mark.parametrize("margin", [0, 300, 2000, 10 ** 9])
+def test_learned_controller_margin_falls_back_to_rule(kron16, margin):
+    """Inside the margin the alpha/beta rule decides (from the directions
+    actually taken); outside it the network's sign decides."""
+    from oracle import mlp
+    K = kron16
+    ref = K["ref"]
+    params = torch.from_numpy(mlp.init_params(5).astype(np.float32)).cuda()
+    for root in K["roots"][:6].tolist():
+        parent, level, st = run_bfs(K["g"], root, K["n"], max_stats=64,
+                                    controller=g3.G3_CTRL_LEARNED, mlp_params=params,
+                                    mlp_margin=margin)
+        _, lref = oracle.bfs(ref["off"], ref["col"], root)
+        assert np.array_equal(level, lref)
+        assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
+        assert st[0]["dir"] == g3.G3_DIR_TD
+        for L in range(1, len(st)):
+            a, prev = st[L], st[L - 1]
+            o0 = a["mlp_out"][0]
+            if abs(abs(o0) - margin / 1000) < 1e-4:
+                continue  # too close to the margin to call
+            if abs(o0) > margin / 1000:
+                want = g3.G3_DIR_BU if o0 < 0 else g3.G3_DIR_TD
+            elif prev["dir"] == g3.G3_DIR_TD:
+                want = g3.G3_DIR_BU if a["m_f"] * 14 > a["m_u"] else g3.G3_DIR_TD
+            else:
+                shrink = a["n_f"] < prev["n_f"] and a["n_f"] * 24 < ref["n_plus"]
+                want = g3.G3_DIR_TD if shrink else g3.G3_DIR_BU
+            assert a["dir"] == want, (root, L, o0)
+    if margin == 10 ** 9:  # never overrides: the heuristic's directions
+        lnew = _levels_new(ref, lref)
+        assert [a["dir"] for a in st] == direction.heuristic_directions(ref["off_r"], lnew)
+
+
 def test_bad_edge_endpoint_rejected():
     with pytest.raises(g3.G3Error) as e:
         g3.g3_build_csr(_dev([0, 1]), _dev([1, 5]), 5)
