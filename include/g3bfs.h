@@ -145,7 +145,9 @@ typedef struct {
                                alpha/beta rule's direction only when its
                                predicted |ln(t_BU / t_TD)| exceeds
                                mlp_margin / 1000 (0, the default: always) */
-  int32_t reserved[6];
+  int32_t mlp_bins;         /* learned controller: 1 (default) the network also
+                               picks the top-down bins; 0 t1..t3 stay */
+  int32_t reserved[5];
 } g3_bfs_opts;
 
 /* Fills the defaults listed above. */

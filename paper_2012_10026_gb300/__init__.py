@@ -43,7 +43,7 @@ class g3_bfs_opts(ctypes.Structure):
                 ("t3", ctypes.c_int32), ("bu_reverse", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
                 ("record_both", ctypes.c_int32), ("mlp_margin", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("mlp_bins", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class g3_level_stats(ctypes.Structure):

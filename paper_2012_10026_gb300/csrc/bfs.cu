@@ -94,13 +94,44 @@ struct Bufs {
   const int32_t* o2n;  // old_of_new (parents are stored as original IDs), or NULL
 };
 
+// (parent's original ID, level) of a labelled vertex packed into one 32-bit
+// word, parent << bits | min(level, lmax) with lmax = 2^bits - 1 and bits =
+// 32 - (bits of n - 1); a level >= lmax is also kept in deep[x]. At SCALE 26
+// the word holds levels up to 62 by itself, and the packed array (4 B per
+// vertex) is half the size the output pass has to gather from.
+struct PlOut {
+  uint32_t* pl;
+  int32_t* deep;
+  int32_t bits;
+};
+
+__device__ __forceinline__ void pl_put(const PlOut& o, int32_t x, int32_t parent,
+                                       int32_t level) {
+  const uint32_t lmax = (1u << o.bits) - 1u;
+  const uint32_t code = (uint32_t)level < lmax ? (uint32_t)level : lmax;
+  o.pl[x] = ((uint32_t)parent << o.bits) | code;
+  if ((uint32_t)level >= lmax) o.deep[x] = level;
+}
+
+__device__ __forceinline__ int2 pl_decode(const PlOut& o, uint32_t w, int32_t x) {
+  const uint32_t lmax = (1u << o.bits) - 1u;
+  const uint32_t code = w & lmax;
+  return make_int2((int32_t)(w >> o.bits), code == lmax ? __ldg(&o.deep[x]) : (int32_t)code);
+}
+
+static int32_t pl_bits(int32_t n) {
+  int bp = 1;
+  while (bp < 31 && ((int64_t)1 << bp) < (int64_t)n) ++bp;
+  return 32 - bp;
+}
+
 struct g3_bfs_ws {
   int32_t nb;
   int64_t nwords;
   uint32_t *visited, *fa, *fb, *vis_save;
   int32_t *qa, *qb, *bins;  // bins: 3 segments of nb entries (warp, CTA, grid)
   int64_t* goff;            // edge offset of each grid-bin vertex
-  int2* pl;                 // (parent, level) per BFS-graph vertex
+  PlOut plo;                // packed (parent, level) per BFS-graph vertex
   int2* nplus;              // (last row entry or -1, degree): Algorithm 6's neighbors+
   int32_t *out_parent, *out_level;  // staging for host outputs (n entries)
   Ctrl* ctrl;
@@ -117,7 +148,7 @@ struct g3_bfs_ws {
 void g3_bfs_ws_free(g3_bfs_ws* ws) {
   if (!ws) return;
   void* all[] = {ws->visited,    ws->fa,        ws->fb,   ws->vis_save, ws->qa,
-                 ws->qb,         ws->bins,      ws->pl,   ws->out_parent,
+                 ws->qb,         ws->bins,      ws->plo.pl, ws->plo.deep, ws->out_parent,
                  ws->out_level,  ws->ctrl,      ws->goff, ws->nplus,
                  ws->log};
   for (void* p : all)
@@ -247,7 +278,7 @@ __device__ __forceinline__ void log_frontier(LevelLog* log, const Ctrl* c) {
 // Sets up F_0 = {root} (root_new < 0 or >= nb: no BFS-graph vertex). The
 // visited bitmap has been cleared on the stream before.
 __global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, int64_t nnz,
-                         const int64_t* off, uint32_t* visited, int2* pl, int32_t* q, Ctrl* c,
+                         const int64_t* off, uint32_t* visited, PlOut plo, int32_t* q, Ctrl* c,
                          LevelLog* log, int t1, int t2, int t3, int cap) {
   int32_t r = new_of_old ? new_of_old[root] : root;
   memset(c, 0, sizeof(Ctrl));
@@ -266,7 +297,7 @@ __global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, in
     return;
   }
   visited[r >> 5] |= 1u << (r & 31);
-  pl[r] = make_int2(root, 0);  // parents are kept as original IDs
+  pl_put(plo, r, root, 0);  // parents are kept as original IDs
   q[0] = r;
   long long d = off[r + 1] - off[r];
   c->nf = 1;
@@ -286,7 +317,7 @@ struct TdArgs {
   const int64_t* off;
   const int32_t* col;
   uint32_t* visited;
-  int2* pl;
+  PlOut plo;
   int32_t lnext;
   int32_t* qnext;
   Ctrl* c;
@@ -343,7 +374,7 @@ __device__ __forceinline__ void td_visit(const TdArgs& a, WarpQueue& q, StatAcc&
                                          int32_t w, int32_t v) {
   bool claim = has && td_claim(a.visited, w);
   if (claim) {
-    a.pl[w] = make_int2(v, a.lnext);  // v: the parent's original ID
+    pl_put(a.plo, w, v, a.lnext);  // v: the parent's original ID
     acc.add_vertex(w, a.off[w + 1] - a.off[w]);
   }
   wq_push(q, claim, w, a.qnext, &a.c->q_len);
@@ -375,19 +406,20 @@ __device__ __forceinline__ void td_row_vec4(const TdArgs& a, WarpQueue& q, StatA
 #define GP_MASK ((1ull << GP_SHIFT) - 1ull)
 
 __device__ __forceinline__ TdArgs td_args(const int64_t* off, const int32_t* col,
-                                          uint32_t* visited, int2* pl, const Bufs& B, Ctrl* c) {
-  return TdArgs{off, col, visited, pl, c->level + 1, (c->qsel ? B.q[0] : B.q[1]), c, B.o2n};
+                                          uint32_t* visited, const PlOut& plo, const Bufs& B,
+                                          Ctrl* c) {
+  return TdArgs{off, col, visited, plo, c->level + 1, (c->qsel ? B.q[0] : B.q[1]), c, B.o2n};
 }
 
 // Thread per frontier vertex: degree < t1 expanded here, larger degrees
 // binned (warp / CTA / grid).
 __global__ void __launch_bounds__(256) td_front(const int64_t* __restrict__ off,
                                                 const int32_t* __restrict__ col,
-                                                uint32_t* visited, int2* pl, Bufs B,
+                                                uint32_t* visited, PlOut plo, Bufs B,
                                                 int32_t* bins, int64_t* goff, int64_t nb1,
                                                 Ctrl* c) {
   if (c->dir != G3_DIR_TD) return;
-  const TdArgs a = td_args(off, col, visited, pl, B, c);
+  const TdArgs a = td_args(off, col, visited, plo, B, c);
   const int32_t* __restrict__ q = (c->qsel ? B.q[1] : B.q[0]);
   const int64_t qlen = c->nf;
   const int t1 = c->t1, t2 = c->t2, t3 = c->t3;
@@ -429,12 +461,12 @@ __global__ void __launch_bounds__(256) td_front(const int64_t* __restrict__ off,
 // warps of the grid (Algorithm 4's even split, applied to every hub at once).
 __global__ void __launch_bounds__(256) td_bins(const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
-                                               uint32_t* visited, int2* pl, Bufs B,
+                                               uint32_t* visited, PlOut plo, Bufs B,
                                                const int32_t* __restrict__ bins,
                                                const int64_t* __restrict__ goff, int64_t nb1,
                                                Ctrl* c) {
   if (c->dir != G3_DIR_TD) return;
-  const TdArgs a = td_args(off, col, visited, pl, B, c);
+  const TdArgs a = td_args(off, col, visited, plo, B, c);
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -505,7 +537,7 @@ template <int REV>
 __global__ void __launch_bounds__(256, 5) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
                                                Bufs B, const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
-                                               const int2* __restrict__ nplus, int2* pl,
+                                               const int2* __restrict__ nplus, PlOut plo,
                                                Ctrl* c) {
   if (c->dir != G3_DIR_BU) return;
   const uint32_t* __restrict__ fcur = (c->fsel ? B.f[1] : B.f[0]);
@@ -583,11 +615,11 @@ __global__ void __launch_bounds__(256, 5) bu_pull(int32_t nb, int64_t nwords, ui
     const uint32_t n0 = __ballot_sync(0xffffffffu, p0 >= 0);
     const uint32_t n1 = __ballot_sync(0xffffffffu, p1 >= 0);
     if (p0 >= 0) {
-      pl[v0] = make_int2(o2n ? __ldg(&o2n[p0]) : p0, lnext);
+      pl_put(plo, (int32_t)v0, o2n ? __ldg(&o2n[p0]) : p0, lnext);
       acc.add_vertex((int32_t)v0, d0);
     }
     if (p1 >= 0) {
-      pl[v1] = make_int2(o2n ? __ldg(&o2n[p1]) : p1, lnext);
+      pl_put(plo, (int32_t)v1, o2n ? __ldg(&o2n[p1]) : p1, lnext);
       acc.add_vertex((int32_t)v1, d1);
     }
     if (lane == 0) {
@@ -675,6 +707,7 @@ struct CtrlArgs {
   int controller, alpha, beta;
   const float* mlp;
   float mlp_margin;
+  int mlp_bins;
   int t1, t2, t3;
   LevelLog* log;
   int graph_mode;
@@ -747,9 +780,11 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
           a3 = clamp_thr(out[3], 10, 26);
       if (a2 <= a1) a2 = a1 * 2;
       if (a3 <= a2) a3 = a2 * 2;
-      c->t1 = a1;
-      c->t2 = a2;
-      c->t3 = a3;
+      if (A.mlp_bins) {
+        c->t1 = a1;
+        c->t2 = a2;
+        c->t3 = a3;
+      }
     }
     __syncwarp();
   }
@@ -774,15 +809,14 @@ __global__ void bfs_select(const Ctrl* c, cudaGraphConditionalHandle h_mode) {
 // --------------------------------------------------------- output mapping
 __global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
                               const int32_t* __restrict__ new_of_old,
-                              const int32_t* __restrict__ old_of_new,
-                              const uint32_t* __restrict__ visited,
-                              const int2* __restrict__ pl, int32_t* parent, int32_t* level) {
+                              const uint32_t* __restrict__ visited, PlOut plo,
+                              int32_t* parent, int32_t* level) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     int32_t p = -1, l = -1;
     const int32_t x = new_of_old ? new_of_old[v] : (int32_t)v;
     if (x < nb && ((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u)) {
-      const int2 t = pl[x];
+      const int2 t = pl_decode(plo, plo.pl[x], x);
       p = t.x;
       l = t.y;
     }
@@ -796,16 +830,15 @@ __global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
 }
 
 // Same mapping, four consecutive original IDs per thread: one 128-bit load
-// of new_of_old, four independent gathers of (parent, level) and of the
-// parent's original ID in flight at once (the random gathers are what bounds
-// this pass, so their latency has to overlap), 128-bit stores. parent and
-// level must be 16-byte aligned.
+// of new_of_old, four independent gathers of the packed (parent, level) word
+// in flight at once (the random gathers are what bounds this pass, so their
+// latency has to overlap), 128-bit stores. parent and level must be 16-byte
+// aligned.
 __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int32_t root,
                                                       const int32_t* __restrict__ new_of_old,
-                                                      const int32_t* __restrict__ old_of_new,
                                                       const uint32_t* __restrict__ visited,
-                                                      const int2* __restrict__ pl,
-                                                      int32_t* parent, int32_t* level) {
+                                                      PlOut plo, int32_t* parent,
+                                                      int32_t* level) {
   const int64_t n4 = n >> 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -824,14 +857,15 @@ __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       r[k] = x[k] < nb && ((__ldg(&visited[x[k] >> 5]) >> (x[k] & 31)) & 1u);
-    int2 t[4];
+    uint32_t w[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) t[k] = r[k] ? __ldg(&pl[x[k]]) : make_int2(-1, -1);
+    for (int k = 0; k < 4; ++k) w[k] = r[k] ? __ldg(&plo.pl[x[k]]) : 0u;
     int p[4], l[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      p[k] = r[k] ? t[k].x : -1;
-      l[k] = t[k].y;
+      const int2 t = r[k] ? pl_decode(plo, w[k], x[k]) : make_int2(-1, -1);
+      p[k] = t.x;
+      l[k] = t.y;
     }
     if ((root >> 2) == i) {
       p[root & 3] = root;
@@ -846,7 +880,7 @@ __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int
     int32_t p = -1, l = -1;
     const int32_t xv = new_of_old ? new_of_old[v] : (int32_t)v;
     if (xv < nb && ((__ldg(&visited[xv >> 5]) >> (xv & 31)) & 1u)) {
-      const int2 t = pl[xv];
+      const int2 t = pl_decode(plo, plo.pl[xv], xv);
       p = t.x;
       l = t.y;
     }
@@ -873,6 +907,7 @@ extern "C" void g3_bfs_opts_default(g3_bfs_opts* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
   o->controller = G3_CTRL_HEURISTIC;
+  o->mlp_bins = 1;
   o->alpha = 14;
   o->beta = 24;
   o->t1 = 32;
@@ -897,6 +932,7 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
   g3_bfs_ws* ws = (g3_bfs_ws*)calloc(1, sizeof(g3_bfs_ws));
   if (!ws) return G3_ENOMEM;
   ws->nb = g->n_bfs;
+  ws->plo.bits = pl_bits(g->n);
   ws->nwords = ((int64_t)g->n_bfs + 31) / 32;
   const size_t nb1 = (size_t)g->n_bfs + 4, nw = (size_t)ws->nwords + 4, n1 = (size_t)g->n + 4;
   struct {
@@ -906,7 +942,8 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
       {(void**)&ws->visited, nw * 4},        {(void**)&ws->fa, nw * 4},
       {(void**)&ws->fb, nw * 4},             {(void**)&ws->vis_save, nw * 4},
       {(void**)&ws->qa, nb1 * 4},            {(void**)&ws->qb, nb1 * 4},
-      {(void**)&ws->bins, nb1 * 4 * 3},      {(void**)&ws->pl, nb1 * 8},
+      {(void**)&ws->bins, nb1 * 4 * 3},      {(void**)&ws->plo.pl, nb1 * 4},
+      {(void**)&ws->plo.deep, nb1 * 4},
       {(void**)&ws->nplus, nb1 * 8},
       {(void**)&ws->goff, nb1 * 8},          {(void**)&ws->out_parent, n1 * 4},
       {(void**)&ws->out_level, n1 * 4},
@@ -982,7 +1019,7 @@ struct Launch {
 static CtrlArgs ctrl_args(const Launch& S, int graph_mode, cudaGraphConditionalHandle h_loop) {
   return CtrlArgs{S.ws->nb,     S.g->nnz,        S.o->controller,
                   S.o->alpha,   S.o->beta,       S.o->mlp_params,
-                  S.o->mlp_margin * 1e-3f,       S.o->t1,
+                  S.o->mlp_margin * 1e-3f,       S.o->mlp_bins,   S.o->t1,
                   S.o->t2,      S.o->t3,         S.ws->log,
                   graph_mode,   h_loop};
 }
@@ -1007,19 +1044,19 @@ static g3_status launch_level(const Launch& S, int mode, int64_t nf, cudaEvent_t
   if (ev_mid) G3_TRY_CUDA(cudaEventRecord(ev_mid, s));
   if (mode == MODE_TD_Q || mode == MODE_TD_B) {
     td_front<<<cap_grid(nf, 256, ws->grid_front), 256, 0, s>>>(
-        S.g->off, S.g->col, ws->visited, ws->pl, S.B, ws->bins, ws->goff, S.nb1, c);
+        S.g->off, S.g->col, ws->visited, ws->plo, S.B, ws->bins, ws->goff, S.nb1, c);
     G3_CHECK_LAUNCH();
-    td_bins<<<ws->grid_bins, 256, 0, s>>>(S.g->off, S.g->col, ws->visited, ws->pl, S.B,
+    td_bins<<<ws->grid_bins, 256, 0, s>>>(S.g->off, S.g->col, ws->visited, ws->plo, S.B,
                                           ws->bins, ws->goff, S.nb1, c);
     G3_CHECK_LAUNCH();
   } else {
     const int grid = cap_grid(ws->nwords, 16, ws->grid_bu);
     if (S.o->bu_reverse)
       bu_pull<1><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.B, S.g->off, S.g->col,
-                                      ws->nplus, ws->pl, c);
+                                      ws->nplus, ws->plo, c);
     else
       bu_pull<0><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.B, S.g->off, S.g->col,
-                                      ws->nplus, ws->pl, c);
+                                      ws->nplus, ws->plo, c);
     G3_CHECK_LAUNCH();
   }
   return G3_OK;
@@ -1049,7 +1086,8 @@ struct NodeParams {
 static bool same_opts(const g3_bfs_opts& a, const g3_bfs_opts& b) {
   return a.controller == b.controller && a.alpha == b.alpha && a.beta == b.beta &&
          a.t1 == b.t1 && a.t2 == b.t2 && a.t3 == b.t3 && a.bu_reverse == b.bu_reverse &&
-         a.mlp_params == b.mlp_params && a.mlp_margin == b.mlp_margin;
+         a.mlp_params == b.mlp_params && a.mlp_margin == b.mlp_margin &&
+         a.mlp_bins == b.mlp_bins;
 }
 
 // Builds the level loop: WHILE(h_loop) { bfs_select -> SWITCH(h_mode) {
@@ -1075,8 +1113,8 @@ static g3_status build_graph(Launch& S) {
   void* a_conv[] = {&S.B, &nwords, &c};
   void* a_clear[] = {&S.B, &nwords, &c};
   void* a_q2b[] = {&S.B, &c};
-  void* a_td[] = {&off, &col, &ws->visited, &ws->pl, &S.B, &ws->bins, &ws->goff, &S.nb1, &c};
-  void* a_bu[] = {&nb, &nwords, &ws->visited, &S.B, &off, &col, &ws->nplus, &ws->pl, &c};
+  void* a_td[] = {&off, &col, &ws->visited, &ws->plo, &S.B, &ws->bins, &ws->goff, &S.nb1, &c};
+  void* a_bu[] = {&nb, &nwords, &ws->visited, &S.B, &off, &col, &ws->nplus, &ws->plo, &c};
   CtrlArgs ca;
   void* a_ctl[] = {&c, &ca};
   void* a_sel[] = {&c, &h_mode};
@@ -1228,7 +1266,7 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
 
   G3_TRY_CUDA(cudaMemsetAsync(ws->visited, 0, (size_t)(ws->nwords + 1) * 4, s));
   bfs_root<<<1, 1, 0, s>>>(g->relabelled ? g->new_of_old : nullptr, root, nb, g->nnz, g->off,
-                           ws->visited, ws->pl, ws->qa, ws->ctrl, ws->log, o->t1, o->t2, o->t3,
+                           ws->visited, ws->plo, ws->qa, ws->ctrl, ws->log, o->t1, o->t2, o->t3,
                            host_driven ? 0x7fffffff : GRAPH_LEVEL_CAP);
   G3_CHECK_LAUNCH();
 
@@ -1267,13 +1305,11 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   int32_t* ol = dev_l ? level : ws->out_level;
   if ((((uintptr_t)op | (uintptr_t)ol) & 15) == 0) {
     bfs_translate4<<<cap_grid((g->n + 3) / 4, 256, ws->grid_tr4), 256, 0, s>>>(
-        g->n, nb, root, g->relabelled ? g->new_of_old : nullptr,
-        g->relabelled ? g->old_of_new : nullptr, ws->visited, ws->pl, op, ol);
+        g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op, ol);
     G3_CHECK_LAUNCH();
   } else {  // outputs not 16-byte aligned
     bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, s>>>(
-        g->n, nb, root, g->relabelled ? g->new_of_old : nullptr,
-        g->relabelled ? g->old_of_new : nullptr, ws->visited, ws->pl, op, ol);
+        g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op, ol);
     G3_CHECK_LAUNCH();
   }
   if (!dev_p)

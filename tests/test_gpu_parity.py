@@ -324,3 +324,26 @@ def test_deep_graph_beyond_graph_level_cap():
         assert oracle.validate(off, col, 0, parent, level) == 0
         assert len(st) == 8 and st[7]["n_f"] == 1
         g.free()
+
+
+@pytest.mark.parametrize("relabel", [True, False])
+@pytest.mark.parametrize("ctrl", ["heuristic", "topdown", "bottomup"])
+def test_levels_past_the_packed_word(relabel, ctrl):
+    # n = 2^26 leaves 6 level bits in the packed (parent, level) word, so
+    # levels from 63 on come from the side table; a 300-vertex path spread
+    # over the ID range, searched from its 101st vertex, reaches level 199
+    n, k, mid = 1 << 26, 300, 100
+    ids = ((np.arange(k, dtype=np.int64) * 223_001 + 17) % n).astype(np.int32)
+    g = gpu_pipeline(ids[:-1], ids[1:], n, relabel)
+    c = {"heuristic": g3.G3_CTRL_HEURISTIC, "topdown": g3.G3_CTRL_TOPDOWN,
+         "bottomup": g3.G3_CTRL_BOTTOMUP}[ctrl]
+    parent, level, _ = run_bfs(g, int(ids[mid]), n, controller=c)
+    want = np.full(n, -1, np.int32)
+    want[ids] = np.abs(np.arange(k) - mid)
+    assert np.array_equal(level, want)
+    pw = np.full(n, -1, np.int32)
+    pos = np.arange(k)
+    pw[ids] = ids[np.clip(np.where(pos > mid, pos - 1, pos + 1), 0, k - 1)]
+    pw[ids[mid]] = ids[mid]
+    assert np.array_equal(parent, pw)
+    g.free()
