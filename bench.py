@@ -36,6 +36,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "harmonic-mean GTEPS over 64 roots, Kronecker SCALE 26; learned vs plain BFS"
 L2_BYTES = 129 * 1024 * 1024
 FALLBACK_HBM_GBS = 6800.0
 
@@ -67,6 +68,8 @@ def parse_args():
                     help="kron: the single-root headline; msbfs: bit-sliced multi-source "
                          "BFS on a Chung-Lu graph; batch: many small graphs in one launch")
     ap.add_argument("--ms-log2n", type=int, default=24, help="msbfs: Chung-Lu 2^k vertices")
+    ap.add_argument("--tune-bfs", type=int, default=1,
+                    help="kron: autotune alpha/beta/bins/scan order first (cached)")
     ap.add_argument("--msbfs-compare", type=int, default=1,
                     help="kron: also time the roots as one bit-sliced multi-source pass")
     ap.add_argument("--ms-roots", type=int, default=256, help="msbfs: sources (64 per launch)")
@@ -151,6 +154,25 @@ def level_bytes(st, nb):
     return 4 * st["n_f"] + 16 * st["n_f"] + 8 * st["m_f"] + 16 * st["n_next"]
 
 
+def _max_over_ranks(dist, x):
+    """Maximum of x over the ranks (x itself without a process group)."""
+    if not dist:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_hm_gteps(dist, world, m, t_ms):
+    """Whole-job harmonic-mean GTEPS of `world` replicas that each searched
+    the same roots: every rank's sum of t/m, the slowest rank's taken, and
+    world x (searches per rank) searches over it."""
+    norm = sum((t / 1e3) / mm for mm, t in zip(m, t_ms))
+    return world * len(m) / _max_over_ranks(dist, norm) / 1e9
+
+
 def harmonic_gteps(m, t_ms):
     return len(m) / sum((t / 1e3) / mm for mm, t in zip(m, t_ms)) / 1e9
 
@@ -226,7 +248,7 @@ def reference_arm(args, rank, world):
             tms.append(dt * 1e3)
     v = harmonic_gteps(ms, tms)
     line = {
-        "impl": "reference", "metric": "harmonic-mean GTEPS over 64 roots, Kronecker SCALE 26",
+        "impl": "reference", "metric": METRIC,
         "value": v, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(tms) / len(tms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -289,20 +311,33 @@ def gpu_arm(args, rank, world):
     args.controller_used = name
     ctrl = {"heuristic": g3.G3_CTRL_HEURISTIC, "learned": g3.G3_CTRL_LEARNED,
             "topdown": g3.G3_CTRL_TOPDOWN, "bottomup": g3.G3_CTRL_BOTTOMUP}[name]
-    kw = dict(controller=ctrl, bu_reverse=args.bu_reverse)
-    mlp_t = None
-    if ctrl == g3.G3_CTRL_LEARNED:
-        with open(args.mlp) as f:
-            mj = json.load(f)
-        mlp_t = torch.tensor(mj["params"], dtype=torch.float32, device="cuda")
-        kw["mlp_params"] = mlp_t
-        kw["mlp_margin"] = int(mj.get("mlp_margin", 0))
-    opts = g3.opts(**kw)  # default path: the level loop runs as one CUDA graph
-    opts_timed = g3.opts(timing=1, **kw)  # host-driven, CUDA events around each level
-    plain_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, bu_reverse=args.bu_reverse)
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
     level = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # autotuned alpha/beta, bins and scan order for this graph-size class
+    # (untimed; 16 tuning roots drawn apart from the timed ones; cached)
+    base = dict(bu_reverse=args.bu_reverse)
+    tune_rec, t_tune = None, 0.0
+    if args.tune_bfs:
+        t_tune = time.perf_counter()
+        troots = graphgen.pick_roots(flags, 16, args.root_seed + 1000).tolist()
+        topts, tune_rec = g3.autotune_bfs(g, troots, parent, level, args.tune_cache or None,
+                                          g3.opts(bu_reverse=args.bu_reverse))
+        t_tune = time.perf_counter() - t_tune
+        base = dict(alpha=topts.alpha, beta=topts.beta, t1=topts.t1, t2=topts.t2, t3=topts.t3,
+                    bu_reverse=topts.bu_reverse)
+    kw = dict(controller=ctrl, **base)
+    mlp_t, learned_note = None, None
+    if ctrl == g3.G3_CTRL_LEARNED:
+        from paper_2012_10026_gb300.train_controller import controller_opts
+        lo, mlp_t, learned_note = controller_opts(args.mlp, info["n_bfs"], **base)
+        kw.update(mlp_params=mlp_t, mlp_margin=lo.mlp_margin, mlp_bins=lo.mlp_bins)
+    opts = g3.opts(**kw)  # default path: the level loop runs as one CUDA graph
+    opts_timed = g3.opts(timing=1, **kw)  # host-driven, CUDA events around each level
+    # the plain method: the alpha/beta rule on the same tuned options, and
+    # with the library defaults
+    plain_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, **base)
+    default_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, bu_reverse=args.bu_reverse)
 
     # m_r per root (bookkeeping, outside any timed region)
     m_r = {}
@@ -360,14 +395,22 @@ def gpu_arm(args, rank, world):
         plain_t = []
         for _ in range(args.steps):
             plain_t += one_step(plain_opts, 0)[0]
+    default_t = None
+    if args.tune_bfs:
+        for _ in range(args.warmup):
+            one_step(default_opts, 0)
+        torch.cuda.synchronize()
+        default_t = []
+        for _ in range(args.steps):
+            default_t += one_step(default_opts, 0)[0]
     # the same 64 roots as one bit-sliced multi-source pass (after the timed
     # region; autotuned push/pull split and warp binning)
     msb = None
     if len(roots) <= 64 and args.msbfs_compare:
         lv8 = torch.empty((len(roots), n), dtype=torch.int8, device="cuda")
-        t_tune = time.perf_counter()
+        t_mtune = time.perf_counter()
         mopts, mrec = g3.autotune_msbfs(g, roots, lv8, args.tune_cache or None)
-        t_tune = time.perf_counter() - t_tune
+        t_mtune = time.perf_counter() - t_mtune
         mt = []
         for i in range(args.warmup + args.steps):
             flush.fill_(1)
@@ -389,19 +432,13 @@ def gpu_arm(args, rank, world):
                "single_root_aggregate_gteps": m_sum / (single / 1e3) / 1e9,
                "single_root_total_ms": single, "levels_equal_single_root": same,
                "push_alpha": mopts.push_alpha, "pull_warp_deg": mopts.pull_warp_deg,
-               "autotune": dict(mrec.to_dict(), seconds=t_tune)}
+               "autotune": dict(mrec.to_dict(), seconds=t_mtune)}
     if dist:
         dist.barrier()
     clocks = stop_clock_sampler(sampler, clk_path, local)
     ms = [m_r[r] for _ in range(args.steps) for r in roots]
     hm = harmonic_gteps(ms, all_t)
-    # whole-job value: replicas run the same work; take the slowest rank
-    norm = sum((t / 1e3) / mm for mm, t in zip(ms, all_t))
-    if dist:
-        tt = torch.tensor([norm], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        norm = float(tt.item())
-    value = world * len(ms) / norm / 1e9
+    value = replica_hm_gteps(dist, world, ms, all_t)
 
     # roofline of the dominant kernel
     nb = info["n_bfs"]
@@ -469,7 +506,7 @@ def gpu_arm(args, rank, world):
     if rank == 0:
         levels = [len(st) for st in all_st]
         line = {
-            "metric": "harmonic-mean GTEPS over 64 roots, Kronecker SCALE 26; learned vs plain BFS",
+            "metric": METRIC,
             "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sum(all_t) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -499,7 +536,15 @@ def gpu_arm(args, rank, world):
             "msbfs_same_roots": msb,
             "plain_heuristic": None if plain_t is None else {
                 "value": harmonic_gteps(ms, plain_t), "unit": "GTEPS",
-                "per_root_ms_median": statistics.median(plain_t)},
+                "per_root_ms_median": statistics.median(plain_t),
+                "options": "alpha/beta rule, same tuned alpha, beta, bins and scan order"},
+            "plain_default_options": None if default_t is None else {
+                "value": harmonic_gteps(ms, default_t), "unit": "GTEPS",
+                "per_root_ms_median": statistics.median(default_t),
+                "options": "alpha/beta rule, library defaults (14, 24, 32/1024/32768)"},
+            "options": {k: v for k, v in kw.items() if k != "mlp_params"},
+            "learned_controller": learned_note,
+            "autotune": None if tune_rec is None else dict(tune_rec.to_dict(), seconds=t_tune),
         }
         print(json.dumps(line), flush=True)
         if args.stats_out:
@@ -532,13 +577,7 @@ def _setup_dist(args):
     return local, world, dist
 
 
-def _max_over_ranks(dist, x):
-    if not dist:
-        return x
-    import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+
 
 
 def _ms_oracle_worker(log2n, roots, q):

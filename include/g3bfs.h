@@ -185,8 +185,9 @@ typedef struct {
  * bottom-up over the unvisited vertices with bitmaps and an early exit on
  * the first parent found (Algorithm 5), as the controller decides.
  *   parent, level : n int32 entries each (original IDs); device OR host
- *                   pointers (a host buffer is filled through a device
- *                   staging copy; pinned memory is fastest).
+ *                   pointers. Page-locked host memory is written directly
+ *                   by the output kernel; pageable host memory is filled
+ *                   through a device staging copy.
  *                   parent[root] = root, level[root] = 0; unreachable and
  *                   isolated vertices get -1 in both. An isolated root is
  *                   valid: only the root is reached.
@@ -194,9 +195,14 @@ typedef struct {
  *   stats         : host array of max_stats entries or NULL; receives one
  *                   record per level while room remains. *n_levels (may be
  *                   NULL) receives the number of non-empty frontiers.
- * The first call on a graph allocates its BFS workspace (about 20 bytes per
- * vertex); later calls allocate nothing. Synchronises `stream` once per level
- * (the controller's decision is read back) and before returning.
+ * The first call on a graph allocates its BFS workspace (about 24 bytes per
+ * vertex); later calls allocate nothing. By default the level loop runs on
+ * the device as one CUDA graph (a WHILE node over a SWITCH of level kinds,
+ * conditions set by the device-side controller; rebuilt when the options
+ * change) and the call synchronises `stream` once after it and before
+ * returning. With opts.timing or opts.record_both the loop is driven from the
+ * host instead and synchronises once per level (the controller's record is
+ * read back). Searches deeper than 4096 levels continue on the host loop.
  * Errors: G3_EINVAL (root outside [0, n), null parent/level, learned
  * controller without parameters), G3_ENOMEM, G3_ECUDA. */
 g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, int32_t* parent,

@@ -992,13 +992,19 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
   return G3_OK;
 }
 
-static bool is_device_ptr(const void* p) {
+// A pointer the device can write for p: p itself for device or managed
+// memory, the device alias of page-locked host memory (the output pass then
+// writes straight into host memory over the chip-to-chip link), NULL for
+// pageable host memory (which goes through a device staging buffer).
+static int32_t* device_view(int32_t* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return nullptr;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) return (int32_t*)at.devicePointer;
+  return nullptr;
 }
 
 static inline int cap_grid(int64_t items, int per_block, int resident) {
@@ -1300,9 +1306,11 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   if (n_levels) *n_levels = nrec;
 
   // outputs in original IDs
-  const bool dev_p = is_device_ptr(parent), dev_l = is_device_ptr(level);
-  int32_t* op = dev_p ? parent : ws->out_parent;
-  int32_t* ol = dev_l ? level : ws->out_level;
+  int32_t* vp = device_view(parent);
+  int32_t* vl = device_view(level);
+  const bool dev_p = vp != nullptr, dev_l = vl != nullptr;
+  int32_t* op = dev_p ? vp : ws->out_parent;
+  int32_t* ol = dev_l ? vl : ws->out_level;
   if ((((uintptr_t)op | (uintptr_t)ol) & 15) == 0) {
     bfs_translate4<<<cap_grid((g->n + 3) / 4, 256, ws->grid_tr4), 256, 0, s>>>(
         g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op, ol);

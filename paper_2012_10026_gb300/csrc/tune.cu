@@ -91,6 +91,9 @@ struct Events {
 };
 
 constexpr int kReps = 3;  // each candidate: the minimum of three timed runs
+// a candidate replaces the best so far only when faster by this factor, so
+// that run-to-run noise does not walk the search away from a good start
+constexpr float kGain = 0.995f;
 
 g3_status cache_hit(const char* path, g3_tune_entry* key, bool* hit) {
   *hit = false;
@@ -274,7 +277,7 @@ extern "C" g3_status g3_autotune_bfs(g3_graph* g, const int32_t* roots, int32_t 
         float ms = 0.f;
         G3_TRY(time_bfs(g, roots, nroots, o, parent, level, fl, ev, s, &ms));
         ++points;
-        if (ms < best_ms) {
+        if (ms < best_ms * kGain) {
           best_ms = ms;
           best = o;
         }
@@ -339,7 +342,7 @@ extern "C" g3_status g3_autotune_msbfs(g3_graph* g, const int32_t* roots, int32_
       float ms = 0.f;
       G3_TRY(time_one(o, &ms));
       ++points;
-      if (ms < best_ms) {
+      if (ms < best_ms * kGain) {
         best_ms = ms;
         best = o;
       }
@@ -402,7 +405,7 @@ extern "C" g3_status g3_autotune_batch(g3_batch* b, const int32_t* roots, int32_
     float ms = 0.f;
     G3_TRY(time_one(o, &ms));
     ++points;
-    if (ms < best_ms) {
+    if (ms < best_ms * kGain) {
       best_ms = ms;
       best = o;
     }

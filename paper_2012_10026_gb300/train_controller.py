@@ -99,6 +99,68 @@ def gated(o0, meta, margin):
     return [(x < 0) if abs(x) > margin else (d == 1) for x, (_, _, d) in zip(o0, meta)]
 
 
+def time_controllers(scale: int, seed: int, nroots: int, root_seed: int, configs: dict,
+                     reps: int = 3, device="cuda"):
+    """Summed device ms of nroots searches per named g3_bfs_opts (the
+    minimum over reps for each root, 256 MB written between searches)."""
+    import torch
+    import graphgen
+    n = 1 << scale
+    src, dst = graphgen.kronecker_edges_dev(scale, 16, seed=seed, device=device)
+    flags = graphgen.nonisolated_flags_dev(src, dst, n).cpu().numpy()
+    roots = graphgen.pick_roots(flags, nroots, root_seed).tolist()
+    g = g3.g3_build_csr(src, dst, n)
+    del src, dst
+    g3.g3_rcm_relabel(g)
+    parent = torch.empty(n, dtype=torch.int32, device=device)
+    level = torch.empty(n, dtype=torch.int32, device=device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, o in configs.items():
+        best = [float("inf")] * len(roots)
+        for _ in range(reps + 1):  # the first round builds the level-loop graph
+            for i, r in enumerate(roots):
+                flush.fill_(1)
+                es.record()
+                g3.g3_bfs(g, r, parent, level, o)
+                ee.record()
+                ee.synchronize()
+                best[i] = min(best[i], es.elapsed_time(ee))
+        out[name] = float(sum(best))
+    g.free()
+    return out
+
+
+DOMAIN_SLACK = 2 ** 0.5  # how far past the trained graph sizes the network is trusted
+
+
+def controller_opts(path: str, n_bfs: int, device="cuda", **base):
+    """g3_bfs options for the trained controller in `path` on a graph of n_bfs
+    BFS vertices, on top of the options in `base`. Inside the graph sizes the
+    network was trained on (within a factor sqrt(2)) it runs with its margin
+    and bin choice; outside them the heuristic keeps every decision (margin
+    set past any output, fixed bins), since the per-level costs it learned do
+    not carry over (the bottom-up scan of the whole bitmap grows with n while
+    a small top-down frontier does not). Returns (opts, params tensor, note);
+    the tensor must outlive the searches."""
+    import torch
+    with open(path) as f:
+        mj = json.load(f)
+    params = torch.tensor(mj["params"], dtype=torch.float32, device=device)
+    lo, hi = mj.get("n_bfs_range", [0, 2 ** 31])
+    inside = lo / DOMAIN_SLACK <= n_bfs <= hi * DOMAIN_SLACK
+    kw = dict(base, controller=g3.G3_CTRL_LEARNED, mlp_params=params)
+    if inside:
+        kw.update(mlp_margin=int(mj.get("mlp_margin", 0)), mlp_bins=int(mj.get("mlp_bins", 1)))
+        note = "inside the trained graph sizes"
+    else:
+        kw.update(mlp_margin=2 ** 30, mlp_bins=0)
+        note = (f"n_bfs {n_bfs} outside the trained sizes {lo}..{hi}: the alpha/beta rule "
+                f"decides every level")
+    return g3.opts(**kw), params, note
+
+
 def train(X, Y, steps=3000, lr=1e-2, seed=0, device="cuda"):
     import torch
     p = torch.from_numpy(init_params(seed)).to(device)
@@ -138,6 +200,8 @@ def main():
     summary = {
         "params": [float(v) for v in p.cpu().numpy()],
         "layout": "W1[32][12], b1[32], W2[4][32], b2[4]",
+        # graph sizes seen in training (BFS vertices); see controller_opts
+        "n_bfs_range": [min(nb for _, nb in runs), max(nb for _, nb in runs)],
         "scales": args.scales, "seeds": args.seeds, "roots_per_graph": args.roots,
         "samples": int(len(X)), "steps": args.steps, "lr": args.lr,
         "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
@@ -157,6 +221,15 @@ def main():
     summary["holdout"] = {"scale": max(args.scales), "levels": int(len(Xh)),
                           "regret_ms_by_margin": table}
     summary["mlp_margin"] = int(round(min(best_m, 1e6) * 1000))
+    # whether the network's bin thresholds beat the fixed ones: timed on the
+    # same held-out graph, with the chosen margin
+    lo = dict(controller=g3.G3_CTRL_LEARNED, mlp_params=p, mlp_margin=summary["mlp_margin"])
+    tt = time_controllers(max(args.scales), 97, args.roots, 98, {
+        "heuristic": g3.opts(),
+        "learned_bins": g3.opts(mlp_bins=1, **lo),
+        "learned_fixed_bins": g3.opts(mlp_bins=0, **lo)})
+    summary["holdout"]["ms"] = tt
+    summary["mlp_bins"] = 1 if tt["learned_bins"] < tt["learned_fixed_bins"] else 0
     if args.eval_scale:
         # held-out graph: per-level times of both directions under the
         # heuristic's path; regret of each controller's choices on it
