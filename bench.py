@@ -68,6 +68,9 @@ def parse_args():
                     help="kron: the single-root headline; msbfs: bit-sliced multi-source "
                          "BFS on a Chung-Lu graph; batch: many small graphs in one launch")
     ap.add_argument("--ms-log2n", type=int, default=24, help="msbfs: Chung-Lu 2^k vertices")
+    ap.add_argument("--rcm", type=int, default=1,
+                    help="kron: 0 searches the graph in its generated labelling (no RCM, "
+                         "isolated vertices kept), for the locality comparison")
     ap.add_argument("--tune-bfs", type=int, default=1,
                     help="kron: autotune alpha/beta/bins/scan order first (cached)")
     ap.add_argument("--msbfs-compare", type=int, default=1,
@@ -262,7 +265,8 @@ def reference_arm(args, rank, world):
 
 
 def workload_config(args):
-    return {"workload": f"kronecker_scale{args.scale}_ef{args.edgefactor}_rcm_{args.roots}roots",
+    rcm = "rcm" if getattr(args, "rcm", 1) else "norcm"
+    return {"workload": f"kronecker_scale{args.scale}_ef{args.edgefactor}_{rcm}_{args.roots}roots",
             "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
             "initiator": [0.57, 0.19, 0.19, 0.05], "gen_seed": args.seed,
             "root_seed": args.root_seed,
@@ -300,7 +304,8 @@ def gpu_arm(args, rank, world):
     g = g3.g3_build_csr(src, dst, n)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    g3.g3_rcm_relabel(g)
+    if args.rcm:
+        g3.g3_rcm_relabel(g)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     info = g.info
