@@ -53,6 +53,8 @@ def lib():
         L.orc_build_csr.restype = ctypes.c_int64
         L.orc_rcm.argtypes = [_i64p, _i32p, ctypes.c_int32, _i32p]
         L.orc_rcm.restype = ctypes.c_int32
+        L.orc_rcm_partial.argtypes = [_i64p, _i32p, ctypes.c_int32, ctypes.c_int32, _i32p]
+        L.orc_rcm_partial.restype = ctypes.c_int32
         L.orc_permute_csr.argtypes = [_i64p, _i32p, ctypes.c_int32, _i32p, ctypes.c_int32,
                                       _i64p, _i32p]
         L.orc_permute_csr.restype = None
@@ -95,6 +97,15 @@ def rcm(off, col):
     n = len(off) - 1
     P = np.empty(max(n, 1), np.int32)
     n_plus = lib().orc_rcm(_p64(off), _p32(col), n, _p32(P))
+    return P[:n].copy(), int(n_plus)
+
+
+def rcm_partial(off, col, p_permille: int):
+    """Partial RCM (Sec. 4.6, reading in oracle.c) -> (P, n_plus)."""
+    off, col = _c64(off), _c32(col)
+    n = len(off) - 1
+    P = np.empty(max(n, 1), np.int32)
+    n_plus = lib().orc_rcm_partial(_p64(off), _p32(col), n, int(p_permille), _p32(P))
     return P[:n].copy(), int(n_plus)
 
 

@@ -18,6 +18,8 @@
  *                     degree, start of each component = first unvisited
  *                     vertex of V+ (minimal degree, Sec. 3.2), FIFO relabel,
  *                     reverse, append V \ V+.
+ *   orc_rcm_partial   partial RCM (Sec. 4.6): Algorithm 3 on the top p of
+ *                     V+ only, the rest in ID order (reading in its comment).
  *   orc_permute_csr   the relabelled CSR the BFS runs on (isolated vertices
  *                     dropped, Sec. 1 contribution 1; rows ascending).
  *   orc_bfs           Algorithm 1 run serially: FIFO frontier, neighbours in
@@ -156,6 +158,76 @@ int32_t orc_rcm(const int64_t* off, const int32_t* col, int32_t n, int32_t* P) {
   for (int32_t v = 0; v < n; ++v)
     if (deg_of(v) == 0) P[k++] = v;
   free(vplus);
+  free(visited);
+  free(nb);
+  return np;
+}
+
+/* Partial RCM (Sec. 4.6): only the top p of V+ is reordered. The paper gives
+ * no procedure; the reading taken here: the top k = ceil(p_permille * |V+| /
+ * 1000) vertices are the last k of V+ in Algorithm 3's (degree, ID) order.
+ * Algorithm 3 runs on that set S alone (starts and neighbour orders as in
+ * orc_rcm, with the graph's degrees; neighbours outside S ignored), and its
+ * reversed order fills positions 0..k-1. The rest of V+ follows in ascending
+ * original ID, then V \ V+. p_permille = 1000 gives orc_rcm exactly.
+ * Returns n_plus. */
+int32_t orc_rcm_partial(const int64_t* off, const int32_t* col, int32_t n,
+                        int32_t p_permille, int32_t* P) {
+  g_off = off;
+  int32_t* vplus = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t));
+  int32_t np = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (deg_of(v) > 0) vplus[np++] = v;
+  qsort(vplus, (size_t)np, sizeof(int32_t), cmp_deg_id);
+  if (p_permille < 0) p_permille = 0;
+  if (p_permille > 1000) p_permille = 1000;
+  const int32_t k = (int32_t)(((int64_t)np * p_permille + 999) / 1000);
+  const int32_t lo = np - k; /* S = vplus[lo .. np) */
+
+  uint8_t* in_s = (uint8_t*)calloc((size_t)n + 1, 1);
+  for (int32_t i = lo; i < np; ++i) in_s[vplus[i]] = 1;
+  uint8_t* visited = (uint8_t*)calloc((size_t)n + 1, 1);
+  int64_t maxdeg = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (deg_of(v) > maxdeg) maxdeg = deg_of(v);
+  int32_t* nb = (int32_t*)malloc(((size_t)maxdeg + 1) * sizeof(int32_t));
+
+  int32_t min_index = lo, slow = 0, fast = 0;
+  while (slow < k) {
+    for (int32_t i = min_index; i < np; ++i) {
+      if (!visited[vplus[i]]) {
+        P[slow] = vplus[i];
+        visited[vplus[i]] = 1;
+        min_index = i + 1;
+        fast = slow + 1;
+        break;
+      }
+    }
+    while (slow < fast) {
+      int32_t v = P[slow];
+      int64_t d = deg_of(v);
+      memcpy(nb, col + off[v], (size_t)d * sizeof(int32_t));
+      qsort(nb, (size_t)d, sizeof(int32_t), cmp_deg_id);
+      for (int64_t j = 0; j < d; ++j) {
+        int32_t w = nb[j];
+        if (in_s[w] && !visited[w]) {
+          visited[w] = 1;
+          P[fast++] = w;
+        }
+      }
+      slow++;
+    }
+  }
+  for (int32_t i = 0, j = k - 1; i < j; ++i, --j) {
+    int32_t t = P[i]; P[i] = P[j]; P[j] = t;
+  }
+  int32_t q = k;
+  for (int32_t v = 0; v < n; ++v)
+    if (deg_of(v) > 0 && !in_s[v]) P[q++] = v;
+  for (int32_t v = 0; v < n; ++v)
+    if (deg_of(v) == 0) P[q++] = v;
+  free(vplus);
+  free(in_s);
   free(visited);
   free(nb);
   return np;

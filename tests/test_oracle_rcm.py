@@ -191,3 +191,89 @@ def test_rcm_bandwidth_vs_scipy_sanity():
     assert oracle.bandwidth(off, col, lab) <= 2 * b - 1
     assert oracle.bandwidth(off, col, lab2) <= 2 * b - 1
     assert oracle.bandwidth(off, col) > 10 * b
+
+
+# ------------------------------------------------------------- partial RCM
+def partial_rcm_by_level_sort(src, dst, n, p_permille):
+    """The level-sort restatement above restricted to S, the last k vertices
+    of V+ in (degree, id) order, k = ceil(p * |V+|): components and levels
+    use only edges inside S (degrees stay the graph's). S's reversed order
+    comes first, then the rest of V+ by id, then the isolated vertices."""
+    adj = adjacency_sets(src, dst, n)
+    deg = [len(a) for a in adj]
+    vplus = sorted((v for v in range(n) if deg[v] > 0), key=lambda v: (deg[v], v))
+    k = (len(vplus) * p_permille + 999) // 1000
+    S = set(vplus[len(vplus) - k:])
+    sadj = [set(w for w in adj[v] if w in S) if v in S else set() for v in range(n)]
+    parent = list(range(n))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for u in S:
+        for w in sadj[u]:
+            ru, rw = find(u), find(w)
+            if ru != rw:
+                parent[ru] = rw
+    comps = {}
+    for v in S:
+        comps.setdefault(find(v), []).append(v)
+    starts = sorted((min(c, key=lambda v: (deg[v], v)) for c in comps.values()),
+                    key=lambda v: (deg[v], v))
+    order, pos = [], {}
+    for s in starts:
+        pos[s] = len(order)
+        order.append(s)
+        level = [s]
+        while level:
+            cand = {}
+            for v in level:
+                for w in sadj[v]:
+                    if w not in pos:
+                        cand[w] = min(cand.get(w, 1 << 60), pos[v])
+            nxt = sorted(cand, key=lambda w: (cand[w], deg[w], w))
+            for w in nxt:
+                pos[w] = len(order)
+                order.append(w)
+            level = nxt
+    rest = sorted(v for v in vplus if v not in S)
+    return order[::-1] + rest + [v for v in range(n) if deg[v] == 0], len(vplus)
+
+
+@pytest.mark.parametrize("block", range(5))
+def test_partial_rcm_equals_level_sort_restatement(block):
+    rng = np.random.default_rng(2000 + block)
+    for _ in range(300):
+        n = int(rng.integers(1, 15))
+        m = int(rng.integers(0, 2 * n + 1))
+        src, dst = random_graph(rng, n, m)
+        pm = int(rng.choice([0, 1, 250, 333, 500, 750, 999, 1000]))
+        off, col = oracle.build_csr(src, dst, n)
+        P, n_plus = oracle.rcm_partial(off, col, pm)
+        P2, n_plus2 = partial_rcm_by_level_sort(src, dst, n, pm)
+        assert n_plus == n_plus2
+        assert P.tolist() == P2, (src.tolist(), dst.tolist(), pm)
+
+
+def test_partial_rcm_end_points_and_invariants():
+    import graphgen
+    src, dst = graphgen.kronecker_edges(10, 16, seed=3)
+    n = 1 << 10
+    off, col = oracle.build_csr(src, dst, n)
+    deg = np.diff(off)
+    P_full, n_plus = oracle.rcm(off, col)
+    P, np2 = oracle.rcm_partial(off, col, 1000)  # p = 1: Algorithm 3 itself
+    assert np2 == n_plus and np.array_equal(P, P_full)
+    P0, _ = oracle.rcm_partial(off, col, 0)  # p = 0: nothing reordered
+    assert np.array_equal(P0, np.concatenate([np.nonzero(deg > 0)[0], np.nonzero(deg == 0)[0]]))
+    for pm in (100, 500):
+        P, _ = oracle.rcm_partial(off, col, pm)
+        k = (n_plus * pm + 999) // 1000
+        assert sorted(P.tolist()) == list(range(n))
+        vplus = sorted(np.nonzero(deg > 0)[0].tolist(), key=lambda v: (deg[v], v))
+        assert set(P[:k].tolist()) == set(vplus[n_plus - k:])  # the top k come first
+        assert P[k:n_plus].tolist() == sorted(vplus[:n_plus - k])
+        assert P[n_plus:].tolist() == np.nonzero(deg == 0)[0].tolist()
