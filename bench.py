@@ -68,6 +68,11 @@ def parse_args():
                     help="kron: the single-root headline; msbfs: bit-sliced multi-source "
                          "BFS on a Chung-Lu graph; batch: many small graphs in one launch")
     ap.add_argument("--ms-log2n", type=int, default=24, help="msbfs: Chung-Lu 2^k vertices")
+    ap.add_argument("--rcm-permille", type=int, default=1000,
+                    help="kron: partial RCM, only the top p/1000 of V+ reordered (Sec. 4.6)")
+    ap.add_argument("--host-loop", type=int, default=0,
+                    help="kron: drive the level loop from the host (for kernel-level "
+                         "profiling; the default runs it as one CUDA graph per search)")
     ap.add_argument("--rcm", type=int, default=1,
                     help="kron: 0 searches the graph in its generated labelling (no RCM, "
                          "isolated vertices kept), for the locality comparison")
@@ -266,6 +271,8 @@ def reference_arm(args, rank, world):
 
 def workload_config(args):
     rcm = "rcm" if getattr(args, "rcm", 1) else "norcm"
+    if rcm == "rcm" and getattr(args, "rcm_permille", 1000) < 1000:
+        rcm = f"rcm{args.rcm_permille}permille"
     return {"workload": f"kronecker_scale{args.scale}_ef{args.edgefactor}_{rcm}_{args.roots}roots",
             "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
             "initiator": [0.57, 0.19, 0.19, 0.05], "gen_seed": args.seed,
@@ -304,7 +311,9 @@ def gpu_arm(args, rank, world):
     g = g3.g3_build_csr(src, dst, n)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    if args.rcm:
+    if args.rcm and args.rcm_permille < 1000:
+        g3.g3_rcm_relabel_partial(g, args.rcm_permille)  # Sec. 4.6
+    elif args.rcm:
         g3.g3_rcm_relabel(g)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
@@ -336,9 +345,12 @@ def gpu_arm(args, rank, world):
     if ctrl == g3.G3_CTRL_LEARNED:
         from paper_2012_10026_gb300.train_controller import controller_opts
         lo, mlp_t, learned_note = controller_opts(args.mlp, info["n_bfs"], **base)
-        kw.update(mlp_params=mlp_t, mlp_margin=lo.mlp_margin, mlp_bins=lo.mlp_bins)
+        kw.update(controller=lo.controller, mlp_params=mlp_t, mlp_margin=lo.mlp_margin,
+                  mlp_bins=lo.mlp_bins)
+    if args.host_loop:  # profiling: every level's kernels as separate stream launches
+        kw["timing"] = 1
     opts = g3.opts(**kw)  # default path: the level loop runs as one CUDA graph
-    opts_timed = g3.opts(timing=1, **kw)  # host-driven, CUDA events around each level
+    opts_timed = g3.opts(**dict(kw, timing=1))  # host-driven, events around each level
     # the plain method: the alpha/beta rule on the same tuned options, and
     # with the library defaults
     plain_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, **base)

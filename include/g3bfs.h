@@ -97,6 +97,19 @@ g3_status g3_build_csr(const int32_t* src, const int32_t* dst, int64_t m, int32_
  * G3_ECUDA. */
 g3_status g3_rcm_relabel(g3_graph* g, void* stream);
 
+/* Partial RCM (Sec. 4.6): reorders only the top p of V+ to cut the
+ * relabelling cost. The paper gives no procedure; here the top
+ * k = ceil(p_permille * n_plus / 1000) vertices are the last k of V+ in
+ * (degree, ID) order, Algorithm 3 runs on that set alone (edges leaving it
+ * ignored, the graph's degrees as ordering key) and its reverse order takes
+ * labels 0..k-1; the rest of V+ takes labels k..n_plus-1 in ascending
+ * original ID; isolated vertices follow as in g3_rcm_relabel, which is
+ * p_permille = 1000. Afterwards the graph is relabelled exactly as after
+ * g3_rcm_relabel (n_plus rows, permutation kept). Synchronises `stream`.
+ * Errors: G3_EINVAL (p_permille outside [0, 1000]), G3_ESTATE, G3_ENOMEM,
+ * G3_ECUDA. */
+g3_status g3_rcm_relabel_partial(g3_graph* g, int32_t p_permille, void* stream);
+
 g3_status g3_graph_info_get(const g3_graph* g, g3_graph_info* info);
 
 /* Copies the permutation (device pointers, n entries each; either may be

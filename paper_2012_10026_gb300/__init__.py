@@ -99,6 +99,7 @@ _SIGS = {
     "g3_build_csr": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp,
                                     ctypes.POINTER(_vp)]),
     "g3_rcm_relabel": (ctypes.c_int, [_vp, _vp]),
+    "g3_rcm_relabel_partial": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
     "g3_graph_info_get": (ctypes.c_int, [_vp, ctypes.POINTER(g3_graph_info)]),
     "g3_get_perm": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "g3_get_csr": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -217,6 +218,12 @@ def g3_build_csr(src, dst, n: int, stream=None) -> "Graph":
 
 def g3_rcm_relabel(graph: "Graph", stream=None):
     _check(lib().g3_rcm_relabel(graph.handle, _stream(stream)), "g3_rcm_relabel")
+
+
+def g3_rcm_relabel_partial(graph: "Graph", p_permille: int, stream=None):
+    """Partial RCM: only the top p_permille / 1000 of V+ reordered (Sec. 4.6)."""
+    _check(lib().g3_rcm_relabel_partial(graph.handle, int(p_permille), _stream(stream)),
+           "g3_rcm_relabel_partial")
 
 
 def g3_graph_info_get(graph: "Graph") -> dict:

@@ -832,8 +832,9 @@ __global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
 // Same mapping, four consecutive original IDs per thread: one 128-bit load
 // of new_of_old, four independent gathers of the packed (parent, level) word
 // in flight at once (the random gathers are what bounds this pass, so their
-// latency has to overlap), 128-bit stores. parent and level must be 16-byte
-// aligned.
+// latency has to overlap), 128-bit stores. The streamed input and the outputs
+// carry evict-first hints so that L2 keeps the gathered words. parent and
+// level must be 16-byte aligned.
 __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int32_t root,
                                                       const int32_t* __restrict__ new_of_old,
                                                       const uint32_t* __restrict__ visited,
@@ -844,7 +845,8 @@ __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int
        i += (int64_t)gridDim.x * blockDim.x) {
     int x[4];
     if (new_of_old) {
-      const int4 xs = __ldg(reinterpret_cast<const int4*>(new_of_old) + i);
+      // streamed once: evict-first, so the packed words stay in L2
+      const int4 xs = __ldcs(reinterpret_cast<const int4*>(new_of_old) + i);
       x[0] = xs.x;
       x[1] = xs.y;
       x[2] = xs.z;
@@ -871,8 +873,8 @@ __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int
       p[root & 3] = root;
       l[root & 3] = 0;
     }
-    reinterpret_cast<int4*>(parent)[i] = make_int4(p[0], p[1], p[2], p[3]);
-    reinterpret_cast<int4*>(level)[i] = make_int4(l[0], l[1], l[2], l[3]);
+    __stcs(reinterpret_cast<int4*>(parent) + i, make_int4(p[0], p[1], p[2], p[3]));
+    __stcs(reinterpret_cast<int4*>(level) + i, make_int4(l[0], l[1], l[2], l[3]));
   }
   // the last n % 4 IDs
   const int64_t v = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __rest
                                                uint64_t full, int64_t heavy_deg,
                                                int32_t* heavy, int32_t* qn,
                                                unsigned long long* ctr) {
+  const bool col_al16 = ((uintptr_t)col & 15) == 0;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nb;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
@@ -247,12 +248,16 @@ __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __rest
         if (e - b >= heavy_deg) {
           big = true;
         } else {
-          // four independent gathers per step; the exit test runs per step
+          // up to the next multiple of 4 one entry at a time, then one
+          // 128-bit column load and four independent gathers per step; the
+          // exit test runs per step (vector loads only on a 16-byte aligned
+          // col, which the allocator gives)
           uint64_t acc = 0;
           int64_t j = b;
-          for (; j + 4 <= e && (acc | vv) != full; j += 4) {
-            const int32_t c0 = col[j], c1 = col[j + 1], c2 = col[j + 2], c3 = col[j + 3];
-            acc |= (__ldg(&F[c0]) | __ldg(&F[c1])) | (__ldg(&F[c2]) | __ldg(&F[c3]));
+          for (; j < e && (j & 3) && (acc | vv) != full; ++j) acc |= __ldg(&F[col[j]]);
+          for (; col_al16 && j + 4 <= e && (acc | vv) != full; j += 4) {
+            const int4 c4 = __ldg(reinterpret_cast<const int4*>(col + j));
+            acc |= (__ldg(&F[c4.x]) | __ldg(&F[c4.y])) | (__ldg(&F[c4.z]) | __ldg(&F[c4.w]));
           }
           for (; j < e && (acc | vv) != full; ++j) acc |= __ldg(&F[col[j]]);
           nv = acc & ~vv;

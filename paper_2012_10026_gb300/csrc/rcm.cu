@@ -17,6 +17,12 @@
 //     key, then each component's slice takes the next positions of its range.
 //  5. Reverse: label = n_plus - 1 - position; isolated vertices get n_plus..n-1
 //     in ascending ID. The CSR is rebuilt under the new labels (rows sorted).
+//
+// Partial RCM (Sec. 4.6) runs the same steps on S = the vertices of rank >= lo
+// only (the top k of V+ by (degree, ID), lo = n_plus - k): edges leaving S are
+// ignored by the hooking and the level expansion, S takes labels k-1-position,
+// and the rest of V+ takes labels k.. in ascending ID. lo = 0 is the full
+// algorithm.
 #include "g3_prims.cuh"
 
 #define INF_U32 0xFFFFFFFFu
@@ -74,10 +80,12 @@ struct HookEdge {
   const int32_t* rank;
   int32_t* p;
   int* changed;
+  int32_t lo;  // only edges inside ranks [lo, n_plus)
   __device__ void operator()(int64_t u, int64_t j, bool active) const {
     if (!active) return;
     int32_t w = col[j];
     if ((int32_t)u >= w) return;  // each undirected edge once
+    if (rank[u] < lo || rank[w] < lo) return;
     int32_t ru = uf_find(p, rank[u]), rw = uf_find(p, rank[w]);
     if (ru == rw) return;
     int32_t lo = ru < rw ? ru : rw, hi = ru < rw ? rw : ru;
@@ -99,12 +107,12 @@ __global__ void rcm_compress(int32_t* p, int32_t n_plus) {
 }
 
 // Component sizes, warp-aggregated per distinct root.
-__global__ void rcm_comp_sizes(const int32_t* __restrict__ p, int32_t n_plus,
+__global__ void rcm_comp_sizes(const int32_t* __restrict__ p, int32_t n_plus, int32_t lo,
                                unsigned long long* size) {
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n_plus;
        base += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = base + threadIdx.x;
-    int32_t root = r < n_plus ? p[r] : -1;
+    int32_t root = (r < n_plus && r >= lo) ? p[r] : -1;
     unsigned peers = __match_any_sync(0xffffffffu, root);
     if (root >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
       atomicAdd(&size[root], (unsigned long long)__popc(peers));
@@ -113,7 +121,8 @@ __global__ void rcm_comp_sizes(const int32_t* __restrict__ p, int32_t n_plus,
 
 struct IsRoot {
   const int32_t* p;
-  __device__ bool operator()(int64_t r) const { return p[r] == (int32_t)r; }
+  int32_t lo;
+  __device__ bool operator()(int64_t r) const { return r >= lo && p[r] == (int32_t)r; }
 };
 struct EmitStart {
   const int32_t* vplus;
@@ -148,13 +157,15 @@ struct ExpandLevel {
   uint32_t* ppos;
   int32_t* next;
   unsigned long long* next_len;
+  const int32_t* rank;
+  int32_t lo;
   __device__ void operator()(int64_t i, int64_t j, bool active) const {
     bool claim = false;
     int32_t w = 0;
     if (active) {
       int32_t v = front[i];
       w = col[off[v] + (j - fseg[i])];
-      if (pos[w] < 0) {
+      if (pos[w] < 0 && rank[w] >= lo) {
         uint32_t old = atomicMin(&ppos[w], (uint32_t)pos[v]);
         claim = old == INF_U32;
       }
@@ -223,14 +234,29 @@ __global__ void rcm_level_tails(const uint64_t* __restrict__ keys, int64_t len, 
 }
 
 // ------------------------------------------------------------- relabel CSR
-__global__ void rcm_labels(const int32_t* __restrict__ pos, int32_t n, int32_t n_plus,
+__global__ void rcm_labels(const int32_t* __restrict__ pos, int32_t n, int32_t k,
                            int32_t* new_of_old) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     int32_t q = pos[v];
-    if (q >= 0) new_of_old[v] = n_plus - 1 - q;
+    if (q >= 0) new_of_old[v] = k - 1 - q;
   }
 }
+
+// Partial RCM: the vertices of V+ below rank lo, labels k.. by ascending ID.
+struct IsUnordered {
+  const int64_t* off;
+  const int32_t* rank;
+  int32_t lo;
+  __device__ bool operator()(int64_t v) const { return off[v + 1] > off[v] && rank[v] < lo; }
+};
+struct EmitUnorderedLabel {
+  int32_t k;
+  int32_t* new_of_old;
+  __device__ void operator()(int64_t v, int64_t pos) const {
+    new_of_old[v] = k + (int32_t)pos;
+  }
+};
 
 __global__ void rcm_inverse(const int32_t* __restrict__ new_of_old, int32_t n,
                             const int64_t* __restrict__ off, int32_t* old_of_new,
@@ -292,7 +318,7 @@ struct RcmBufs {
   }
 };
 
-static g3_status rcm_impl(g3_graph* g, cudaStream_t s, RcmBufs& B) {
+static g3_status rcm_impl(g3_graph* g, int32_t p_permille, cudaStream_t s, RcmBufs& B) {
   const int32_t n = g->n;
   const int64_t nnz = g->nnz;
   const int bits_v = g3_bits_for(n);
@@ -310,6 +336,9 @@ static g3_status rcm_impl(g3_graph* g, cudaStream_t s, RcmBufs& B) {
   int64_t nplus64 = 0;
   G3_TRY(read_i64(B.partial + (n + CP_TILE - 1) / CP_TILE, &nplus64, s));
   const int32_t n_plus = (int32_t)nplus64;
+  // the top k of V+ are reordered (all of it for the full algorithm)
+  const int32_t k = (int32_t)(((int64_t)n_plus * p_permille + 999) / 1000);
+  const int32_t lo = n_plus - k;
   const int bits_d = g3_bits_for(g->max_degree + 1);
   uint64_t* sorted;
   G3_TRY(g3_radix_sort_u64(B.ka, B.kb, n_plus, bits_d + bits_v, &sorted, s));
@@ -327,7 +356,7 @@ static g3_status rcm_impl(g3_graph* g, cudaStream_t s, RcmBufs& B) {
   for (int it = 0; n_plus > 0; ++it) {
     G3_TRY_CUDA(cudaMemsetAsync(B.counters, 0, sizeof(unsigned long long), s));
     rcm_hook<<<grid, 256, 0, s>>>(g->off, n,
-                                  HookEdge{g->col, B.rank, B.p, (int*)B.counters});
+                                  HookEdge{g->col, B.rank, B.p, (int*)B.counters, lo});
     G3_CHECK_LAUNCH();
     rcm_compress<<<g3_grid_for(n_plus, 256), 256, 0, s>>>(B.p, n_plus);
     G3_CHECK_LAUNCH();
@@ -347,7 +376,7 @@ static g3_status rcm_impl(g3_graph* g, cudaStream_t s, RcmBufs& B) {
   G3_TRY(g3_alloc(&B.first, (size_t)n_plus + 1, s));
   G3_TRY_CUDA(cudaMemsetAsync(B.base, 0, ((size_t)n_plus + 1) * sizeof(int64_t), s));
   if (n_plus > 0) {
-    rcm_comp_sizes<<<g3_grid_for(n_plus, 256), 256, 0, s>>>(B.p, n_plus,
+    rcm_comp_sizes<<<g3_grid_for(n_plus, 256), 256, 0, s>>>(B.p, n_plus, lo,
                                                             (unsigned long long*)B.base);
     G3_CHECK_LAUNCH();
   }
@@ -359,7 +388,7 @@ static g3_status rcm_impl(g3_graph* g, cudaStream_t s, RcmBufs& B) {
   G3_TRY(g3_alloc(&B.fseg, (size_t)n_plus + 1, s));
   G3_TRY_CUDA(cudaMemsetAsync(B.pos, 0xFF, (size_t)n * sizeof(int32_t), s));
   G3_TRY_CUDA(cudaMemsetAsync(B.ppos, 0xFF, (size_t)n * sizeof(uint32_t), s));
-  G3_TRY(g3_compact((int64_t)n_plus, IsRoot{B.p},
+  G3_TRY(g3_compact((int64_t)n_plus, IsRoot{B.p, lo},
                     EmitStart{B.vplus, B.base, B.pos, B.cursor, B.front}, B.partial, s));
   int64_t nf = 0;
   G3_TRY(read_i64(B.partial + (n_plus + CP_TILE - 1) / CP_TILE, &nf, s));
@@ -373,7 +402,8 @@ static g3_status rcm_impl(g3_graph* g, cudaStream_t s, RcmBufs& B) {
     G3_TRY_CUDA(cudaMemsetAsync(B.counters + 1, 0, sizeof(unsigned long long), s));
     rcm_expand<<<grid, 256, 0, s>>>(
         B.fseg, nf,
-        ExpandLevel{B.front, B.fseg, g->off, g->col, B.pos, B.ppos, B.next, B.counters + 1});
+        ExpandLevel{B.front, B.fseg, g->off, g->col, B.pos, B.ppos, B.next, B.counters + 1,
+                    B.rank, lo});
     G3_CHECK_LAUNCH();
     int64_t len = 0;
     G3_TRY(read_i64((const int64_t*)(B.counters + 1), &len, s));
@@ -394,8 +424,11 @@ static g3_status rcm_impl(g3_graph* g, cudaStream_t s, RcmBufs& B) {
   }
 
   // 5. labels, inverse, relabelled CSR
-  rcm_labels<<<g3_grid_for(n, 256), 256, 0, s>>>(B.pos, n, n_plus, g->new_of_old);
+  rcm_labels<<<g3_grid_for(n, 256), 256, 0, s>>>(B.pos, n, k, g->new_of_old);
   G3_CHECK_LAUNCH();
+  if (lo > 0)
+    G3_TRY(g3_compact((int64_t)n, IsUnordered{g->off, B.rank, lo},
+                      EmitUnorderedLabel{k, g->new_of_old}, B.partial, s));
   G3_TRY(g3_compact((int64_t)n, IsIsolated{g->off}, EmitIsolatedLabel{n_plus, g->new_of_old},
                     B.partial, s));
   G3_TRY(g3_alloc(&B.deg_new, (size_t)n_plus + 1, s));
@@ -438,16 +471,19 @@ static g3_status rcm_impl(g3_graph* g, cudaStream_t s, RcmBufs& B) {
   return G3_OK;
 }
 
-extern "C" g3_status g3_rcm_relabel(g3_graph* g, void* stream) {
+static g3_status relabel(g3_graph* g, int32_t p_permille, cudaStream_t s, const char* name) {
   if (!g) {
-    g3_set_error("g3_rcm_relabel: graph is NULL");
+    g3_set_error("%s: graph is NULL", name);
+    return G3_EINVAL;
+  }
+  if (p_permille < 0 || p_permille > 1000) {
+    g3_set_error("%s: p_permille %d outside [0, 1000]", name, p_permille);
     return G3_EINVAL;
   }
   if (g->relabelled) {
-    g3_set_error("g3_rcm_relabel: graph already relabelled");
+    g3_set_error("%s: graph already relabelled", name);
     return G3_ESTATE;
   }
-  cudaStream_t s = (cudaStream_t)stream;
   if (g->ws || g->ms) {
     cudaStreamSynchronize(s);
     g3_bfs_ws_free(g->ws);
@@ -456,16 +492,24 @@ extern "C" g3_status g3_rcm_relabel(g3_graph* g, void* stream) {
     g->ms = nullptr;
   }
   RcmBufs B;
-  g3_status st = rcm_impl(g, s, B);
+  g3_status st = rcm_impl(g, p_permille, s, B);
   B.release(s);
   if (st == G3_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-      g3_set_error("g3_rcm_relabel: %s", cudaGetErrorString(e));
+      g3_set_error("%s: %s", name, cudaGetErrorString(e));
       return G3_ECUDA;
     }
   } else {
     cudaStreamSynchronize(s);
   }
   return st;
+}
+
+extern "C" g3_status g3_rcm_relabel(g3_graph* g, void* stream) {
+  return relabel(g, 1000, (cudaStream_t)stream, "g3_rcm_relabel");
+}
+
+extern "C" g3_status g3_rcm_relabel_partial(g3_graph* g, int32_t p_permille, void* stream) {
+  return relabel(g, p_permille, (cudaStream_t)stream, "g3_rcm_relabel_partial");
 }

@@ -139,9 +139,9 @@ def controller_opts(path: str, n_bfs: int, device="cuda", **base):
     """g3_bfs options for the trained controller in `path` on a graph of n_bfs
     BFS vertices, on top of the options in `base`. Inside the graph sizes the
     network was trained on (within a factor sqrt(2)) it runs with its margin
-    and bin choice; outside them the heuristic keeps every decision (margin
-    set past any output, fixed bins), since the per-level costs it learned do
-    not carry over (the bottom-up scan of the whole bitmap grows with n while
+    and bin choice; outside them the alpha/beta rule takes every decision and
+    the network is not run, since the per-level costs it learned do not carry
+    over (the bottom-up scan of the whole bitmap grows with n while
     a small top-down frontier does not). Returns (opts, params tensor, note);
     the tensor must outlive the searches."""
     import torch
@@ -154,8 +154,8 @@ def controller_opts(path: str, n_bfs: int, device="cuda", **base):
     if inside:
         kw.update(mlp_margin=int(mj.get("mlp_margin", 0)), mlp_bins=int(mj.get("mlp_bins", 1)))
         note = "inside the trained graph sizes"
-    else:
-        kw.update(mlp_margin=2 ** 30, mlp_bins=0)
+    else:  # the rule decides every level; the network is not evaluated at all
+        kw.update(controller=g3.G3_CTRL_HEURISTIC, mlp_margin=0, mlp_bins=0)
         note = (f"n_bfs {n_bfs} outside the trained sizes {lo}..{hi}: the alpha/beta rule "
                 f"decides every level")
     return g3.opts(**kw), params, note

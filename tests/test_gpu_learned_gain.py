@@ -42,4 +42,4 @@ def test_controller_opts_falls_back_outside_trained_sizes(tmp_path):
     o, _, note = tc.controller_opts(str(path), 1 << 22, alpha=20)
     assert (o.controller, o.mlp_margin, o.mlp_bins, o.alpha) == (g3.G3_CTRL_LEARNED, 250, 1, 20)
     o, _, note = tc.controller_opts(str(path), 1 << 25)
-    assert o.mlp_margin >= 1 << 30 and o.mlp_bins == 0 and "outside" in note
+    assert o.controller == g3.G3_CTRL_HEURISTIC and "outside" in note

@@ -347,3 +347,41 @@ def test_levels_past_the_packed_word(relabel, ctrl):
     pw[ids[mid]] = ids[mid]
     assert np.array_equal(parent, pw)
     g.free()
+
+
+@pytest.mark.parametrize("pm", [0, 1, 250, 500, 999, 1000])
+def test_partial_rcm_permutation_and_bfs_equal_oracle(pm):
+    cases = [graphgen.kronecker_edges(14, 16, seed=21) + (1 << 14,)]
+    rng = np.random.default_rng(pm)
+    for _ in range(4):
+        n = int(rng.integers(2, 3000))
+        cases.append(random_graph(rng, n, int(rng.integers(n // 2, 4 * n))) + (n,))
+    for src, dst, n in cases:
+        off, col = oracle.build_csr(src, dst, n)
+        P, n_plus = oracle.rcm_partial(off, col, pm)
+        g = g3.g3_build_csr(_dev(src), _dev(dst), n)
+        g3.g3_rcm_relabel_partial(g, pm)
+        assert g.info["n_plus"] == n_plus
+        old_of_new, _ = g.perm()
+        assert np.array_equal(old_of_new.cpu().numpy(), P), (n, pm)
+        roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), 3, 5).tolist()
+        for r in roots:
+            parent, level, _ = run_bfs(g, r, n)
+            _, lref = oracle.bfs(off, col, r)
+            assert np.array_equal(level, lref)
+            assert oracle.validate(off, col, r, parent, level) == 0
+        g.free()
+
+
+def test_partial_rcm_bad_fraction():
+    src, dst = path_graph(10)
+    g = g3.g3_build_csr(_dev(src), _dev(dst), 10)
+    for bad in (-1, 1001):
+        with pytest.raises(g3.G3Error) as e:
+            g3.g3_rcm_relabel_partial(g, bad)
+        assert e.value.status == g3.G3_EINVAL
+    g3.g3_rcm_relabel_partial(g, 500)
+    with pytest.raises(g3.G3Error) as e:
+        g3.g3_rcm_relabel_partial(g, 500)
+    assert e.value.status == g3.G3_ESTATE
+    g.free()
