@@ -162,6 +162,31 @@ def level_bytes(st, nb):
     return 4 * st["n_f"] + 16 * st["n_f"] + 8 * st["m_f"] + 16 * st["n_next"]
 
 
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu launch-list
+    summary, when the kernel source is unchanged since that capture (the
+    summary records the source file's sha256); else None."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "launches_bfs_kron26.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, "no committed capture"
+    m = re.search(r"traffic: kernel=(\S+) bytes_per_launch=(\d+) source=(\S+) "
+                  r"sha256=([0-9a-f]+)", text)
+    if not m or m.group(1) != kernel:
+        return None, "no capture of this kernel"
+    src = os.path.join(ROOT, m.group(3))
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None, "source missing"
+    if sha != m.group(4):
+        return None, "kernel source changed since the capture"
+    return int(m.group(2)), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {path[len(ROOT)+1:]}"
+
+
 def _max_over_ranks(dist, x):
     """Maximum of x over the ranks (x itself without a process group)."""
     if not dist:
@@ -469,6 +494,7 @@ def gpu_arm(args, rank, world):
     dom = 1 if agg[1][1] >= agg[0][1] else 0
     peak, peak_kind = load_peaks()
     bytes_, tms, launches_dom = agg[dom]
+    traffic, traffic_src = measured_traffic("bu_pull" if dom == 1 else "td_bins")
     achieved = bytes_ / (tms / 1e3) / 1e9 if tms > 0 else 0.0
     # kernels run inside the level-loop graphs (not host launches): per level
     # the body selector and the controller, plus the SWITCH body's kernels
@@ -531,7 +557,8 @@ def gpu_arm(args, rank, world):
             "roofline": {"bound": "hbm",
                          "kernel": "bu_pull" if dom == 1 else "td_front+td_bins",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": traffic_src,
                          "peak_kind": peak_kind, "launches": launches_dom,
                          "avg_launch_ms": tms / max(launches_dom, 1),
                          "bytes_per_launch": bytes_ / max(launches_dom, 1),
