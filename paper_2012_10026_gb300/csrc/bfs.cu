@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(256) td_front(const int64_t* __restrict__ off,
 // The three bins in one launch: warp per warp-bin vertex, CTA per CTA-bin
 // vertex, and the grid bin as one flattened edge range split evenly over all
 // warps of the grid (Algorithm 4's even split, applied to every hub at once).
-__global__ void __launch_bounds__(256) td_bins(const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(256, 5) td_bins(const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
                                                uint32_t* visited, PlOut plo, Bufs B,
                                                const int32_t* __restrict__ bins,
@@ -534,7 +534,7 @@ __device__ __forceinline__ int32_t bu_scan_rest(const int32_t* __restrict__ col,
 }
 
 template <int REV>
-__global__ void __launch_bounds__(256, 5) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
+__global__ void __launch_bounds__(256, 6) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
                                                Bufs B, const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
                                                const int2* __restrict__ nplus, PlOut plo,
@@ -692,7 +692,7 @@ __global__ void bitmap_to_q(Bufs B, int64_t nwords, Ctrl* c) {
 // ------------------------------------------------------------- controller
 // Learned controller: the 12-32-4 MLP of g3_mlp.cuh on the frontier record.
 __device__ void mlp_features(const Ctrl* c, int32_t nb, int prev_dir, float* f) {
-  mlp_features_raw(c->nf, c->mf, c->nu, c->mu, c->id_min, c->id_max, nb, c->level, prev_dir,
+  mlp_features_raw(c->nf, c->mf, c->nu, c->mu, c->id_min, c->id_max, nb, prev_dir,
                    c->hist, f);
 }
 

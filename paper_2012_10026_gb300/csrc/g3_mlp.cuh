@@ -20,8 +20,7 @@
 //  8..11 fraction of F_L in the degree buckets [0,32) [32,1024) [1024,32768) rest
 __device__ __forceinline__ void mlp_features_raw(long long nf, long long mf, long long nu,
                                                  long long mu, int id_min, int id_max, int32_t nb,
-                                                 int level, int prev_dir, const long long* hist,
-                                                 float* f) {
+                                                 int prev_dir, const long long* hist, float* f) {
   const float fnf = (float)nf, fmf = (float)mf, fnu = (float)nu, fmu = (float)mu;
   f[0] = log2f(1.f + fnf);
   f[1] = log2f(1.f + fmf);

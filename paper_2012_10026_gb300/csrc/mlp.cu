@@ -162,7 +162,7 @@ struct FeatIn {
 __global__ void mlp_features_k(const FeatIn* in, int count, int32_t nb, float* x) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < count; s += gridDim.x * blockDim.x) {
     const FeatIn& r = in[s];
-    mlp_features_raw(r.nf, r.mf, r.nu, r.mu, r.id_min, r.id_max, nb, r.level, r.prev_dir,
+    mlp_features_raw(r.nf, r.mf, r.nu, r.mu, r.id_min, r.id_max, nb, r.prev_dir,
                      r.hist, x + (size_t)s * MLP_IN);
   }
 }

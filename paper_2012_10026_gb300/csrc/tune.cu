@@ -256,13 +256,14 @@ extern "C" g3_status g3_autotune_bfs(g3_graph* g, const int32_t* roots, int32_t 
   G3_TRY(time_bfs(g, roots, nroots, best, parent, level, fl, ev, s, &best_ms));
   e.ms_default = best_ms;
   int points = 1;
-  static const int32_t alphas[] = {6, 10, 14, 20, 28, 40};
-  static const int32_t betas[] = {12, 18, 24, 36, 48};
+  // the paper's own tuned pair is alpha 64, beta 8 (Sec. 3.6)
+  static const int32_t alphas[] = {6, 10, 14, 20, 28, 40, 64, 96, 128};
+  static const int32_t betas[] = {8, 12, 18, 24, 36, 48};
   static const int32_t bins[][3] = {{32, 1024, 32768}, {16, 512, 16384}, {64, 2048, 65536},
                                     {32, 256, 8192},   {8, 256, 32768},   {32, 2048, 262144}};
   for (int pass = 0; pass < 2; ++pass) {
     for (int c = 0; c < 4; ++c) {
-      const int count = c == 0 ? 6 : c == 1 ? 5 : c == 2 ? 6 : 2;
+      const int count = c == 0 ? 9 : c == 1 ? 6 : c == 2 ? 6 : 2;
       for (int i = 0; i < count; ++i) {
         g3_bfs_opts o = best;
         if (c == 0) o.alpha = alphas[i];
