@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(256) td_front(const int64_t* __restrict__ off,
 // The three bins in one launch: warp per warp-bin vertex, CTA per CTA-bin
 // vertex, and the grid bin as one flattened edge range split evenly over all
 // warps of the grid (Algorithm 4's even split, applied to every hub at once).
-__global__ void __launch_bounds__(256, 5) td_bins(const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(256, 6) td_bins(const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
                                                uint32_t* visited, PlOut plo, Bufs B,
                                                const int32_t* __restrict__ bins,
