@@ -208,8 +208,8 @@ typedef struct {
  *   stats         : host array of max_stats entries or NULL; receives one
  *                   record per level while room remains. *n_levels (may be
  *                   NULL) receives the number of non-empty frontiers.
- * The first call on a graph allocates its BFS workspace (about 24 bytes per
- * vertex); later calls allocate nothing. By default the level loop runs on
+ * The first call on a graph allocates its BFS workspace (about 52 bytes per
+ * BFS vertex plus 8 per vertex of the input); later calls allocate nothing. By default the level loop runs on
  * the device as one CUDA graph (a WHILE node over a SWITCH of level kinds,
  * conditions set by the device-side controller; rebuilt when the options
  * change) and the call synchronises `stream` once after it and before
@@ -248,8 +248,8 @@ void g3_msbfs_opts_default(g3_msbfs_opts* o);
  *              only themselves).
  *   n_levels : (nullable) number of levels run.
  *   ms       : (nullable) time of the call on the device, CUDA events.
- * The first call on a graph allocates its workspace (about 100 bytes per
- * vertex). Synchronises `stream` once per level and before returning.
+ * The first call on a graph allocates its workspace (about 112 bytes per
+ * BFS vertex). Synchronises `stream` once per level and before returning.
  * Errors: G3_EINVAL, G3_ERANGE (a level above 126 does not fit int8),
  * G3_ENOMEM, G3_ECUDA. */
 g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k, const g3_msbfs_opts* opts,

@@ -105,11 +105,20 @@ struct PlOut {
   int32_t bits;
 };
 
+// The packed words are stored with an L2 evict-last policy: the output pass
+// gathers them after the search, so they should outlive the streamed rows.
+__device__ __forceinline__ void st_keep_l2(uint32_t* a, uint32_t v) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ void pl_put(const PlOut& o, int32_t x, int32_t parent,
                                        int32_t level) {
   const uint32_t lmax = (1u << o.bits) - 1u;
   const uint32_t code = (uint32_t)level < lmax ? (uint32_t)level : lmax;
-  o.pl[x] = ((uint32_t)parent << o.bits) | code;
+  st_keep_l2(o.pl + x, ((uint32_t)parent << o.bits) | code);
   if ((uint32_t)level >= lmax) o.deep[x] = level;
 }
 
