@@ -691,6 +691,8 @@ def msbfs_arm(args, rank, world):
     ev_s = torch.cuda.Event(enable_timing=True)
     ev_e = torch.cuda.Event(enable_timing=True)
 
+    work = []  # per-launch work counts for the roofline
+
     def step():
         t = []
         for b in batches:
@@ -700,6 +702,7 @@ def msbfs_arm(args, rank, world):
             ev_e.record()
             ev_e.synchronize()
             t.append(ev_s.elapsed_time(ev_e))
+            work.append(g3.g3_msbfs_last_stats(g))
         return t
 
     for _ in range(args.warmup):
@@ -732,10 +735,17 @@ def msbfs_arm(args, rank, world):
         ev_e.record()
         ev_e.synchronize()
         plain_t.append(ev_s.elapsed_time(ev_e))
-    # compulsory bytes per launch: the BFS-graph CSR read once, the per-vertex
-    # state words (vis, F, next: 3 x 8 B) written once, 64 B of levels per vertex
+    # algorithmic bytes per launch from the launch's own work counts: a pull
+    # level reads every vertex's source word (8 B) and, for the vertices it
+    # scans, two row bounds (16 B), the entries it reads (4 B each) with the
+    # frontier word of each (8 B) and writes the next-frontier word (8 B); a
+    # push level reads every pushed entry (4 B), the target's word (8 B) and
+    # ORs into it (8 B); the output reads 64 B of levels per BFS vertex and
+    # writes k bytes per vertex
     nb, nnz = info["n_bfs"], info["nnz"]
-    comp = 8 * (nb + 1) + 4 * nnz + 24 * nb + 64 * n
+    w_t = work[-len(times):]
+    comp = sum(8 * nb * w["pull_levels"] + 24 * w["pull_vertices"] + 12 * w["pull_entries"]
+               + 20 * w["push_entries"] + 64 * nb + 64 * n for w in w_t) / len(w_t)
     avg_ms = sum(times) / len(times)
     peak, peak_kind = load_peaks()
     cpu = None
@@ -765,8 +775,11 @@ def msbfs_arm(args, rank, world):
                          "achieved": comp / (avg_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": comp / (avg_ms / 1e3) / 1e9 / peak, "traffic": None,
                          "peak_kind": peak_kind, "bytes_per_launch": comp,
-                         "bytes_model": "compulsory: CSR once + 3x8 B state + 64 B levels "
-                                        "per vertex (a lower bound; levels re-read state)"},
+                         "bytes_model": "per launch from g3_msbfs_last_stats: 8 B x nb per "
+                                        "pull level, 24 B per scanned vertex, 12 B per read "
+                                        "entry, 20 B per pushed entry, 64 B x nb + 64 B x n "
+                                        "output",
+                         "work_last_launch": w_t[-1]},
             "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks,
             "e2e": None,
             "graph": {"n": info["n"], "n_plus": info["n_plus"], "nnz": info["nnz"],

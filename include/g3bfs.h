@@ -255,6 +255,19 @@ void g3_msbfs_opts_default(g3_msbfs_opts* o);
 g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k, const g3_msbfs_opts* opts,
                    int8_t* level, int32_t* n_levels, float* ms, void* stream);
 
+/* Work counts of the last g3_msbfs call on the graph (for the roofline). */
+typedef struct {
+  int32_t levels, pull_levels, push_levels, reserved;
+  int64_t pull_entries;   /* row entries the pull levels read (early exits counted
+                             where they happened) */
+  int64_t pull_vertices;  /* vertices whose rows the pull levels scanned */
+  int64_t push_entries;   /* row entries of the pushed frontier vertices */
+} g3_msbfs_stats;
+
+/* Copies the counts of the last g3_msbfs call. Host only, no synchronisation.
+ * Errors: G3_EINVAL, G3_ESTATE (no multi-source search on the graph yet). */
+g3_status g3_msbfs_last_stats(const g3_graph* g, g3_msbfs_stats* out);
+
 /* ------------------------------------------------- batched small graphs */
 
 /* Many small graphs searched in one persistent, CUDA-graph-captured launch

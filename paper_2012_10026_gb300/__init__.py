@@ -69,6 +69,13 @@ class g3_msbfs_opts(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 6)]
 
 
+class g3_msbfs_stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("pull_levels", ctypes.c_int32),
+                ("push_levels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("pull_entries", ctypes.c_int64), ("pull_vertices", ctypes.c_int64),
+                ("push_entries", ctypes.c_int64)]
+
+
 class g3_batch_opts(ctypes.Structure):
     _fields_ = [("warp_max_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
@@ -115,6 +122,7 @@ _SIGS = {
                                 ctypes.POINTER(g3_msbfs_opts), _vp,
                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
                                 _vp]),
+    "g3_msbfs_last_stats": (ctypes.c_int, [_vp, ctypes.POINTER(g3_msbfs_stats)]),
     "g3_batch_opts_default": (None, [ctypes.POINTER(g3_batch_opts)]),
     "g3_batch_pack": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, _vp,
                                      ctypes.POINTER(_vp)]),
@@ -294,6 +302,13 @@ def g3_msbfs(graph: "Graph", roots, level, options: g3_msbfs_opts | None = None,
                           _ptr(level), ctypes.byref(nl), ctypes.byref(ms), _stream(stream)),
            "g3_msbfs")
     return nl.value, ms.value
+
+
+def g3_msbfs_last_stats(graph: "Graph") -> dict:
+    """Work counts of the last g3_msbfs call on the graph."""
+    st = g3_msbfs_stats()
+    _check(lib().g3_msbfs_last_stats(graph.handle, ctypes.byref(st)), "g3_msbfs_last_stats")
+    return {k: getattr(st, k) for k, _ in st._fields_ if k != "reserved"}
 
 
 class Batch:

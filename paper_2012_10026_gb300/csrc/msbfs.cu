@@ -33,8 +33,10 @@ struct g3_ms_ws {
   int2* items;       // (vertex, chunk index >= 1) of split rows
   int64_t items_cap;
   // [0] next queue len, [1] next sum of degrees, [2] heavy len, [3] items,
-  // [4] pending heavy vertices
+  // [4] pending heavy vertices (per level); [5] row entries read and [6]
+  // vertices scanned by the pull levels (per call)
   unsigned long long* ctr;
+  g3_msbfs_stats last;  // of the last call
   unsigned long long* h_ctr;
   int32_t* d_roots;
   cudaEvent_t ev[2];
@@ -235,6 +237,7 @@ __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __rest
                                                int32_t* heavy, int32_t* qn,
                                                unsigned long long* ctr) {
   const bool col_al16 = ((uintptr_t)col & 15) == 0;
+  unsigned long long rd_all = 0, sc_all = 0;  // work counts, added once per warp
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nb;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
@@ -248,6 +251,7 @@ __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __rest
         if (e - b >= heavy_deg) {
           big = true;
         } else {
+          sc_all += 1;
           // up to the next multiple of 4 one entry at a time, then one
           // 128-bit column load and four independent gathers per step; the
           // exit test runs per step (vector loads only on a 16-byte aligned
@@ -260,6 +264,7 @@ __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __rest
             acc |= (__ldg(&F[c4.x]) | __ldg(&F[c4.y])) | (__ldg(&F[c4.z]) | __ldg(&F[c4.w]));
           }
           for (; j < e && (acc | vv) != full; ++j) acc |= __ldg(&F[col[j]]);
+          rd_all += (unsigned long long)(j - b);
           nv = acc & ~vv;
           if (nv) {
             ms_take((int32_t)v, nv, vis, vv, lv, lnext);
@@ -275,6 +280,14 @@ __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __rest
     for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
     if ((threadIdx.x & 31) == 0 && d) atomicAdd(&ctr[1], d);
   }
+  for (int o = 16; o; o >>= 1) {
+    rd_all += __shfl_xor_sync(0xffffffffu, rd_all, o);
+    sc_all += __shfl_xor_sync(0xffffffffu, sc_all, o);
+  }
+  if ((threadIdx.x & 31) == 0 && sc_all) {
+    atomicAdd(&ctr[5], rd_all);
+    atomicAdd(&ctr[6], sc_all);
+  }
 }
 
 // Frontier sources among row entries [b, e) (warp-wide call): the OR of
@@ -282,11 +295,13 @@ __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __rest
 __device__ __forceinline__ uint64_t ms_pull_range(int64_t b, int64_t e, uint64_t have,
                                                   uint64_t full,
                                                   const int32_t* __restrict__ col,
-                                                  const uint64_t* __restrict__ F, int lane) {
+                                                  const uint64_t* __restrict__ F, int lane,
+                                                  int64_t& read) {
   uint64_t acc = 0;
   for (int64_t j0 = b; j0 < e; j0 += 32) {
     const int64_t j = j0 + lane;
     uint64_t x = j < e ? __ldg(&F[col[j]]) : 0ull;
+    read += e - j0 < 32 ? e - j0 : 32;
     for (int o = 16; o; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
     acc |= x;
     if ((acc | have) == full) break;
@@ -321,11 +336,13 @@ __global__ void __launch_bounds__(256) ms_pull_heavy(const int32_t* __restrict__
   const int64_t len = (int64_t)ctr[2];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int64_t read = 0, scanned = 0;  // work counts, added once per warp
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < len; i += nwarps) {
     const int32_t v = heavy[i];
     const uint64_t vv = vis[v];
     const int64_t b = off[v], e = off[v + 1];
-    const uint64_t acc = ms_pull_range(b, min(e, b + MS_CHUNK), vv, full, col, F, lane);
+    const uint64_t acc = ms_pull_range(b, min(e, b + MS_CHUNK), vv, full, col, F, lane, read);
+    ++scanned;
     if (e - b > MS_CHUNK && (acc | vv) != full) {
       ms_queue_chunks(v, e - b, items, &ctr[3], lane);
       if (lane == 0) {
@@ -336,6 +353,10 @@ __global__ void __launch_bounds__(256) ms_pull_heavy(const int32_t* __restrict__
       ms_emit(v, acc & ~vv, vv, vis, Fn, lv, lnext, qn, e - b, ctr);
     }
   }
+  if (lane == 0 && scanned) {
+    atomicAdd(&ctr[5], (unsigned long long)read);
+    atomicAdd(&ctr[6], (unsigned long long)scanned);
+  }
 }
 
 // Pull of the queued chunks, one warp per item; partial ORs meet in N[v].
@@ -345,17 +366,19 @@ __global__ void __launch_bounds__(256) ms_pull_chunks(const int2* __restrict__ i
                                                       const uint64_t* __restrict__ F,
                                                       const uint64_t* __restrict__ vis,
                                                       uint64_t* N, uint64_t full,
-                                                      const unsigned long long* ctr) {
+                                                      unsigned long long* ctr) {
   const int64_t len = (int64_t)ctr[3];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int64_t read = 0;  // entries read, added once per warp
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < len; i += nwarps) {
     const int2 it = items[i];
     const int64_t b = off[it.x] + (int64_t)it.y * MS_CHUNK;
-    const uint64_t acc =
-        ms_pull_range(b, min(off[it.x + 1], b + MS_CHUNK), vis[it.x], full, col, F, lane);
+    const uint64_t acc = ms_pull_range(b, min(off[it.x + 1], b + MS_CHUNK), vis[it.x], full,
+                                       col, F, lane, read);
     if (lane == 0 && acc) atomicOr((unsigned long long*)&N[it.x], acc);
   }
+  if (lane == 0 && read) atomicAdd(&ctr[5], (unsigned long long)read);
 }
 
 // Finishes the split heavy vertices: new sources = N[v] & ~vis[v]; N cleared.
@@ -490,6 +513,8 @@ extern "C" g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k,
   uint64_t *F = w->fa, *Fn = w->fb;
   int32_t *q = w->qa, *qn = w->qb;
   int32_t L = 0;
+  g3_msbfs_stats stats;
+  memset(&stats, 0, sizeof(stats));
   for (;; ++L) {
     G3_TRY_CUDA(cudaMemcpyAsync(h, w->ctr, 24, cudaMemcpyDeviceToHost, s));
     G3_TRY_CUDA(cudaStreamSynchronize(s));
@@ -503,6 +528,12 @@ extern "C" g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k,
     }
     G3_TRY_CUDA(cudaMemsetAsync(w->ctr, 0, 40, s));
     const bool pull = mf * (int64_t)o.push_alpha > g->nnz;
+    if (pull) {
+      stats.pull_levels++;
+    } else {
+      stats.push_levels++;
+      stats.push_entries += mf;  // every row entry of the frontier is pushed
+    }
     const int8_t lnext = (int8_t)(L + 1);
     if (pull) {
       ms_pull<<<grid, 256, 0, s>>>(nb, g->off, g->col, F, w->vis, Fn, w->lv, lnext, full,
@@ -546,12 +577,30 @@ extern "C" g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k,
     qn = tq;
   }
   if (n_levels) *n_levels = L;
+  stats.levels = L;
   ms_out<<<grid, 256, 0, s>>>(g->n, nb, k, n2o, w->vis, w->lv, level);
   G3_CHECK_LAUNCH();
   ms_roots_out<<<1, 64, 0, s>>>(w->d_roots, k, g->n, level);
   G3_CHECK_LAUNCH();
   G3_TRY_CUDA(cudaEventRecord(w->ev[1], s));
+  G3_TRY_CUDA(cudaMemcpyAsync(h + 5, w->ctr + 5, 16, cudaMemcpyDeviceToHost, s));
   G3_TRY_CUDA(cudaStreamSynchronize(s));
   if (ms) cudaEventElapsedTime(ms, w->ev[0], w->ev[1]);
+  stats.pull_entries = (int64_t)h[5];
+  stats.pull_vertices = (int64_t)h[6];
+  w->last = stats;
+  return G3_OK;
+}
+
+extern "C" g3_status g3_msbfs_last_stats(const g3_graph* g, g3_msbfs_stats* out) {
+  if (!g || !out) {
+    g3_set_error("g3_msbfs_last_stats: null argument");
+    return G3_EINVAL;
+  }
+  if (!g->ms) {
+    g3_set_error("g3_msbfs_last_stats: no multi-source search has run on this graph");
+    return G3_ESTATE;
+  }
+  *out = g->ms->last;
   return G3_OK;
 }

@@ -63,7 +63,8 @@ def test_bad_arguments_rejected_on_host(L):
 def test_struct_layouts_match_header(tmp_path):
     # the C compiler's layout of each struct in include/g3bfs.h must equal the
     # binding's ctypes layout, field by field
-    structs = [g3.g3_graph_info, g3.g3_bfs_opts, g3.g3_level_stats]
+    structs = [g3.g3_graph_info, g3.g3_bfs_opts, g3.g3_level_stats, g3.g3_msbfs_opts,
+               g3.g3_msbfs_stats, g3.g3_batch_opts, g3.g3_tune_entry]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "g3bfs.h"', 'int main(void){']
     for S in structs:
         lines.append(f'printf("{S.__name__} %zu\\n", sizeof({S.__name__}));')

@@ -108,3 +108,30 @@ def test_msbfs_level_range_and_bad_args():
         g3.g3_msbfs(g, [n], lv)
     g.free()
     g2.free()
+
+
+def test_msbfs_work_counts():
+    src, dst = graphgen.kronecker_edges(12, 16, seed=4)
+    n = 1 << 12
+    off, col = oracle.build_csr(src, dst, n)
+    deg = np.diff(off)
+    g = g3.g3_build_csr(_dev(src), _dev(dst), n)
+    g3.g3_rcm_relabel(g)
+    root = int(np.argmax(deg))
+    _, lref = oracle.bfs(off, col, root)
+    # push only, one source: every reached vertex is pushed once
+    lv, nl, _ = _run(g, n, [root], push_alpha=1)
+    st = g3.g3_msbfs_last_stats(g)
+    assert st["levels"] == nl == st["push_levels"] and st["pull_levels"] == 0
+    assert st["push_entries"] == int(deg[lref >= 0].sum())
+    assert st["pull_entries"] == 0 and st["pull_vertices"] == 0
+    # pull only: each pull level scans the vertices not yet reached by every
+    # source; one source -> the unreached vertices of the level, early exits
+    lv, nl, _ = _run(g, n, [root], push_alpha=1 << 30)
+    st = g3.g3_msbfs_last_stats(g)
+    assert st["pull_levels"] == nl and st["push_levels"] == 0
+    nb = g.info["n_bfs"]
+    reached_by = [int(((lref >= 0) & (lref <= L) & (deg > 0)).sum()) for L in range(nl)]
+    assert st["pull_vertices"] == sum(nb - r for r in reached_by)
+    assert 0 < st["pull_entries"] <= int(deg.sum()) * nl
+    g.free()
