@@ -87,7 +87,9 @@ def parse_args():
                     help="msbfs: fixed warp-pull degree (-1: autotuned)")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--batch-warp-max-n", type=int, default=-1,
-                    help="batch: warp-per-graph size limit (-1: autotuned)")
+                    help="batch: warp-per-graph size limit (-1: autotuned with the mode)")
+    ap.add_argument("--batch-mode", type=int, default=0,
+                    help="batch, with --batch-warp-max-n: 0 persistent kernel, 1 union search")
     ap.add_argument("--tune-cache", default=os.path.join(ROOT, "paper_2012_10026_gb300",
                                                          "tune_cache.txt"),
                     help="msbfs/batch: autotuner cache ('' = tune afresh, no cache)")
@@ -862,7 +864,7 @@ def batch_arm(args, rank, world):
         o, tune_rec = g3.autotune_batch(b, roots, parent, level, args.tune_cache or None)
         t_tune = time.perf_counter() - t_tune
     else:
-        o = g3.batch_opts(warp_max_n=args.batch_warp_max_n)
+        o = g3.batch_opts(warp_max_n=args.batch_warp_max_n, mode=args.batch_mode)
     g3.g3_bfs_batch(b, roots, parent, level, o)
     src_all = torch.cat(srcs)
     del srcs
@@ -938,7 +940,7 @@ def batch_arm(args, rank, world):
         line = _common_line(args, world, f"GTEPS, {len(specs)} small Kronecker graphs "
                             "(SCALE 8-14) in one captured launch", value, "GTEPS", times,
                             {"workload": f"kronecker_batch{len(specs)}_scale8-14_ef16_rcm_1root",
-                             "warp_max_n": o.warp_max_n,
+                             "warp_max_n": o.warp_max_n, "mode": o.mode,
                              "l2": "256 MB write between launches (L2 flush)",
                              "parallelism": "replicas"})
         line.update({

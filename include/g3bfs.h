@@ -275,10 +275,17 @@ g3_status g3_msbfs_last_stats(const g3_graph* g, g3_msbfs_stats* out);
 typedef struct g3_batch g3_batch;
 
 typedef struct {
-  int32_t warp_max_n;  /* graphs with at most this many BFS vertices are searched
-                          by one warp, larger ones by a whole CTA (1024; at most
-                          2048 are ever given to a warp) */
-  int32_t reserved[7];
+  int32_t warp_max_n;  /* mode 0: graphs with at most this many BFS vertices are
+                          searched by one warp, larger ones by a whole CTA (1024;
+                          at most 2048 are ever given to a warp) */
+  int32_t mode;        /* 0 (default): one persistent kernel, each graph searched
+                          by its own warp or CTA with its bitmaps in shared
+                          memory, captured once into a CUDA graph; 1: one
+                          level-synchronous search over the union of the graphs
+                          seeded with all roots at once (the graphs are disjoint,
+                          so the levels of one cannot reach another), run by the
+                          single-source kernels and level-loop graph */
+  int32_t reserved[6];
 } g3_batch_opts;
 
 void g3_batch_opts_default(g3_batch_opts* o);
@@ -295,10 +302,11 @@ g3_status g3_batch_info_get(const g3_batch* b, int32_t* G, int64_t* N, int64_t* 
 
 /* One BFS per graph: roots (device, G entries, union original IDs, root g in
  * graph g's range), parent and level (device, N entries each, union original
- * IDs; a root outside its graph's range leaves that graph all -1). The first
- * call with a given (roots, parent, level, warp_max_n) captures the launch into
- * a CUDA graph; later calls only launch it. ms (nullable): device time of the
- * launch, which then synchronises; otherwise the call is asynchronous. */
+ * IDs; a root outside its graph's range leaves that graph all -1). Mode 0: the
+ * first call with a given (roots, parent, level, warp_max_n) captures the
+ * launch into a CUDA graph, later calls only launch it; asynchronous unless ms
+ * is given. Mode 1: synchronises (the controller's record is read back).
+ * ms (nullable): device time of the call, which then synchronises. */
 g3_status g3_bfs_batch(g3_batch* b, const int32_t* roots, const g3_batch_opts* opts,
                        int32_t* parent, int32_t* level, float* ms, void* stream);
 
@@ -318,7 +326,8 @@ typedef struct {
   int32_t size_class;  /* floor(log2(BFS vertices per graph)) */
   int32_t deg_class;   /* floor(log2(CSR entries per BFS vertex)) */
   int32_t p[6];        /* chosen values: BFS (alpha, beta, t1, t2, t3, bu_reverse);
-                          MS-BFS (push_alpha, pull_warp_deg); batch (warp_max_n);
+                          MS-BFS (push_alpha, pull_warp_deg); batch (warp_max_n,
+                          mode);
                           unused slots 0 */
   int32_t points;      /* candidates timed; 0 when the entry came from the cache */
   float ms;            /* device ms of the chosen point (BFS: summed over roots) */
@@ -350,8 +359,8 @@ g3_status g3_tune_cache_store(const char* path, const g3_tune_entry* e);
  *                       beta, (t1, t2, t3) and bu_reverse; the controller stays.
  *   g3_autotune_msbfs : roots host (k <= 64), level as for g3_msbfs; full grid
  *                       over push_alpha x pull_warp_deg.
- *   g3_autotune_batch : roots/parent/level as for g3_bfs_batch; warp_max_n
- *                       over {0, 64, ..., 2048}.
+ *   g3_autotune_batch : roots/parent/level as for g3_bfs_batch; mode 0 with
+ *                       warp_max_n over {0, 64, ..., 2048}, and mode 1.
  * Errors: those of the timed call, G3_EINVAL, G3_ENOMEM. */
 g3_status g3_autotune_bfs(g3_graph* g, const int32_t* roots, int32_t nroots, int32_t* parent,
                           int32_t* level, const char* cache_path, g3_bfs_opts* opts,

@@ -77,7 +77,8 @@ class g3_msbfs_stats(ctypes.Structure):
 
 
 class g3_batch_opts(ctypes.Structure):
-    _fields_ = [("warp_max_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("warp_max_n", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class g3_tune_entry(ctypes.Structure):

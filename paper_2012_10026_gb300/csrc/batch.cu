@@ -3,7 +3,8 @@
 //
 // g3_batch_pack concatenates already relabelled graphs into one union CSR
 // (graph g keeps the vertex range [voff[g], voff[g+1]) in both ID spaces).
-// g3_bfs_batch runs one persistent kernel, captured once into a CUDA graph
+// Two ways to search the batch (g3_batch_opts.mode):
+//  0  one persistent kernel per launch, captured once into a CUDA graph
 // together with the reset of its work counters: resident blocks take graphs
 // from two work lists with an atomic counter -- graphs with at most
 // warp_max_n BFS vertices are searched by one warp each, larger ones by a
@@ -13,6 +14,11 @@
 // claims) or bottom-up (lane per vertex, early exit on the first frontier
 // neighbour), chosen by the same alpha/beta rule as g3_bfs; parent[] and
 // level[] are written in original IDs inside the graph's own ID range.
+//  1  one level-synchronous search over the whole union, seeded with every
+//     graph's root at once: the graphs are disjoint, so no level of one can
+//     reach another, and the single-source machinery (degree-binned top-down,
+//     bottom-up pull, device controller, level loop as a CUDA graph) runs
+//     over all of them with the whole GPU behind every level.
 #include <stdlib.h>
 #include <string.h>
 
@@ -44,6 +50,7 @@ struct g3_batch {
   int32_t g_thresh;
   int32_t n_warp, n_cta;
   cudaEvent_t ev[2];
+  g3_graph ug;  // the union as a relabelled graph (arrays above, not owned)
 };
 
 struct BatchArgs {
@@ -252,6 +259,7 @@ extern "C" void g3_batch_free(g3_batch* b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   for (int i = 0; i < 2; ++i)
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  g3_bfs_ws_free(b->ug.ws);
   delete b;
 }
 
@@ -263,7 +271,7 @@ extern "C" g3_status g3_batch_pack(g3_graph* const* graphs, int32_t G, void* str
   }
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
-  int64_t N = 0, nnz = 0;
+  int64_t N = 0, nnz = 0, maxdeg = 0;
   for (int32_t i = 0; i < G; ++i) {
     const g3_graph* g = graphs[i];
     if (!g || !g->relabelled) {
@@ -277,6 +285,7 @@ extern "C" g3_status g3_batch_pack(g3_graph* const* graphs, int32_t G, void* str
     }
     N += g->n;
     nnz += g->nnz;
+    maxdeg = std::max<int64_t>(maxdeg, g->max_degree);
   }
   if (N >= (1ll << 31)) {
     g3_set_error("g3_batch_pack: %lld vertices in total do not fit int32", (long long)N);
@@ -365,6 +374,18 @@ extern "C" g3_status g3_batch_pack(g3_graph* const* graphs, int32_t G, void* str
     return st;
   }
   b->g_thresh = -1;
+  // the union as one relabelled graph: every union vertex is a BFS-graph
+  // vertex (isolated ones have empty rows)
+  b->ug.n = (int32_t)N;
+  b->ug.nnz = nnz;
+  b->ug.max_degree = maxdeg;
+  b->ug.n_bfs = (int32_t)N;
+  b->ug.n_plus = (int32_t)N;
+  b->ug.relabelled = 1;
+  b->ug.off = b->off;
+  b->ug.col = b->col;
+  b->ug.old_of_new = b->orig_of;
+  b->ug.new_of_old = b->label_of;
   *out = b;
   return G3_OK;
 }
@@ -373,6 +394,7 @@ extern "C" void g3_batch_opts_default(g3_batch_opts* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
   o->warp_max_n = 1024;
+  o->mode = 0;
 }
 
 extern "C" g3_status g3_batch_info_get(const g3_batch* b, int32_t* G, int64_t* N, int64_t* nnz) {
@@ -452,11 +474,21 @@ extern "C" g3_status g3_bfs_batch(g3_batch* b, const int32_t* roots, const g3_ba
   }
   g3_batch_opts o;
   if (opts) o = *opts; else g3_batch_opts_default(&o);
-  if (o.warp_max_n < 0) {
+  if (o.warp_max_n < 0 || o.mode < 0 || o.mode > 1) {
     g3_set_error("g3_bfs_batch: bad options");
     return G3_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (o.mode == 1) {
+    G3_TRY_CUDA(cudaEventRecord(b->ev[0], s));
+    G3_TRY(g3_bfs_multi_root(&b->ug, roots, b->G, b->voff, nullptr, parent, level, s));
+    G3_TRY_CUDA(cudaEventRecord(b->ev[1], s));
+    if (ms) {
+      G3_TRY_CUDA(cudaEventSynchronize(b->ev[1]));
+      cudaEventElapsedTime(ms, b->ev[0], b->ev[1]);
+    }
+    return G3_OK;
+  }
   if (!b->gexec || b->g_roots != roots || b->g_parent != parent || b->g_level != level ||
       b->g_thresh != o.warp_max_n) {
     G3_TRY_CUDA(cudaStreamSynchronize(s));

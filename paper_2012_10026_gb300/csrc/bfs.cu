@@ -321,6 +321,68 @@ __global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, in
   log_frontier(log, c);
 }
 
+// Sets up F_0 with several roots at once: root i counts when it is a
+// BFS-graph vertex and, with lo given, lies in [lo[i], lo[i+1]) (the batched
+// search over disjoint graphs seeds one root per graph, so their levels
+// cannot interfere). Repeated roots are seeded once. One block.
+__global__ void __launch_bounds__(1024) bfs_roots_multi(
+    const int32_t* __restrict__ roots, int32_t count, const int32_t* __restrict__ lo,
+    const int32_t* new_of_old, int32_t nb, int64_t nnz, const int64_t* off, uint32_t* visited,
+    PlOut plo, int32_t* q, Ctrl* c, LevelLog* log, int t1, int t2, int t3, int cap) {
+  __shared__ unsigned long long s_nf, s_mf, s_hist[4];
+  __shared__ int s_min, s_max;
+  if (threadIdx.x == 0) {
+    s_nf = s_mf = 0;
+    for (int k = 0; k < 4; ++k) s_hist[k] = 0;
+    s_min = 0x7fffffff;
+    s_max = -1;
+  }
+  __syncthreads();
+  for (int32_t i = threadIdx.x; i < count; i += blockDim.x) {
+    const int32_t root = roots[i];
+    if (lo && (root < lo[i] || root >= lo[i + 1])) continue;
+    const int32_t r = new_of_old ? new_of_old[root] : root;
+    if (r < 0 || r >= nb) continue;
+    const uint32_t bit = 1u << (r & 31);
+    if (atomicOr(&visited[r >> 5], bit) & bit) continue;
+    pl_put(plo, r, root, 0);
+    q[atomicAdd(&s_nf, 1ull)] = r;
+    const long long d = off[r + 1] - off[r];
+    atomicAdd(&s_mf, (unsigned long long)d);
+    atomicAdd(&s_hist[deg_bucket(d)], 1ull);
+    atomicMin(&s_min, r);
+    atomicMax(&s_max, r);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  memset(c, 0, sizeof(Ctrl));
+  reset_next(c);
+  c->t1 = t1;
+  c->t2 = t2;
+  c->t3 = t3;
+  c->dir = G3_DIR_TD;
+  c->fmt_queue = 1;
+  c->cap = cap;
+  const long long nf = (long long)s_nf, mf = (long long)s_mf;
+  if (nf == 0) {
+    c->nu = nb;
+    c->mu = nnz;
+    c->mode = MODE_DONE;
+    return;
+  }
+  c->nf = nf;
+  c->mf = mf;
+  for (int k = 0; k < 4; ++k) c->hist[k] = (long long)s_hist[k];
+  c->id_min = s_min;
+  c->id_max = s_max;
+  c->n_visited = nf;
+  c->m_visited = mf;
+  c->nu = nb - nf;
+  c->mu = nnz - mf;
+  c->mode = MODE_TD_Q;
+  log_frontier(log, c);
+}
+
 // --------------------------------------------------------------- top-down
 struct TdArgs {
   const int64_t* off;
@@ -1268,9 +1330,16 @@ static void fill_record(g3_level_stats* r, int32_t L, const LevelLog& e) {
   r->t3 = e.t3;
 }
 
+// Several roots (device array) instead of one: see bfs_roots_multi.
+struct MultiRoots {
+  const int32_t* roots;
+  int32_t count;
+  const int32_t* lo;
+};
+
 static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32_t* parent,
                           int32_t* level, g3_level_stats* stats, int32_t max_stats,
-                          int32_t* n_levels, cudaStream_t s) {
+                          int32_t* n_levels, cudaStream_t s, const MultiRoots* mr = nullptr) {
   if (!g->ws) G3_TRY(ws_create(g, &g->ws));
   g3_bfs_ws* ws = g->ws;
   const int32_t nb = ws->nb;
@@ -1282,9 +1351,18 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   if (stats && max_stats > 0) memset(stats, 0, sizeof(g3_level_stats) * (size_t)max_stats);
 
   G3_TRY_CUDA(cudaMemsetAsync(ws->visited, 0, (size_t)(ws->nwords + 1) * 4, s));
-  bfs_root<<<1, 1, 0, s>>>(g->relabelled ? g->new_of_old : nullptr, root, nb, g->nnz, g->off,
-                           ws->visited, ws->plo, ws->qa, ws->ctrl, ws->log, o->t1, o->t2, o->t3,
-                           host_driven ? 0x7fffffff : GRAPH_LEVEL_CAP);
+  const int cap = host_driven ? 0x7fffffff : GRAPH_LEVEL_CAP;
+  if (mr) {
+    bfs_roots_multi<<<1, 1024, 0, s>>>(mr->roots, mr->count, mr->lo,
+                                       g->relabelled ? g->new_of_old : nullptr, nb, g->nnz,
+                                       g->off, ws->visited, ws->plo, ws->qa, ws->ctrl, ws->log,
+                                       o->t1, o->t2, o->t3, cap);
+    root = -1;  // the output pass has no single root to patch
+  } else {
+    bfs_root<<<1, 1, 0, s>>>(g->relabelled ? g->new_of_old : nullptr, root, nb, g->nnz, g->off,
+                             ws->visited, ws->plo, ws->qa, ws->ctrl, ws->log, o->t1, o->t2,
+                             o->t3, cap);
+  }
   G3_CHECK_LAUNCH();
 
   if (!host_driven) {
@@ -1355,6 +1433,17 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   free(hl);
   G3_TRY_CUDA(e);
   return G3_OK;
+}
+
+g3_status g3_bfs_multi_root(g3_graph* g, const int32_t* roots, int32_t count, const int32_t* lo,
+                            const g3_bfs_opts* opts, int32_t* parent, int32_t* level,
+                            cudaStream_t s) {
+  g3_bfs_opts o;
+  if (opts) o = *opts; else g3_bfs_opts_default(&o);
+  MultiRoots mr{roots, count, lo};
+  g3_status st = bfs_impl(g, -1, &o, parent, level, nullptr, 0, nullptr, s, &mr);
+  if (st != G3_OK) cudaStreamSynchronize(s);
+  return st;
 }
 
 extern "C" g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, int32_t* parent,

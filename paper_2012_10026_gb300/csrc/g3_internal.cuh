@@ -89,6 +89,12 @@ struct g3_graph {
 };
 
 void g3_bfs_ws_free(g3_bfs_ws* ws);
+// Search from several roots at once (device array; root i counts when it lies
+// in [lo[i], lo[i+1]), lo nullable); used by the batched search over a union
+// of disjoint graphs. Synchronises.
+g3_status g3_bfs_multi_root(g3_graph* g, const int32_t* roots, int32_t count, const int32_t* lo,
+                            const g3_bfs_opts* opts, int32_t* parent, int32_t* level,
+                            cudaStream_t s);
 void g3_ms_ws_free(g3_ms_ws* ws);
 
 // ----------------------------------------------------------- device utils

@@ -377,6 +377,7 @@ extern "C" g3_status g3_autotune_batch(g3_batch* b, const int32_t* roots, int32_
   G3_TRY(cache_hit(cache_path, &e, &hit));
   if (hit) {
     opts->warp_max_n = e.p[0];
+    opts->mode = e.p[1];
     if (rec) *rec = e;
     return G3_OK;
   }
@@ -398,10 +399,16 @@ extern "C" g3_status g3_autotune_batch(g3_batch* b, const int32_t* roots, int32_
   G3_TRY(time_one(best, &best_ms));
   e.ms_default = best_ms;
   int points = 1;
-  static const int32_t limits[] = {0, 64, 128, 256, 512, 1024, 2048};
+  // mode 0 with each warp-group limit, then mode 1 (the union search)
+  static const int32_t limits[] = {0, 64, 128, 256, 512, 1024, 2048, -1};
   for (int32_t w : limits) {
     g3_batch_opts o = *opts;
-    o.warp_max_n = w;
+    if (w >= 0) {
+      o.mode = 0;
+      o.warp_max_n = w;
+    } else {
+      o.mode = 1;
+    }
     if (!memcmp(&o, opts, sizeof(o))) continue;
     float ms = 0.f;
     G3_TRY(time_one(o, &ms));
@@ -413,6 +420,7 @@ extern "C" g3_status g3_autotune_batch(g3_batch* b, const int32_t* roots, int32_
   }
   *opts = best;
   e.p[0] = best.warp_max_n;
+  e.p[1] = best.mode;
   e.points = points;
   e.ms = best_ms;
   if (cache_path) G3_TRY(g3_tune_cache_store(cache_path, &e));

@@ -79,8 +79,9 @@ def _roots(graphs, seed):
     return roots
 
 
-@pytest.mark.parametrize("warp_max_n", [0, 256, 1024, 1 << 30])
-def test_batch_levels_equal_oracle(batch, warp_max_n):
+@pytest.mark.parametrize("warp_max_n,mode", [(0, 0), (256, 0), (1024, 0), (1 << 30, 0),
+                                             (1024, 1)])
+def test_batch_levels_equal_oracle(batch, warp_max_n, mode):
     info = batch.info
     assert info["G"] == len(GRAPHS)
     assert info["N"] == sum(n for _, _, n in GRAPHS)
@@ -90,7 +91,8 @@ def test_batch_levels_equal_oracle(batch, warp_max_n):
         d_roots = _dev(np.asarray(roots) + voff[:-1])
         parent = torch.full((info["N"],), 7, dtype=torch.int32, device="cuda")
         level = torch.full((info["N"],), 7, dtype=torch.int32, device="cuda")
-        ms = g3.g3_bfs_batch(batch, d_roots, parent, level, g3.batch_opts(warp_max_n=warp_max_n))
+        ms = g3.g3_bfs_batch(batch, d_roots, parent, level,
+                             g3.batch_opts(warp_max_n=warp_max_n, mode=mode))
         assert ms > 0
         _check(GRAPHS, roots, parent.cpu().numpy(), level.cpu().numpy())
 
@@ -115,7 +117,8 @@ def test_batch_relaunch_reuses_capture(batch):
     _check(GRAPHS, roots, parent.cpu().numpy(), level.cpu().numpy())
 
 
-def test_batch_isolated_and_foreign_roots():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_isolated_and_foreign_roots(mode):
     graphs = GRAPHS[:1] + GRAPHS[-1:] + GRAPHS[1:6]  # graph 1: the sparse random one
     b = _pack(graphs)
     N = b.info["N"]
@@ -131,7 +134,7 @@ def test_batch_isolated_and_foreign_roots():
     glob[2] = voff[3]
     parent = torch.empty((N,), dtype=torch.int32, device="cuda")
     level = torch.empty((N,), dtype=torch.int32, device="cuda")
-    g3.g3_bfs_batch(b, _dev(glob), parent, level)
+    g3.g3_bfs_batch(b, _dev(glob), parent, level, g3.batch_opts(mode=mode))
     roots[2] = -1
     p, lv = parent.cpu().numpy(), level.cpu().numpy()
     _check(graphs, roots, p, lv)

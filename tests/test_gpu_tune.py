@@ -91,9 +91,10 @@ def test_autotune_batch(tmp_path):
     level = torch.empty(N, dtype=torch.int32, device="cuda")
     cache = str(tmp_path / "tune.txt")
     o, rec = g3.autotune_batch(b, d_roots, parent, level, cache)
-    assert rec.points == 7 and rec.ms <= rec.ms_default and rec.p[0] == o.warp_max_n
+    assert rec.points == 8 and rec.ms <= rec.ms_default
+    assert (rec.p[0], rec.p[1]) == (o.warp_max_n, o.mode)
     _, rec2 = g3.autotune_batch(b, d_roots, parent, level, cache)
-    assert rec2.points == 0 and rec2.p[0] == o.warp_max_n
+    assert rec2.points == 0 and (rec2.p[0], rec2.p[1]) == (o.warp_max_n, o.mode)
     g3.g3_bfs_batch(b, d_roots, parent, level, o)
     p, lv = parent.cpu().numpy(), level.cpu().numpy()
     for (s, d, n, r), vb in zip(host, voff):
