@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -151,7 +152,7 @@ def stop_clock_sampler(proc, path, gpu_index):
 
 
 def level_bytes(st, nb):
-    """Algorithmic bytes of one level's expansion kernels (see DESIGN.md):
+    """Algorithmic bytes of one level's expansion kernels:
     bottom-up: visited word read, two row bounds per unvisited vertex (8 B
     streamed), col entry + frontier-bitmap word per examined edge, parent and
     level per new vertex, next-frontier and visited word writes;
@@ -410,8 +411,7 @@ def gpu_arm(args, rank, world):
 
     for _ in range(args.warmup):
         one_step(opts, 0)
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/g3_clocks_{rank}.csv"
+    clk_path = os.path.join(tempfile.gettempdir(), f"g3_clocks_{rank}.csv")
     sampler = start_clock_sampler(clk_path)
     if dist:
         dist.barrier()
@@ -709,8 +709,7 @@ def msbfs_arm(args, rank, world):
 
     for _ in range(args.warmup):
         step()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_ms_rank{rank}.csv") \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/g3_clocks_ms_{rank}.csv"
+    clk_path = os.path.join(tempfile.gettempdir(), f"g3_clocks_ms_{rank}.csv")
     sampler = start_clock_sampler(clk_path)
     if dist:
         dist.barrier()
@@ -884,8 +883,7 @@ def batch_arm(args, rank, world):
 
     for _ in range(args.warmup):
         step()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv") \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/g3_clocks_b_{rank}.csv"
+    clk_path = os.path.join(tempfile.gettempdir(), f"g3_clocks_b_{rank}.csv")
     sampler = start_clock_sampler(clk_path)
     if dist:
         dist.barrier()

@@ -1,5 +1,5 @@
 """What the trained controller gains over the alpha/beta rule: trained on the
-GPU from record_both timings of small Kronecker graphs, judged by regret
+GPU from record_both timings of small Kronecker graphs, scored by regret
 (time of the chosen direction minus the faster one, summed over levels) on
 a held-out graph of a trained size, both controllers scored on the same
 recorded per-level times."""
