@@ -77,6 +77,9 @@ def parse_args():
     ap.add_argument("--rcm", type=int, default=1,
                     help="kron: 0 searches the graph in its generated labelling (no RCM, "
                          "isolated vertices kept), for the locality comparison")
+    ap.add_argument("--learned-check-scale", type=int, default=24,
+                    help="kron, learned controller: also compare it with the rule on a "
+                         "graph of this (trained) SCALE; 0 skips")
     ap.add_argument("--tune-bfs", type=int, default=1,
                     help="kron: autotune alpha/beta/bins/scan order first (cached)")
     ap.add_argument("--msbfs-compare", type=int, default=1,
@@ -548,6 +551,13 @@ def gpu_arm(args, rank, world):
             cpu = {"value": None, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                    "sample": "oracle leg did not finish: " + (d or {}).get("error", "timeout")}
 
+    # the trained controller against the rule on a graph of a size it was
+    # trained on (the headline graph is outside them, see learned_controller)
+    g.free()
+    check = None
+    if ctrl == g3.G3_CTRL_LEARNED and args.learned_check_scale > 0:
+        check = learned_check(args, flush)
+
     if rank == 0:
         levels = [len(st) for st in all_st]
         line = {
@@ -590,6 +600,7 @@ def gpu_arm(args, rank, world):
                 "options": "alpha/beta rule, library defaults (14, 24, 32/1024/32768)"},
             "options": {k: v for k, v in kw.items() if k != "mlp_params"},
             "learned_controller": learned_note,
+            "learned_vs_rule_trained_size": check,
             "autotune": None if tune_rec is None else dict(tune_rec.to_dict(), seconds=t_tune),
         }
         print(json.dumps(line), flush=True)
@@ -597,9 +608,50 @@ def gpu_arm(args, rank, world):
             with open(args.stats_out, "w") as f:
                 json.dump({"roots": roots, "m_r": [m_r[r] for r in roots], "times_ms": all_t,
                            "stats": all_st}, f)
-    g.free()
     if dist:
         dist.destroy_process_group()
+
+
+def learned_check(args, flush, reps=3):
+    """Harmonic-mean GTEPS of the trained controller and of the alpha/beta
+    rule (library defaults for both) over 64 roots of a Kronecker graph of a
+    size the controller was trained on; per root the best of `reps` runs."""
+    import torch
+    import graphgen
+    import paper_2012_10026_gb300 as g3
+    from paper_2012_10026_gb300.train_controller import controller_opts
+    scale, n = args.learned_check_scale, 1 << args.learned_check_scale
+    src, dst = graphgen.kronecker_edges_dev(scale, args.edgefactor, seed=args.seed)
+    flags = graphgen.nonisolated_flags_dev(src, dst, n).cpu().numpy()
+    roots = graphgen.pick_roots(flags, 64, args.root_seed).tolist()
+    g = g3.g3_build_csr(src, dst, n)
+    g3.g3_rcm_relabel(g)
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    m_r = []
+    for r in roots:
+        g3.g3_bfs(g, r, parent, level)
+        m_r.append(int((level[src.long()] >= 0).sum().item()))
+    del src, dst
+    lo, params, note = controller_opts(args.mlp, g.info["n_bfs"])
+    ev_s = torch.cuda.Event(enable_timing=True)
+    ev_e = torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"kronecker_scale{scale}_ef{args.edgefactor}_rcm_64roots",
+           "controller": note}
+    for name, o in (("learned", lo), ("rule", g3.opts())):
+        best = [float("inf")] * len(roots)
+        for _ in range(reps + 1):  # the first pass builds the level-loop graph
+            for i, r in enumerate(roots):
+                flush.fill_(1)
+                ev_s.record()
+                g3.g3_bfs(g, r, parent, level, o)
+                ev_e.record()
+                ev_e.synchronize()
+                best[i] = min(best[i], ev_s.elapsed_time(ev_e))
+        out[name] = {"value": harmonic_gteps(m_r, best), "unit": "GTEPS",
+                     "total_ms": sum(best)}
+    g.free()
+    return out
 
 
 # ------------------------------------------------- secondary workloads
