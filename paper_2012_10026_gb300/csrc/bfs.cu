@@ -1365,9 +1365,35 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   }
   G3_CHECK_LAUNCH();
 
+  // outputs in original IDs: device (or device-visible host) buffers, else
+  // staging buffers copied to the host at the end
+  int32_t* vp = device_view(parent);
+  int32_t* vl = device_view(level);
+  const bool dev_p = vp != nullptr, dev_l = vl != nullptr;
+  int32_t* op = dev_p ? vp : ws->out_parent;
+  int32_t* ol = dev_l ? vl : ws->out_level;
+  auto translate = [&]() -> g3_status {
+    if ((((uintptr_t)op | (uintptr_t)ol) & 15) == 0) {
+      bfs_translate4<<<cap_grid((g->n + 3) / 4, 256, ws->grid_tr4), 256, 0, s>>>(
+          g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op,
+          ol);
+    } else {  // outputs not 16-byte aligned
+      bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, s>>>(
+          g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op,
+          ol);
+    }
+    G3_CHECK_LAUNCH();
+    return G3_OK;
+  };
+  bool translated = false;
   if (!host_driven) {
     if (!ws->gexec || !same_opts(ws->gopts, *o)) G3_TRY(build_graph(S));
     G3_TRY_CUDA(cudaGraphLaunch(ws->gexec, s));
+    // the output pass goes right behind the level loop, without waiting for
+    // the host to read the controller; it is repeated below in the rare case
+    // of a search deeper than one graph launch runs
+    G3_TRY(translate());
+    translated = true;
   }
   // Host-driven levels: everything in host-driven mode, and what a graph
   // launch left over (searches deeper than its level cap).
@@ -1380,6 +1406,7 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
       cudaEventElapsedTime(&stats[L - 1].ms_expand, ws->ev[1], ws->ev[2]);
     }
     if (h->mode == MODE_DONE) break;
+    translated = false;
     const int mode = h->mode;
     if (o->record_both && stats && L < max_stats)
       G3_TRY(record_trials(S, h->nf, &stats[L], s));
@@ -1394,21 +1421,7 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   const int32_t nrec = h->level;  // non-empty frontiers F_0 .. F_{nrec-1}
   if (n_levels) *n_levels = nrec;
 
-  // outputs in original IDs
-  int32_t* vp = device_view(parent);
-  int32_t* vl = device_view(level);
-  const bool dev_p = vp != nullptr, dev_l = vl != nullptr;
-  int32_t* op = dev_p ? vp : ws->out_parent;
-  int32_t* ol = dev_l ? vl : ws->out_level;
-  if ((((uintptr_t)op | (uintptr_t)ol) & 15) == 0) {
-    bfs_translate4<<<cap_grid((g->n + 3) / 4, 256, ws->grid_tr4), 256, 0, s>>>(
-        g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op, ol);
-    G3_CHECK_LAUNCH();
-  } else {  // outputs not 16-byte aligned
-    bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, s>>>(
-        g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op, ol);
-    G3_CHECK_LAUNCH();
-  }
+  if (!translated) G3_TRY(translate());
   if (!dev_p)
     G3_TRY_CUDA(cudaMemcpyAsync(parent, op, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
   if (!dev_l)
