@@ -204,25 +204,26 @@ __device__ __forceinline__ void batch_search(const BatchArgs& A, int32_t g, uint
   }
 }
 
-// Persistent kernel over all graphs: first every CTA takes graphs of the
-// CTA list (largest first) as a whole, then, once that list is drained, each
-// warp takes graphs of the warp list on its own; the tail of the big graphs
-// overlaps the small ones. counters[0] / [1] are the two lists' cursors.
-__global__ void __launch_bounds__(256) batch_bfs(BatchArgs A, const int32_t* __restrict__ order_cta,
+// Persistent kernel over all graphs, 512 threads per CTA: first every CTA
+// takes graphs of the CTA list (largest first) as a whole, then, once that
+// list is drained, each warp takes graphs of the warp list on its own; the
+// tail of the big graphs overlaps the small ones. counters[0] / [1] are the
+// two lists' cursors. (512-thread CTAs halve each big graph's per-thread
+// chains against 256 at the same occupancy.)
+__global__ void __launch_bounds__(512) batch_bfs(BatchArgs A, const int32_t* __restrict__ order_cta,
                                                  int32_t n_cta,
                                                  const int32_t* __restrict__ order_warp,
                                                  int32_t n_warp, unsigned* counters) {
-  static_assert(3 * BT_CTA_WORDS == 8 * 3 * BT_WARP_WORDS, "shared layouts must coincide");
-  __shared__ uint32_t bm[3 * BT_CTA_WORDS];
-  __shared__ unsigned long long s_cnt[8][2];
-  __shared__ int s_gi[8];
+  __shared__ uint32_t bm[16 * 3 * BT_WARP_WORDS];
+  __shared__ unsigned long long s_cnt[16][2];
+  __shared__ int s_gi[16];
   for (;;) {
     if (threadIdx.x == 0) s_gi[0] = (int)atomicAdd(&counters[0], 1u);
     __syncthreads();
     const int gi = s_gi[0];
     __syncthreads();
     if (gi >= n_cta) break;
-    batch_search<256, BT_CTA_WORDS>(A, order_cta[gi], bm, s_cnt[0], threadIdx.x);
+    batch_search<512, BT_CTA_WORDS>(A, order_cta[gi], bm, s_cnt[0], threadIdx.x);
     __syncthreads();
   }
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -429,9 +430,9 @@ static g3_status batch_capture(g3_batch* b, const int32_t* roots, int32_t* paren
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_bfs, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_bfs, 512, 0);
   const int grid =
-      std::max(1, std::min(sms * std::max(per, 1), std::max(b->n_cta, (b->n_warp + 7) / 8)));
+      std::max(1, std::min(sms * std::max(per, 1), std::max(b->n_cta, (b->n_warp + 15) / 16)));
   BatchArgs A{b->N, b->off, b->col, b->orig_of, b->label_of, b->voff, b->np, roots, parent, level};
   cudaStream_t cs;
   G3_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -439,7 +440,7 @@ static g3_status batch_capture(g3_batch* b, const int32_t* roots, int32_t* paren
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(b->counters, 0, 16, cs);
-    batch_bfs<<<grid, 256, 0, cs>>>(A, b->order_cta, b->n_cta, b->order_warp, b->n_warp,
+    batch_bfs<<<grid, 512, 0, cs>>>(A, b->order_cta, b->n_cta, b->order_warp, b->n_warp,
                                     b->counters);
   e = cudaStreamEndCapture(cs, &graph);
   }
