@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "harmonic-mean GTEPS over 64 roots, Kronecker SCALE 26; learned vs plain BFS"
 L2_BYTES = 129 * 1024 * 1024
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0  # HBM3e nominal, for context beside the measured peak
 
 
 def parse_args():
@@ -570,6 +571,7 @@ def gpu_arm(args, rank, world):
                          "kernel": "bu_pull" if dom == 1 else "td_front+td_bins",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "traffic_source": traffic_src,
                          "peak_kind": peak_kind, "launches": launches_dom,
                          "avg_launch_ms": tms / max(launches_dom, 1),
@@ -827,6 +829,7 @@ def msbfs_arm(args, rank, world):
             "roofline": {"bound": "hbm", "kernel": "g3_msbfs launch (all its kernels)",
                          "achieved": comp / (avg_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": comp / (avg_ms / 1e3) / 1e9 / peak, "traffic": None,
+                         "frac_of_nominal": comp / (avg_ms / 1e3) / 1e9 / NOMINAL_HBM_GBS,
                          "peak_kind": peak_kind, "bytes_per_launch": comp,
                          "bytes_model": "per launch from g3_msbfs_last_stats: 8 B x nb per "
                                         "pull level, 24 B per scanned vertex, 12 B per read "
@@ -997,6 +1000,7 @@ def batch_arm(args, rank, world):
             "roofline": {"bound": "hbm", "kernel": "batch_bfs (warp- and CTA-group launches)",
                          "achieved": comp / (avg_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": comp / (avg_ms / 1e3) / 1e9 / peak, "traffic": None,
+                         "frac_of_nominal": comp / (avg_ms / 1e3) / 1e9 / NOMINAL_HBM_GBS,
                          "peak_kind": peak_kind, "bytes_per_launch": comp,
                          "bytes_model": "compulsory: union CSR once + parent/level written + "
                                         "label map read once"},
