@@ -9,7 +9,8 @@ generators (``graphgen``).
 The arithmetic lives in ``oracle.c`` (serial C, compiled with plain gcc) and in
 the pure-Python/numpy modules next to it:
 
-* ``oracle.c``       CSR (Sec. 3.1, Eq. 2), RCM (Algorithm 3), relabelled CSR,
+* ``oracle.c``       CSR (Sec. 3.1, Eq. 2), RCM (Algorithm 3), partial RCM
+                     (Sec. 4.6), relabelled CSR,
                      serial BFS (Algorithm 1), validator, bandwidth (Eq. 1),
                      bottom-up edges examined (Algorithm 2).
 * ``direction.py``   the per-level top-down / bottom-up switching rule.
