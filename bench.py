@@ -13,11 +13,17 @@ time of the g3_bfs call (CUDA events on the launching stream). Preprocessing
 (CSR build, RCM) is timed once and reported beside the metric, as the paper
 reports RCM time separately (Table 5).
 
+Parity: every root's level[] of the last timed step is compared with the CPU
+oracle's, every parent[] is checked by the BFS-tree rules and the RCM
+permutation is certified as Algorithm 3's output, on the host cores after the
+timed region; the oracle's search times of that pass are the CPU baseline.
+
 Arms:
   --impl gb300 (default)  the CUDA library through its C ABI
   --impl reference        the CPU oracle (serial C) on the host cores, one root
-                          per step -- the paper's method has no runnable
-                          reference implementation
+                          per step, the steps run concurrently one per core --
+                          the paper's method has no runnable reference
+                          implementation
 Multi-GPU: a single-root BFS does not shard; N ranks run N independent
 replicas (weak scaling) and the value is the whole-job rate.
 """
@@ -59,8 +65,10 @@ def parse_args():
                     default="auto", help="auto: learned when trained parameters exist")
     ap.add_argument("--mlp", default=os.path.join(ROOT, "paper_2012_10026_gb300",
                                                   "mlp_params.json"))
-    ap.add_argument("--cpu-baseline", type=int, default=1, help="run the oracle leg (rank 0)")
-    ap.add_argument("--cpu-roots", type=int, default=1, help="roots in the oracle sample")
+    ap.add_argument("--cpu-baseline", type=int, default=1,
+                    help="run the oracle leg (rank 0): kron: every root's levels, parents "
+                         "and the permutation checked with the oracle, whose search times "
+                         "are the CPU baseline")
     ap.add_argument("--cpu-timeout", type=float, default=600.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--bu-reverse", type=int, default=1,
@@ -218,41 +226,157 @@ def harmonic_gteps(m, t_ms):
 
 
 # --------------------------------------------------------- CPU oracle leg
-def _oracle_worker(scale, ef, seed, root_seed, nroots, k, q):
-    """Spawned process: host generation, oracle CSR, oracle BFS on k roots."""
+def host_cores():
     try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def host_mem_available():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 16 << 30
+
+
+def oracle_threads(n, want):
+    """Concurrent oracle searches the host can take: at most `want`, one per
+    core but one kept for the launching thread, and about 5 arrays of n int32
+    (the GPU's outputs, the oracle's outputs, its queue) each in memory."""
+    per = 5 * 4 * n + (64 << 20)
+    by_mem = max(1, (host_mem_available() - (24 << 30)) // per)
+    return int(max(1, min(want, host_cores() - 1, by_mem)))
+
+
+class ParityLeg:
+    """Checks the GPU's results on the same graph with the CPU oracle, on
+    host threads (the oracle's C entry points run without the GIL):
+
+    * from the start, in the background: the host twin of the generator and
+      the oracle's CSR (untimed);
+    * per root, after the timed region: the oracle BFS, its level[] compared
+      with the GPU's element by element, and the GPU's parent[] checked by the
+      BFS-tree rules (rule 5 of the validator, the edge rule, follows from the
+      level equality); the oracle BFS times of this pass are the CPU
+      baseline (roots run concurrently, one per host core);
+    * the GPU's RCM permutation certified as Algorithm 3's output
+      (orc_rcm_check: the conditions that make it unique), since Algorithm 3
+      itself, with a sort of every row, takes many minutes at 2^26 vertices.
+    """
+
+    def __init__(self, scale, edgefactor, seed, root_seed, nroots):
+        import threading
+        self.scale, self.n = scale, 1 << scale
+        self.args = (scale, edgefactor, seed, root_seed, nroots)
+        self.err = None
+        self.gen_done = threading.Event()
+        self.csr_done = threading.Event()
+        self.th = threading.Thread(target=self._prepare, daemon=True)
+        self.th.start()
+
+    def _prepare(self):
+        try:
+            import graphgen
+            import oracle
+            scale, ef, seed, root_seed, nroots = self.args
+            t0 = time.time()
+            src, dst = graphgen.kronecker_edges(scale, ef, seed=seed)
+            self.roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, self.n),
+                                             nroots, root_seed).tolist()
+            self.gen_s = time.time() - t0
+            self.gen_done.set()
+            t1 = time.time()
+            self.off, self.col = oracle.build_csr(src, dst, self.n)
+            self.csr_s = time.time() - t1
+        except Exception as e:  # reported in the line, never fatal for the GPU arm
+            self.err = repr(e)
+        finally:
+            self.gen_done.set()
+            self.csr_done.set()
+
+    def wait_generation(self, timeout=600.0):
+        """The host generator runs on every core (OpenMP): timed GPU work
+        waits until it is done."""
+        self.gen_done.wait(timeout)
+
+    def check(self, roots, m_r, fetch, perm, timeout=3600.0):
+        """fetch(i) -> (parent, level) numpy int32 [n] of roots[i] in original
+        IDs; perm: the GPU's old_of_new (None: no RCM). Returns the parity
+        and cpu_baseline records."""
+        from concurrent.futures import ThreadPoolExecutor
+        import threading
         import numpy as np
-        import graphgen
         import oracle
-        n = 1 << scale
-        t0 = time.time()
-        src, dst = graphgen.kronecker_edges(scale, ef, seed=seed)
-        roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), nroots, root_seed)
-        t1 = time.time()
-        off, col = oracle.build_csr(src, dst, n)
-        t2 = time.time()
-        res = []
-        for r in roots[:k].tolist():
+        self.csr_done.wait(timeout)
+        if self.err or not hasattr(self, "off"):
+            return {"error": self.err or "oracle CSR not ready"}, None
+        if list(roots) != list(self.roots):
+            return {"error": "root draw differs between the host and device generators"}, None
+        T = oracle_threads(self.n, 64)
+        gate = threading.Semaphore(T)
+        off, col = self.off, self.col
+
+        def one(i, r, par, lev):
+            try:
+                s = time.perf_counter()
+                _, lo = oracle.bfs(off, col, r)
+                dt = time.perf_counter() - s
+                exact = bool(np.array_equal(lo, lev))
+                del lo
+                v = oracle.validate_tree(off, col, r, par, lev) if exact else (-1, -1)
+                return r, exact, v == 0, dt, None if v == 0 else v
+            finally:
+                gate.release()
+
+        def rcm_cert():
             s = time.perf_counter()
-            _, level = oracle.bfs(off, col, r)
-            dt = time.perf_counter() - s
-            m_r = int(np.count_nonzero(level[src] >= 0))
-            res.append((r, m_r, dt))
-        q.put({"ok": True, "gen_s": t1 - t0, "csr_s": t2 - t1, "runs": res})
-    except Exception as e:  # reported, never fatal for the GPU arm
-        q.put({"ok": False, "error": repr(e)})
+            res = oracle.rcm_check(off, col, perm)
+            return res, time.perf_counter() - s
 
-
-def start_oracle_leg(args, k):
-    ctx = mp.get_context("spawn")
-    q = ctx.Queue()
-    p = ctx.Process(target=_oracle_worker, args=(args.scale, args.edgefactor, args.seed,
-                                                  args.root_seed, args.roots, k, q), daemon=True)
-    p.start()
-    return p, q
+        w0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=T + 1) as ex:
+            fr = ex.submit(rcm_cert) if perm is not None else None
+            futs = []
+            for i, r in enumerate(roots):
+                gate.acquire()
+                par, lev = fetch(i)
+                futs.append(ex.submit(one, i, r, par, lev))
+                del par, lev
+            res = [f.result() for f in futs]
+            cert = fr.result() if fr is not None else None
+        wall = time.perf_counter() - w0
+        bad = [{"root": r, "level_exact": e, "rule": v} for r, e, ok, _, v in res if not ok]
+        parity = {"roots_checked": len(res), "level_exact": sum(1 for x in res if x[1]),
+                  "parent_valid": sum(1 for x in res if x[2]),
+                  "perm_exact": None if cert is None else cert[0] == 0,
+                  "perm_check": None if cert is None else
+                  ("orc_rcm_check: the permutation meets the conditions that make "
+                   "Algorithm 3's output unique" if cert[0] == 0 else f"failed {cert[0]}"),
+                  "perm_check_s": None if cert is None else cert[1],
+                  "failures": bad[:8],
+                  "oracle": f"host twin of the generator {self.gen_s:.1f} s, oracle CSR "
+                            f"{self.csr_s:.1f} s, {len(res)} oracle BFS + tree checks on "
+                            f"{T} threads {wall:.1f} s"}
+        ms = [m_r[r] for r in roots]
+        ts = [x[3] * 1e3 for x in res]
+        cpu = {"value": harmonic_gteps(ms, ts), "unit": "GTEPS", "cores": T, "kind": "oracle",
+               "sample": f"all {len(res)} roots of the workload, serial oracle BFS (one root "
+                         f"per thread, {T} at a time on {host_cores()} host cores) on the "
+                         f"oracle's own CSR of the same graph; per-root times while the "
+                         f"other threads run",
+               "aggregate_gteps": sum(ms) / wall / 1e9,
+               "per_root_s": {"min": min(x[3] for x in res),
+                              "median": statistics.median(x[3] for x in res),
+                              "max": max(x[3] for x in res)}}
+        return parity, cpu
 
 
 def finish_oracle_leg(p, q, timeout):
+    """Result of a spawned oracle process (None when it did not answer)."""
     try:
         d = q.get(timeout=timeout)
     except Exception:
@@ -264,9 +388,12 @@ def finish_oracle_leg(p, q, timeout):
 
 # ------------------------------------------------------------ reference arm
 def reference_arm(args, rank, world):
-    """CPU oracle timed on the host cores, one root per step."""
+    """The CPU oracle timed on the host cores: one root per step, the steps
+    run concurrently (one root per thread, one thread per core); each root's
+    time is its own search's."""
     if rank != 0:
         return
+    from concurrent.futures import ThreadPoolExecutor
     import numpy as np
     import graphgen
     import oracle
@@ -276,16 +403,26 @@ def reference_arm(args, rank, world):
     roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), args.roots,
                                 args.root_seed)
     off, col = oracle.build_csr(src, dst, n)
+    # generated tuples per first endpoint: m_r = sum over the reached vertices
+    tuples_from = np.bincount(src, minlength=n)
+    del src, dst
     setup_s = time.time() - t0
-    ms, tms = [], []
-    for i in range(args.warmup + args.steps):
+    nsteps = args.warmup + args.steps
+    T = oracle_threads(n, nsteps)
+
+    def step(i):
         r = int(roots[i % len(roots)])
         s = time.perf_counter()
         _, level = oracle.bfs(off, col, r)
         dt = time.perf_counter() - s
-        if i >= args.warmup:
-            ms.append(int(np.count_nonzero(level[src] >= 0)))
-            tms.append(dt * 1e3)
+        return int(tuples_from[level >= 0].sum()), dt * 1e3
+
+    w0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=T) as ex:
+        res = list(ex.map(step, range(nsteps)))
+    wall = time.perf_counter() - w0
+    ms = [m for m, _ in res[args.warmup:]]
+    tms = [t for _, t in res[args.warmup:]]
     v = harmonic_gteps(ms, tms)
     line = {
         "impl": "reference", "metric": METRIC,
@@ -293,9 +430,12 @@ def reference_arm(args, rank, world):
         "warmup": args.warmup, "ms_per_step": sum(tms) / len(tms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": workload_config(args),
-        "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": T, "kind": "oracle",
                          "sample": f"one root per step (roots in draw order), serial oracle "
-                                   f"BFS on the oracle's CSR; setup {setup_s:.1f} s untimed"},
+                                   f"BFS on the oracle's CSR, the {nsteps} steps run "
+                                   f"concurrently on {T} threads ({host_cores()} host cores; "
+                                   f"each time is its own search's); setup {setup_s:.1f} s "
+                                   f"untimed, searches {wall:.1f} s wall"},
         "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -309,8 +449,6 @@ def workload_config(args):
             "scale": args.scale, "edgefactor": args.edgefactor, "roots": args.roots,
             "initiator": [0.57, 0.19, 0.19, 0.05], "gen_seed": args.seed,
             "root_seed": args.root_seed,
-            "controller": getattr(args, "controller_used", args.controller),
-            "bu_reverse": args.bu_reverse,
             "l2": "256 MB write between roots (L2 flush); CSR larger than L2",
             "parallelism": "replicas"}
 
@@ -329,9 +467,9 @@ def gpu_arm(args, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    oracle_proc = None
+    parity = None
     if rank == 0 and args.cpu_baseline:
-        oracle_proc = start_oracle_leg(args, args.cpu_roots)
+        parity = ParityLeg(args.scale, args.edgefactor, args.seed, args.root_seed, args.roots)
 
     L = g3.lib()
     n = 1 << args.scale
@@ -379,6 +517,10 @@ def gpu_arm(args, rank, world):
         lo, mlp_t, learned_note = controller_opts(args.mlp, info["n_bfs"], **base)
         kw.update(controller=lo.controller, mlp_params=mlp_t, mlp_margin=lo.mlp_margin,
                   mlp_bins=lo.mlp_bins)
+    decided = {g3.G3_CTRL_HEURISTIC: "alpha/beta rule", g3.G3_CTRL_LEARNED: "learned MLP",
+               g3.G3_CTRL_TOPDOWN: "top-down only", g3.G3_CTRL_BOTTOMUP: "bottom-up only"}
+    controller_rec = {"requested": args.controller, "decided_by": decided[kw["controller"]],
+                      "note": learned_note}
     if args.host_loop:  # profiling: every level's kernels as separate stream launches
         kw["timing"] = 1
     opts = g3.opts(**kw)  # default path: the level loop runs as one CUDA graph
@@ -401,12 +543,20 @@ def gpu_arm(args, rank, world):
     ev_s = torch.cuda.Event(enable_timing=True)
     ev_e = torch.cuda.Event(enable_timing=True)
 
-    def one_step(o, nstats):
+    # the timed searches write root i's outputs to slot i, so that every
+    # root's result of the last timed step can be checked with the oracle
+    slots = None
+    if parity is not None:
+        slots = (torch.empty((len(roots), n), dtype=torch.int32, device="cuda"),
+                 torch.empty((len(roots), n), dtype=torch.int32, device="cuda"))
+
+    def one_step(o, nstats, keep=False):
         times, stats = [], []
-        for r in roots:
+        for i, r in enumerate(roots):
+            p_out, l_out = (slots[0][i], slots[1][i]) if keep else (parent, level)
             flush.fill_(1)
             ev_s.record()
-            st = g3.g3_bfs(g, r, parent, level, o, max_stats=nstats)
+            st = g3.g3_bfs(g, r, p_out, l_out, o, max_stats=nstats)
             ev_e.record()
             ev_e.synchronize()
             times.append(ev_s.elapsed_time(ev_e))
@@ -415,6 +565,8 @@ def gpu_arm(args, rank, world):
 
     for _ in range(args.warmup):
         one_step(opts, 0)
+    if parity is not None:  # the host generator runs on every core
+        parity.wait_generation()
     clk_path = os.path.join(tempfile.gettempdir(), f"g3_clocks_{rank}.csv")
     sampler = start_clock_sampler(clk_path)
     if dist:
@@ -424,7 +576,7 @@ def gpu_arm(args, rank, world):
     w0 = time.perf_counter()
     all_t = []
     for _ in range(args.steps):
-        t, _ = one_step(opts, 0)
+        t, _ = one_step(opts, 0, keep=slots is not None)
         all_t += t
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
@@ -516,6 +668,23 @@ def gpu_arm(args, rank, world):
             prev = s["dir"]
     launches += graph_kernels * args.steps
 
+    # the oracle checks every root's result of the last timed step and the
+    # permutation, on the host cores (before the end-to-end leg, whose host
+    # wall time the busy cores would disturb)
+    parity_rec, cpu = None, None
+    if parity is not None:
+        perm = g.perm()[0].cpu().numpy() if (args.rcm and args.rcm_permille >= 1000) else None
+
+        def fetch(i):
+            return slots[0][i].cpu().numpy(), slots[1][i].cpu().numpy()
+
+        parity_rec, cpu = parity.check(roots, m_r, fetch, perm)
+        del slots
+        torch.cuda.empty_cache()
+        if cpu is None:
+            cpu = {"value": None, "unit": "GTEPS", "cores": 0, "kind": "oracle",
+                   "sample": "oracle leg did not finish: " + str(parity_rec.get("error"))}
+
     # end to end through the C ABI with pinned host outputs
     e2e = None
     if not args.no_e2e:
@@ -534,23 +703,12 @@ def gpu_arm(args, rank, world):
                     et.append(dt * 1e3)
         e2e = {"value": harmonic_gteps(ms, et), "unit": "GTEPS", "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": len(roots) * 2 * n * 4,
-               "note": "root passed by value; parent[] and level[] copied to pinned host memory"}
+               "note": "the graph stays resident on the device (built and relabelled once, "
+                       "as the paper times the search apart from preprocessing), so a "
+                       "search's only input is the root, passed by value: h2d is 0 by "
+                       "design; parent[] and level[] of every root are written to pinned "
+                       "host memory inside the host-timed region"}
 
-    cpu = None
-    if oracle_proc is not None:
-        d = finish_oracle_leg(*oracle_proc, timeout=args.cpu_timeout)
-        if d and d.get("ok"):
-            runs = d["runs"]
-            cpu = {"value": harmonic_gteps([x[1] for x in runs], [x[2] * 1e3 for x in runs]),
-                   "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                   "sample": f"{len(runs)} of the {len(roots)} roots ({[x[0] for x in runs]}), "
-                             f"serial oracle BFS on the oracle's own CSR of the same graph "
-                             f"(host generation {d['gen_s']:.1f} s and oracle CSR "
-                             f"{d['csr_s']:.1f} s untimed)",
-                   "seconds": [x[2] for x in runs]}
-        else:
-            cpu = {"value": None, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                   "sample": "oracle leg did not finish: " + (d or {}).get("error", "timeout")}
 
     # the trained controller against the rule on a graph of a size it was
     # trained on (the headline graph is outside them, see learned_controller)
@@ -579,6 +737,8 @@ def gpu_arm(args, rank, world):
                          "timed_in": "instrumented step after the timed region: the same "
                                      "kernels launched level by level, CUDA events on the "
                                      "launching stream around each level's expansion"},
+            "parity": parity_rec,
+            "controller": controller_rec,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "graph_launches": graph_launches,
             "instrumented_hm_gteps": harmonic_gteps([m_r[r] for r in roots], inst_t),

@@ -9,8 +9,9 @@ generators (``graphgen``).
 The arithmetic lives in ``oracle.c`` (serial C, compiled with plain gcc) and in
 the pure-Python/numpy modules next to it:
 
-* ``oracle.c``       CSR (Sec. 3.1, Eq. 2), RCM (Algorithm 3), partial RCM
-                     (Sec. 4.6), relabelled CSR,
+* ``oracle.c``       CSR (Sec. 3.1, Eq. 2), RCM (Algorithm 3) and a
+                     certificate check of it, partial RCM (Sec. 4.6),
+                     relabelled CSR,
                      serial BFS (Algorithm 1), validator, bandwidth (Eq. 1),
                      bottom-up edges examined (Algorithm 2).
 * ``direction.py``   the per-level top-down / bottom-up switching rule.
@@ -56,6 +57,8 @@ def lib():
         L.orc_rcm.restype = ctypes.c_int32
         L.orc_rcm_partial.argtypes = [_i64p, _i32p, ctypes.c_int32, ctypes.c_int32, _i32p]
         L.orc_rcm_partial.restype = ctypes.c_int32
+        L.orc_rcm_check.argtypes = [_i64p, _i32p, ctypes.c_int32, _i32p, _i64p]
+        L.orc_rcm_check.restype = ctypes.c_int32
         L.orc_permute_csr.argtypes = [_i64p, _i32p, ctypes.c_int32, _i32p, ctypes.c_int32,
                                       _i64p, _i32p]
         L.orc_permute_csr.restype = None
@@ -64,6 +67,8 @@ def lib():
         L.orc_validate.argtypes = [_i64p, _i32p, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
                                    _i64p]
         L.orc_validate.restype = ctypes.c_int32
+        L.orc_validate_tree.argtypes = L.orc_validate.argtypes
+        L.orc_validate_tree.restype = ctypes.c_int32
         L.orc_bandwidth.argtypes = [_i64p, _i32p, ctypes.c_int32, _i32p]
         L.orc_bandwidth.restype = ctypes.c_int64
         L.orc_bu_examined.argtypes = [_i64p, _i32p, ctypes.c_int32, _i32p, ctypes.c_int32,
@@ -110,6 +115,19 @@ def rcm_partial(off, col, p_permille: int):
     return P[:n].copy(), int(n_plus)
 
 
+def rcm_check(off, col, P):
+    """0 when P is Algorithm 3's permutation of the graph, checked through
+    the conditions that make it unique (no re-run of Algorithm 3), else
+    (rule number, offending Cuthill-McKee position); see oracle.c."""
+    off, col, P = _c64(off), _c32(col), _c32(P)
+    n = len(off) - 1
+    if len(P) != n:
+        return (1, -1)
+    bad = np.zeros(1, np.int64)
+    r = lib().orc_rcm_check(_p64(off), _p32(col), n, _p32(P), _p64(bad))
+    return 0 if r == 0 else (int(r), int(bad[0]))
+
+
 def permutation_arrays(P):
     """(old_of_new, new_of_old) from the RCM permutation P."""
     P = _c32(P)
@@ -147,6 +165,17 @@ def validate(off, col, root: int, parent, level):
     bad = np.zeros(1, np.int64)
     r = lib().orc_validate(_p64(off), _p32(col), n, int(root), _p32(parent), _p32(level),
                            _p64(bad))
+    return 0 if r == 0 else (int(r), int(bad[0]))
+
+
+def validate_tree(off, col, root: int, parent, level):
+    """Rules 1-4 of validate() (no pass over every edge): for a level[]
+    already found equal to bfs()'s, where rule 5 holds by itself."""
+    off, col, parent, level = _c64(off), _c32(col), _c32(parent), _c32(level)
+    n = len(off) - 1
+    bad = np.zeros(1, np.int64)
+    r = lib().orc_validate_tree(_p64(off), _p32(col), n, int(root), _p32(parent),
+                                _p32(level), _p64(bad))
     return 0 if r == 0 else (int(r), int(bad[0]))
 
 

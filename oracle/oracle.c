@@ -20,12 +20,17 @@
  *                     reverse, append V \ V+.
  *   orc_rcm_partial   partial RCM (Sec. 4.6): Algorithm 3 on the top p of
  *                     V+ only, the rest in ID order (reading in its comment).
+ *   orc_rcm_check     certificate check that a permutation is Algorithm 3's
+ *                     output (the conditions that make it unique), for sizes
+ *                     where running Algorithm 3 itself takes too long.
  *   orc_permute_csr   the relabelled CSR the BFS runs on (isolated vertices
  *                     dropped, Sec. 1 contribution 1; rows ascending).
  *   orc_bfs           Algorithm 1 run serially: FIFO frontier, neighbours in
  *                     CSR order, the first discoverer becomes the predecessor;
  *                     pi(s)=s, -1 when unreachable (Sec. 2.1).
- *   orc_validate      the predecessor-map rules implied by Sec. 2.1.
+ *   orc_validate      the predecessor-map rules implied by Sec. 2.1;
+ *                     orc_validate_tree the same rules but the edge pass,
+ *                     for levels already compared with orc_bfs.
  *   orc_bandwidth     Eq. 1.
  *   orc_bu_examined   edges a bottom-up step examines (Algorithm 2, bottom-up
  *                     branch): per unvisited vertex, neighbours in CSR order up
@@ -233,6 +238,91 @@ int32_t orc_rcm_partial(const int64_t* off, const int32_t* col, int32_t n,
   return np;
 }
 
+/* Certificate check of an RCM permutation against Algorithm 3, without
+ * running Algorithm 3 (whose per-row sorts take many minutes at 2^26
+ * vertices). P maps position -> original ID as orc_rcm returns it. Let Q be
+ * the Cuthill-McKee order (P[0 .. n_plus) read backwards), pos[v] the
+ * position of v in Q, and mp(w) / mx(w) the smallest / largest position of a
+ * neighbour of w. Algorithm 3 appends a vertex either as the start of a new
+ * component (its queue being empty) or while dequeuing its earliest-placed
+ * neighbour, the unvisited neighbours of each dequeued vertex in increasing
+ * (degree, ID). Its Q is therefore the one order of V+ with
+ *   1. P a permutation of [0, n); P[0 .. n_plus) = V+ (degree > 0) and
+ *      P[n_plus .. n) = V \ V+ in ascending ID;
+ *   2. a vertex with mp(w) > pos(w) (a start) comes when every vertex before
+ *      it has all its neighbours before it (the queue is empty), and it is
+ *      the minimal (degree, ID) vertex among Q[pos(w) ..];
+ *   3. the other vertices (mp(w) < pos(w)) appear in strictly increasing
+ *      (mp(w), degree(w), ID(w)).
+ * Uniqueness: if Q' satisfies 1-3 and first differs from Algorithm 3's Q at
+ * position j, then either Q[j] is a start, whose queue-empty state and
+ * minimality rule 2 gives to Q'[j] as well, or Q[j] has a neighbour in the
+ * common prefix, so Q'[j] cannot be a start (rule 2) and rule 3 orders Q[j]
+ * before Q'[j] by the same key in both orders -- a contradiction either way.
+ * Returns 0 when P passes, else the rule number with the offending position
+ * in *bad. */
+int32_t orc_rcm_check(const int64_t* off, const int32_t* col, int32_t n,
+                      const int32_t* P, int64_t* bad) {
+  *bad = -1;
+  int32_t np = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (off[v + 1] > off[v]) np++;
+  int32_t* pos = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t));
+  uint8_t* start = (uint8_t*)calloc((size_t)n + 1, 1);
+  for (int32_t v = 0; v < n; ++v) pos[v] = -1;
+  int32_t rc = 0;
+  /* rule 1 */
+  for (int32_t i = 0; i < n && !rc; ++i) {
+    int32_t v = P[i];
+    if (v < 0 || v >= n || pos[v] >= 0) { rc = 1; *bad = i; break; }
+    int64_t d = off[v + 1] - off[v];
+    if ((i < np) != (d > 0)) { rc = 1; *bad = i; break; }
+    if (i > np && P[i] < P[i - 1]) { rc = 1; *bad = i; break; }
+    pos[v] = i < np ? np - 1 - i : i; /* Cuthill-McKee position */
+  }
+  /* forward pass: rules 2 (queue empty) and 3 */
+  int64_t prefmax = -1;
+  int64_t k_mp = -1, k_deg = -1, k_id = -1; /* key of the last non-start */
+  for (int32_t j = 0; j < np && !rc; ++j) {
+    int32_t w = P[np - 1 - j];
+    int64_t mp = INT64_MAX, mx = -1;
+    for (int64_t e = off[w]; e < off[w + 1]; ++e) {
+      int64_t q = pos[col[e]];
+      if (q < mp) mp = q;
+      if (q > mx) mx = q;
+    }
+    int64_t d = off[w + 1] - off[w];
+    if (mp > j) { /* a start: no vertex before it has a neighbour after it */
+      start[j] = 1;
+      if (prefmax >= j) { rc = 2; *bad = j; break; }
+    } else {
+      if (mp < k_mp || (mp == k_mp && (d < k_deg || (d == k_deg && w <= k_id)))) {
+        rc = 3;
+        *bad = j;
+        break;
+      }
+      k_mp = mp;
+      k_deg = d;
+      k_id = w;
+    }
+    if (mx > prefmax) prefmax = mx;
+  }
+  /* backward pass: rule 2 (a start is the minimal (degree, ID) remaining) */
+  int64_t b_deg = INT64_MAX, b_id = INT64_MAX;
+  for (int32_t j = np - 1; j >= 0 && !rc; --j) {
+    int32_t w = P[np - 1 - j];
+    int64_t d = off[w + 1] - off[w];
+    if (d < b_deg || (d == b_deg && w < b_id)) {
+      b_deg = d;
+      b_id = w;
+    }
+    if (start[j] && b_id != w) { rc = 2; *bad = j; }
+  }
+  free(pos);
+  free(start);
+  return rc;
+}
+
 /* Relabelled CSR over the n_plus non-isolated vertices: row i holds the new
  * labels of the neighbours of original vertex P[i], ascending.
  * off_new: n_plus+1 entries; col_new: nnz entries. */
@@ -302,9 +392,9 @@ static int has_edge(const int64_t* off, const int32_t* col, int32_t u, int32_t v
  *   5  every edge joins two unreached vertices or two reached vertices whose
  *      levels differ by at most one
  * Rules 2 and 5 together force level[] to equal the hop distance. */
-int32_t orc_validate(const int64_t* off, const int32_t* col, int32_t n,
-                     int32_t root, const int32_t* parent, const int32_t* level,
-                     int64_t* bad) {
+static int32_t validate_tree_rules(const int64_t* off, const int32_t* col, int32_t n,
+                                   int32_t root, const int32_t* parent,
+                                   const int32_t* level, int64_t* bad) {
   *bad = -1;
   if (root < 0 || root >= n || parent[root] != root || level[root] != 0) {
     *bad = root;
@@ -323,6 +413,14 @@ int32_t orc_validate(const int64_t* off, const int32_t* col, int32_t n,
       return 2;
     }
   }
+  return 0;
+}
+
+int32_t orc_validate(const int64_t* off, const int32_t* col, int32_t n,
+                     int32_t root, const int32_t* parent, const int32_t* level,
+                     int64_t* bad) {
+  int32_t r = validate_tree_rules(off, col, n, root, parent, level, bad);
+  if (r) return r;
   for (int32_t u = 0; u < n; ++u) {
     for (int64_t j = off[u]; j < off[u + 1]; ++j) {
       int32_t w = col[j];
@@ -332,6 +430,16 @@ int32_t orc_validate(const int64_t* off, const int32_t* col, int32_t n,
     }
   }
   return 0;
+}
+
+/* Rules 1-4 of orc_validate only, for a level[] already known to equal the
+ * hop distances (compared with orc_bfs), where rule 5 holds by itself: the
+ * parents then form a BFS tree exactly when rules 1-4 hold. Skips the pass
+ * over every edge, which dominates orc_validate on large graphs. */
+int32_t orc_validate_tree(const int64_t* off, const int32_t* col, int32_t n,
+                          int32_t root, const int32_t* parent, const int32_t* level,
+                          int64_t* bad) {
+  return validate_tree_rules(off, col, n, root, parent, level, bad);
 }
 
 /* Eq. 1: BW(A) = max{ i - j : A_ij != 0, i > j } under the labelling

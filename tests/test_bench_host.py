@@ -1,8 +1,11 @@
-"""bench.py's host-side arithmetic (no GPU): the TEPS mean, the per-level
-algorithmic-bytes model and the traffic record of the committed capture."""
+"""bench.py's host-side logic (no GPU): the TEPS mean, the per-level
+algorithmic-bytes model, the traffic record of the committed capture and the
+oracle parity pass (with the oracle's own results in the GPU's place, and
+planted errors)."""
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -32,3 +35,53 @@ def test_committed_traffic_record_parses():
     traffic, src = bench.measured_traffic("bu_pull")
     assert (traffic is not None and traffic > 0) or src == "kernel source changed since the capture"
     assert bench.measured_traffic("no_such_kernel")[0] is None
+
+
+def _parity_case(scale, nroots):
+    import graphgen
+    import oracle
+    n = 1 << scale
+    src, dst = graphgen.kronecker_edges(scale, 16, seed=1)
+    roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), nroots, 2).tolist()
+    off, col = oracle.build_csr(src, dst, n)
+    P, _ = oracle.rcm(off, col)
+    outs = [oracle.bfs(off, col, r) for r in roots]
+    m_r = {r: int((lv[src] >= 0).sum()) for r, (_, lv) in zip(roots, outs)}
+    return roots, outs, P, m_r
+
+
+def test_parity_leg_accepts_oracle_results_and_flags_planted_errors():
+    """The bench's oracle pass on the CPU, with the oracle's own results in
+    the GPU's place: all roots pass; a planted level error, a planted parent
+    error and a swapped permutation entry are each reported."""
+    roots, outs, P, m_r = _parity_case(12, 6)
+    leg = bench.ParityLeg(12, 16, 1, 2, 6)
+    rec, cpu = leg.check(roots, m_r, lambda i: outs[i], P)
+    assert rec["roots_checked"] == 6 and rec["level_exact"] == 6
+    assert rec["parent_valid"] == 6 and rec["perm_exact"] is True
+    assert cpu["value"] > 0 and cpu["cores"] >= 1 and cpu["kind"] == "oracle"
+
+    bad = [(p.copy(), lv.copy()) for p, lv in outs]
+    v = int(np.flatnonzero(bad[1][1] > 1)[0])
+    bad[1][1][v] += 1                      # a wrong level
+    w = int(np.flatnonzero(bad[3][1] > 1)[0])
+    bad[3][0][w] = roots[3]                # a parent that is not a neighbour one level up
+    Q = P.copy()
+    Q[[0, 1]] = Q[[1, 0]]
+    rec, _ = leg.check(roots, m_r, lambda i: bad[i], Q)
+    assert rec["level_exact"] == 5 and rec["parent_valid"] == 4
+    assert rec["perm_exact"] is False
+    assert {f["root"] for f in rec["failures"]} == {roots[1], roots[3]}
+
+
+def test_parity_leg_rejects_other_roots():
+    roots, outs, P, m_r = _parity_case(10, 3)
+    leg = bench.ParityLeg(10, 16, 1, 2, 3)
+    other = list(reversed(roots))
+    rec, cpu = leg.check(other, m_r, lambda i: outs[i], P)
+    assert "error" in rec and cpu is None
+
+
+def test_oracle_threads_bounds():
+    assert 1 <= bench.oracle_threads(1 << 26, 64) <= max(1, bench.host_cores() - 1)
+    assert bench.oracle_threads(1 << 10, 1) == 1

@@ -197,3 +197,39 @@ def test_bu_examined_closed_forms(n):
     assert oracle.bu_examined(off, col, level, 0) == n - 1
     # after the last level nothing is found: every unvisited row is scanned
     assert oracle.bu_examined(off, col, level, 1) == 0
+
+
+def test_validate_tree_equals_validate_when_levels_exact():
+    """validate_tree (rules 1-4) decides like validate whenever level[] is
+    the oracle's: on random valid BFS trees (any neighbour one level up as
+    parent) and on parent mutations of each kind."""
+    rng = np.random.default_rng(21)
+    for _ in range(40):
+        n = int(rng.integers(5, 60))
+        src, dst = random_graph(rng, n, int(rng.integers(n, 3 * n)))
+        off, col = oracle.build_csr(src, dst, n)
+        root = int(rng.integers(0, n))
+        _, level = oracle.bfs(off, col, root)
+        parent = np.full(n, -1, np.int32)
+        parent[root] = root
+        for v in range(n):
+            if level[v] > 0:
+                up = [u for u in col[off[v]:off[v + 1]] if level[u] == level[v] - 1]
+                parent[v] = up[int(rng.integers(0, len(up)))]
+        assert oracle.validate(off, col, root, parent, level) == 0
+        assert oracle.validate_tree(off, col, root, parent, level) == 0
+        reached = [v for v in range(n) if level[v] > 0]
+        for v in reached[:5]:
+            for u in range(n):
+                if u == parent[v]:
+                    continue
+                p = parent.copy()
+                p[v] = u
+                a = oracle.validate(off, col, root, p, level)
+                b = oracle.validate_tree(off, col, root, p, level)
+                assert (a == 0) == (b == 0)
+                if a:
+                    assert a == b
+    off, col, root, parent, level = _valid_instance()
+    p = parent.copy(); p[root] = int(np.flatnonzero(level > 0)[0])
+    assert oracle.validate_tree(off, col, root, p, level)[0] == 1
