@@ -71,8 +71,15 @@ def parse_args():
                          "are the CPU baseline")
     ap.add_argument("--cpu-timeout", type=float, default=600.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-bfs", type=int, default=1,
+                    help="kron, with the oracle leg: also time the paper's multithreaded "
+                         "hybrid BFS on the host cores")
     ap.add_argument("--bu-reverse", type=int, default=1,
                     help="bottom-up scans rows from the highest label (degree-aware order)")
+    ap.add_argument("--bu-kernel", type=int, default=0,
+                    help="bottom-up kernel: 0 word tiles (compact per-warp lists), 1 word pairs")
+    ap.add_argument("--out-split", type=int, default=0,
+                    help="output pass: 0 auto, 1 one pass, 2 two passes over label halves")
     ap.add_argument("--stats-out", default="")
     ap.add_argument("--workload", choices=["kron", "msbfs", "batch"], default="kron",
                     help="kron: the single-root headline; msbfs: bit-sliced multi-source "
@@ -375,6 +382,40 @@ class ParityLeg:
         return parity, cpu
 
 
+def host_hybrid_leg(g, roots, m_r, gpu_level):
+    """The paper's own multithreaded hybrid BFS (Algorithms 4-6, hostbfs/) on
+    the host cores, on the GPU's RCM-relabelled graph copied to the host:
+    every root timed (wall time of the search, outputs in original IDs) and
+    its level[] compared with the GPU's (which the oracle checked)."""
+    import numpy as np
+    import hostbfs
+    import torch
+    off, col = g.csr(device="cpu")
+    o2n, n2o = g.perm(device="cpu")
+    torch.cuda.synchronize()
+    n = g.info["n"]
+    T = max(1, host_cores() - 1)
+    hb = hostbfs.HostBFS(off.numpy(), col.numpy(), o2n.numpy(), n2o.numpy(), n, threads=T)
+    parent = np.empty(n, np.int32)
+    level = np.empty(n, np.int32)
+    hb.bfs(int(roots[0]), parent=parent, level=level)  # first touch of the workspace
+    ts, same = [], 0
+    for i, r in enumerate(roots):
+        s = time.perf_counter()
+        hb.bfs(int(r), parent=parent, level=level)
+        ts.append((time.perf_counter() - s) * 1e3)
+        same += int(np.array_equal(level, gpu_level(i)))
+    hb.close()
+    ms = [m_r[r] for r in roots]
+    return {"value": harmonic_gteps(ms, ts), "unit": "GTEPS", "cores": T,
+            "kind": "the paper's hybrid BFS on the host (Algorithms 4-6: even neighbour split, "
+                    "descending partitions with fetch_add stealing, neighbors+ first, shrinking "
+                    "partitions, 128-bit copy/OR), OpenMP",
+            "sample": f"all {len(roots)} roots, one search at a time on {T} threads, on the "
+                      f"GPU's RCM graph copied to the host",
+            "levels_equal_gpu": same, "per_root_ms_median": statistics.median(ts)}
+
+
 def finish_oracle_leg(p, q, timeout):
     """Result of a spawned oracle process (None when it did not answer)."""
     try:
@@ -500,7 +541,7 @@ def gpu_arm(args, rank, world):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     # autotuned alpha/beta, bins and scan order for this graph-size class
     # (untimed; 16 tuning roots drawn apart from the timed ones; cached)
-    base = dict(bu_reverse=args.bu_reverse)
+    base = dict(bu_reverse=args.bu_reverse, bu_kernel=args.bu_kernel, out_split=args.out_split)
     tune_rec, t_tune = None, 0.0
     if args.tune_bfs:
         t_tune = time.perf_counter()
@@ -509,7 +550,8 @@ def gpu_arm(args, rank, world):
                                           g3.opts(bu_reverse=args.bu_reverse))
         t_tune = time.perf_counter() - t_tune
         base = dict(alpha=topts.alpha, beta=topts.beta, t1=topts.t1, t2=topts.t2, t3=topts.t3,
-                    bu_reverse=topts.bu_reverse)
+                    bu_reverse=topts.bu_reverse, bu_kernel=args.bu_kernel,
+                    out_split=args.out_split)
     kw = dict(controller=ctrl, **base)
     mlp_t, learned_note = None, None
     if ctrl == g3.G3_CTRL_LEARNED:
@@ -528,7 +570,8 @@ def gpu_arm(args, rank, world):
     # the plain method: the alpha/beta rule on the same tuned options, and
     # with the library defaults
     plain_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, **base)
-    default_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, bu_reverse=args.bu_reverse)
+    default_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, bu_reverse=args.bu_reverse,
+                           bu_kernel=args.bu_kernel, out_split=args.out_split)
 
     # m_r per root (bookkeeping, outside any timed region)
     m_r = {}
@@ -671,7 +714,7 @@ def gpu_arm(args, rank, world):
     # the oracle checks every root's result of the last timed step and the
     # permutation, on the host cores (before the end-to-end leg, whose host
     # wall time the busy cores would disturb)
-    parity_rec, cpu = None, None
+    parity_rec, cpu, host_par = None, None, None
     if parity is not None:
         perm = g.perm()[0].cpu().numpy() if (args.rcm and args.rcm_permille >= 1000) else None
 
@@ -679,6 +722,8 @@ def gpu_arm(args, rank, world):
             return slots[0][i].cpu().numpy(), slots[1][i].cpu().numpy()
 
         parity_rec, cpu = parity.check(roots, m_r, fetch, perm)
+        if args.host_bfs:
+            host_par = host_hybrid_leg(g, roots, m_r, lambda i: slots[1][i].cpu().numpy())
         del slots
         torch.cuda.empty_cache()
         if cpu is None:
@@ -739,7 +784,8 @@ def gpu_arm(args, rank, world):
                                      "launching stream around each level's expansion"},
             "parity": parity_rec,
             "controller": controller_rec,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "cpu_baseline": cpu, "cpu_baseline_parallel": host_par,
+            "e2e": e2e, "gpu_launches": int(launches),
             "graph_launches": graph_launches,
             "instrumented_hm_gteps": harmonic_gteps([m_r[r] for r in roots], inst_t),
             "clocks": clocks,

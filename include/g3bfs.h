@@ -123,8 +123,10 @@ g3_status g3_get_perm(const g3_graph* g, int32_t* old_of_new, int32_t* new_of_ol
  * col nnz int32 entries. Either may be NULL. Asynchronous. */
 g3_status g3_get_csr(const g3_graph* g, int64_t* off, int32_t* col, void* stream);
 
-/* Frees the graph and every device buffer it owns (synchronises nothing;
- * the caller must not have work on the graph in flight). NULL is a no-op. */
+/* Frees the graph and every device buffer it owns. It first waits for all
+ * work on the current device (cudaDeviceSynchronize), so that the frees come
+ * after any search still reading the graph on whatever stream it was queued.
+ * NULL is a no-op. */
 void g3_graph_free(g3_graph* g);
 
 /* ---------------------------------------------------------------- BFS */
@@ -160,7 +162,17 @@ typedef struct {
                                mlp_margin / 1000 (0, the default: always) */
   int32_t mlp_bins;         /* learned controller: 1 (default) the network also
                                picks the top-down bins; 0 t1..t3 stay */
-  int32_t reserved[5];
+  int32_t out_split;        /* output pass (original IDs): 0 (default) and 1
+                               one pass; 2 two passes over label halves (each
+                               gathers from half of the packed (parent, level)
+                               array) when both outputs are device memory */
+  int32_t bu_kernel;        /* bottom-up kernel: 0 (default) word tiles -- a
+                               warp owns 32 bitmap words; dense tiles are
+                               worked lane by word, sparse ones as one compact
+                               list; four rows in flight per lane; 2 the same
+                               with two rows in flight; 1 word pairs -- a lane
+                               owns one vertex of each of two words */
+  int32_t reserved[3];
 } g3_bfs_opts;
 
 /* Fills the defaults listed above. */
@@ -409,16 +421,37 @@ g3_status g3_mlp_train(float* params, const float* x, const float* y, const floa
 g3_status g3_mlp_features(const g3_level_stats* stats, int32_t count, int32_t n_bfs, float* x,
                           void* stream);
 
+/* ------------------------------------------------------ test hooks */
+
+/* Fault injection for tests of the error paths (the paper has no
+ * counterpart). G3_INJECT_ALLOC: the value-th device allocation the library
+ * makes from now on (every stream-ordered buffer and every workspace buffer
+ * of any call) fails as if the device were out of memory, once; the call
+ * then returns G3_ENOMEM with nothing of its own left allocated and the
+ * graph as it was before the call. value <= 0 disarms it.
+ * G3_INJECT_RCM_ROUNDS: caps the rounds of component hooking in the RCM
+ * relabel (default 4096); a relabel that needs more returns G3_ETIMEOUT and
+ * leaves the graph not relabelled. value <= 0 restores the default.
+ * Process-wide; not for concurrent use. Errors: G3_EINVAL (unknown kind). */
+enum { G3_INJECT_ALLOC = 1, G3_INJECT_RCM_ROUNDS = 2 };
+g3_status g3_debug_inject(int32_t kind, int64_t value);
+
+/* Bytes currently allocated from the current device's default memory pool
+ * (the pool the stream-ordered buffers come from), for leak checks around a
+ * failed call. Errors: G3_EINVAL (null), G3_ECUDA. */
+g3_status g3_debug_pool_used(int64_t* bytes);
+
 /* ------------------------------------------------- allocation-free BFS */
 
 /* The paper has no counterpart to this entry point: it serves callers that
  * cannot allocate device memory when they search -- code running inside a
  * host framework that has already reserved the device memory for its own
  * pool, or latency-critical paths where cudaMalloc / cudaFree could
- * synchronise the device. It performs a top-down BFS (Algorithm 1) over a
- * caller-provided CSR and allocates nothing: its scratch (visited bitmap, two
- * frontier queues, counters) is one fixed-size static device array of about
- * 8.4 MB that every GPU loading the library holds until the process exits.
+ * synchronise the device. It performs a level-synchronous top-down BFS over
+ * a caller-provided CSR and allocates nothing: its scratch (visited bitmap,
+ * two frontier queues, counters) is one fixed-size static device array of
+ * 8,519,936 bytes (about 8.5 MB) that every GPU loading the library holds
+ * until the process exits.
  *   off, col      : device pointers, CSR of an undirected graph with n rows
  *                   (off: n+1 int64, col: off[n] int32 entries, as produced by
  *                   g3_get_csr), read only.
@@ -431,7 +464,9 @@ g3_status g3_mlp_features(const g3_level_stats* stats, int32_t count, int32_t n_
  * contents (each call clears what must start at zero): calls whose GPU work
  * overlaps race, so serialise them. The first call on a device looks up the
  * array's address (cudaGetSymbolAddress, that device current); make that
- * first call before any stream capture. Synchronises `stream` once per level.
+ * first call before any stream capture. The address is cached per device for
+ * the life of the process: after cudaDeviceReset on that device, do not call
+ * this entry point again. Synchronises `stream` once per level.
  * Errors: G3_EINVAL, G3_ECUDA. */
 #define G3_NOALLOC_MAX_N (1 << 20)
 g3_status g3_bfs_noalloc(const int64_t* off, const int32_t* col, int32_t n, int32_t root,

@@ -43,7 +43,8 @@ class g3_bfs_opts(ctypes.Structure):
                 ("t3", ctypes.c_int32), ("bu_reverse", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
                 ("record_both", ctypes.c_int32), ("mlp_margin", ctypes.c_int32),
-                ("mlp_bins", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("mlp_bins", ctypes.c_int32), ("out_split", ctypes.c_int32),
+                ("bu_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class g3_level_stats(ctypes.Structure):
@@ -155,8 +156,11 @@ _SIGS = {
                                     ctypes.c_float, _vp, _vp]),
     "g3_mlp_features": (ctypes.c_int, [ctypes.POINTER(g3_level_stats), ctypes.c_int32,
                                        ctypes.c_int32, _vp, _vp]),
+    "g3_debug_inject": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
+    "g3_debug_pool_used": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
 }
 NOALLOC_MAX_N = 1 << 20
+G3_INJECT_ALLOC, G3_INJECT_RCM_ROUNDS = 1, 2
 
 
 def lib():
@@ -272,6 +276,19 @@ def g3_bfs(graph: "Graph", root: int, parent, level, options: g3_bfs_opts | None
     if stats is None:
         return []
     return [stats[i].to_dict() for i in range(min(nlev.value, max_stats))]
+
+
+def g3_debug_inject(kind: int, value: int):
+    """Test hook: fail the value-th device allocation from now (G3_INJECT_ALLOC)
+    or cap the RCM hooking rounds (G3_INJECT_RCM_ROUNDS); value <= 0 resets."""
+    _check(lib().g3_debug_inject(int(kind), int(value)), "g3_debug_inject")
+
+
+def g3_debug_pool_used() -> int:
+    """Bytes in use from the current device's default memory pool."""
+    v = ctypes.c_int64()
+    _check(lib().g3_debug_pool_used(ctypes.byref(v)), "g3_debug_pool_used")
+    return int(v.value)
 
 
 def g3_bfs_noalloc(off, col, n: int, root: int, parent, level, stream=None):

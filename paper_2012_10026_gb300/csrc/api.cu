@@ -53,10 +53,16 @@ extern "C" g3_status g3_get_csr(const g3_graph* g, int64_t* off, int32_t* col, v
 
 extern "C" void g3_graph_free(g3_graph* g) {
   if (!g) return;
+  // the graph's arrays were allocated stream-ordered on the callers'
+  // streams; waiting for the device first orders the frees after any work
+  // still reading them, whatever stream it was queued on
+  cudaDeviceSynchronize();
+  cudaGetLastError();
   if (g->ws) g3_bfs_ws_free(g->ws);
   if (g->ms) g3_ms_ws_free(g->ms);
   void* all[] = {g->off, g->col, g->old_of_new, g->new_of_old};
   for (void* p : all)
     if (p) cudaFreeAsync(p, 0);
+  cudaStreamSynchronize(0);
   free(g);
 }

@@ -306,7 +306,7 @@ extern "C" g3_status g3_batch_pack(g3_graph* const* graphs, int32_t G, void* str
              {(void**)&b->order_warp, (size_t)G * 4}, {(void**)&b->order_cta, (size_t)G * 4},
              {(void**)&b->counters, 16}};
   for (auto& r : req) {
-    if (cudaMalloc(r.p, r.bytes) != cudaSuccess) {
+    if (g3_alloc_should_fail() || cudaMalloc(r.p, r.bytes) != cudaSuccess) {
       cudaGetLastError();
       g3_set_error("g3_batch_pack: cudaMalloc(%zu) failed", r.bytes);
       g3_batch_free(b);

@@ -148,7 +148,7 @@ struct g3_bfs_ws {
   LevelLog* log;
   cudaEvent_t ev[6];
   // resident-grid sizes (SMs x blocks per SM) per kernel
-  int grid_front, grid_bins, grid_bu, grid_conv, grid_tr, grid_tr4;
+  int grid_front, grid_bins, grid_bu, grid_tiles, grid_tiles2, grid_conv, grid_tr, grid_tr4;
   // graph mode: instantiated level loop and the options it was built for
   cudaGraphExec_t gexec;
   g3_bfs_opts gopts;
@@ -438,17 +438,38 @@ __device__ __forceinline__ void wq_push(WarpQueue& q, bool want, int32_t item, i
   __shared__ int32_t wq_mem[8][WQ_CAP];                    \
   WarpQueue q{wq_mem[threadIdx.x >> 5], 0}
 
-// Claims w for v and records the statistics of the claimed vertex (the next
-// frontier's degree sum, label range and histogram). All 32 lanes must call
-// it together.
-__device__ __forceinline__ void td_visit(const TdArgs& a, WarpQueue& q, StatAcc& acc, bool has,
-                                         int32_t w, int32_t v) {
-  bool claim = has && td_claim(a.visited, w);
-  if (claim) {
-    pl_put(a.plo, w, v, a.lnext);  // v: the parent's original ID
-    acc.add_vertex(w, a.off[w + 1] - a.off[w]);
-  }
-  wq_push(q, claim, w, a.qnext, &a.c->q_len);
+// Claims up to four neighbours w[k] (has[k]) for v at once: the four
+// visited-word reads, then the atomicOr of those still clear, are issued
+// together so that a lane keeps four claims in flight instead of one
+// dependent read-atomic pair at a time. The winners write (parent, level),
+// record their statistics and are appended to the next queue. All 32 lanes
+// must call it together.
+__device__ __forceinline__ void td_visit4(const TdArgs& a, WarpQueue& q, StatAcc& acc,
+                                          const bool has[4], const int32_t w[4], int32_t v) {
+  uint32_t word[4];
+  bool cand[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) word[k] = has[k] ? __ldcg(&a.visited[w[k] >> 5]) : ~0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cand[k] = has[k] && !((word[k] >> (w[k] & 31)) & 1u);
+  uint32_t old[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    old[k] = cand[k] ? atomicOr(&a.visited[w[k] >> 5], 1u << (w[k] & 31)) : ~0u;
+  bool claim[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) claim[k] = cand[k] && !((old[k] >> (w[k] & 31)) & 1u);
+  int64_t dg[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dg[k] = claim[k] ? a.off[w[k] + 1] - a.off[w[k]] : 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (claim[k]) {
+      pl_put(a.plo, w[k], v, a.lnext);  // v: the parent's original ID
+      acc.add_vertex(w[k], dg[k]);
+    }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) wq_push(q, claim[k], w[k], a.qnext, &a.c->q_len);
 }
 
 // Processes row entries [b, e) of vertex v with `nthr` cooperating threads
@@ -463,10 +484,10 @@ __device__ __forceinline__ void td_row_vec4(const TdArgs& a, WarpQueue& q, StatA
     const int64_t j = a0 + 4 * (t + s * nthr);
     int4 x = make_int4(0, 0, 0, 0);
     if (j < e) x = *reinterpret_cast<const int4*>(a.col + j);
-    td_visit(a, q, acc, j + 0 >= b && j + 0 < e, x.x, vo);
-    td_visit(a, q, acc, j + 1 >= b && j + 1 < e, x.y, vo);
-    td_visit(a, q, acc, j + 2 >= b && j + 2 < e, x.z, vo);
-    td_visit(a, q, acc, j + 3 >= b && j + 3 < e, x.w, vo);
+    const bool has[4] = {j >= b && j < e, j + 1 >= b && j + 1 < e, j + 2 >= b && j + 2 < e,
+                         j + 3 >= b && j + 3 < e};
+    const int32_t w[4] = {x.x, x.y, x.z, x.w};
+    td_visit4(a, q, acc, has, w, vo);
   }
 }
 
@@ -517,10 +538,15 @@ __global__ void __launch_bounds__(256) td_front(const int64_t* __restrict__ off,
     const int cnt = small ? (int)d : 0;
     const int maxc = __reduce_max_sync(0xffffffffu, cnt);
     const int32_t vo = cnt ? orig_of(a.o2n, v) : 0;
-    for (int k = 0; k < maxc; ++k) {
-      bool has = k < cnt;
-      int32_t w = has ? col[b + k] : 0;
-      td_visit(a, wq, acc, has, w, vo);
+    for (int k = 0; k < maxc; k += 4) {
+      bool has[4];
+      int32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        has[u] = k + u < cnt;
+        w[u] = has[u] ? col[b + k + u] : 0;
+      }
+      td_visit4(a, wq, acc, has, w, vo);
     }
   }
   wq_flush(wq, a.qnext, &c->q_len);
@@ -530,7 +556,7 @@ __global__ void __launch_bounds__(256) td_front(const int64_t* __restrict__ off,
 // The three bins in one launch: warp per warp-bin vertex, CTA per CTA-bin
 // vertex, and the grid bin as one flattened edge range split evenly over all
 // warps of the grid (Algorithm 4's even split, applied to every hub at once).
-__global__ void __launch_bounds__(256, 6) td_bins(const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(256, 5) td_bins(const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
                                                uint32_t* visited, PlOut plo, Bufs B,
                                                const int32_t* __restrict__ bins,
@@ -561,22 +587,20 @@ __global__ void __launch_bounds__(256, 6) td_bins(const int64_t* __restrict__ of
   const unsigned long long gp = c->g_pack;
   const int64_t nh = (int64_t)(gp >> GP_SHIFT), E = (int64_t)(gp & GP_MASK);
   if (E > 0) {
+    // every warp owns an equal range [j0, j1) of the hubs' concatenated
+    // lists and walks the hub segments it overlaps, 128 entries per step
     const int32_t* gbin = bins + 2 * nb1;
-    const int64_t per = (((E + nwarps - 1) / nwarps) + 31) & ~31ll;
+    const int64_t per = (((E + nwarps - 1) / nwarps) + 127) & ~127ll;
     const int64_t j0 = gw * per, j1 = min(E, j0 + per);
     if (j0 < j1) {
-      int64_t h = g3_upper_bound_i64(goff, nh, j0) - 1;
-      for (int64_t base = j0; base < j1; base += 32) {
-        const int64_t j = base + lane;
-        const bool act = j < j1;
-        int32_t vo = 0, w = 0;
-        if (act) {
-          while (h + 1 < nh && goff[h + 1] <= j) ++h;
-          const int32_t v = gbin[h];
-          w = col[off[v] + (j - goff[h])];
-          vo = orig_of(a.o2n, v);
-        }
-        td_visit(a, wq, acc, act, w, vo);
+      for (int64_t h = g3_upper_bound_i64(goff, nh, j0) - 1; h < nh && goff[h] < j1; ++h) {
+        const int64_t s0 = max(j0, goff[h]);
+        const int64_t s1 = min(j1, h + 1 < nh ? goff[h + 1] : E);
+        if (s0 >= s1) continue;
+        const int32_t v = gbin[h];
+        const int64_t rb = off[v] + (s0 - goff[h]), re = off[v] + (s1 - goff[h]);
+        const int64_t steps = (re - (rb & ~3ll) + 127) / 128;
+        td_row_vec4(a, wq, acc, v, rb, re, lane, 32, steps);
       }
     }
   }
@@ -703,6 +727,225 @@ __global__ void __launch_bounds__(256, 6) bu_pull(int32_t nb, int64_t nwords, ui
     }
   }
   acc.flush(c);
+}
+
+// Rest of a row after a missed first probe, four entries per step: their
+// four column loads and then their four frontier probes are in flight
+// together, and the first hit in scan order wins, so k (entries examined, up
+// to and including the parent) is the same as for a one-at-a-time scan.
+// Entries past the row's end are never loaded.
+template <int REV>
+__device__ __forceinline__ int32_t bu_scan_rest4(const int32_t* __restrict__ col,
+                                                 const uint32_t* __restrict__ fcur, int64_t b,
+                                                 int64_t e, int64_t& k) {
+  const int64_t d = e - b;
+  while (k < d) {
+    int32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t kk = k + q;
+      w[q] = kk < d ? __ldg(&col[REV ? e - 1 - kk : b + kk]) : -1;
+    }
+    bool h[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[q] = w[q] >= 0 && in_frontier(fcur, w[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (h[q]) {
+        k += q + 1;
+        return w[q];
+      }
+    k = k + 4 < d ? k + 4 : d;
+  }
+  return -1;
+}
+
+// One round of the bottom-up search for up to U vertices per lane (v[u] < 0:
+// none): first all their neighbors+ entries (last row entry and degree, 8
+// coalesced bytes each; in CSR order the row bounds and first entry), then
+// all their first probes, then the rest of the missed rows four entries per
+// step. Found vertices get (parent, level) and their statistics; found[u]
+// tells which.
+template <int REV, int U>
+__device__ __forceinline__ void bu_round(const int32_t (&v)[U], bool (&found)[U],
+                                         const int64_t* __restrict__ off,
+                                         const int32_t* __restrict__ col,
+                                         const int2* __restrict__ nplus,
+                                         const uint32_t* __restrict__ fcur,
+                                         const int32_t* __restrict__ o2n, const PlOut& plo,
+                                         int32_t lnext, StatAcc& acc) {
+  int32_t x[U], d[U];
+  int64_t bq[U], eq[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    x[u] = -1;
+    d[u] = 0;
+    bq[u] = eq[u] = 0;
+  }
+  if (REV) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (v[u] >= 0) {
+        const int2 tt = nplus[v[u]];
+        x[u] = tt.x;
+        d[u] = tt.y;
+      }
+  } else {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (v[u] >= 0) {
+        bq[u] = off[v[u]];
+        eq[u] = off[v[u] + 1];
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      d[u] = (int32_t)(eq[u] - bq[u]);
+      if (d[u] > 0) x[u] = __ldg(&col[bq[u]]);
+    }
+  }
+  int32_t p[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) p[u] = (x[u] >= 0 && in_frontier(fcur, x[u])) ? x[u] : -1;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    int64_t k = d[u] > 0 ? 1 : 0;
+    if (p[u] < 0 && d[u] > 1) {
+      if (REV) {
+        eq[u] = off[v[u] + 1];
+        bq[u] = eq[u] - d[u];
+      }
+      p[u] = bu_scan_rest4<REV>(col, fcur, bq[u], eq[u], k);
+    }
+    acc.ex += (unsigned)k;
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    found[u] = p[u] >= 0;
+    if (found[u]) {
+      pl_put(plo, v[u], o2n ? __ldg(&o2n[p[u]]) : p[u], lnext);
+      acc.add_vertex(v[u], d[u]);
+    }
+  }
+}
+
+// Bottom-up level over word tiles (Algorithms 5 and 6). A warp owns 32
+// consecutive words of the visited bitmap (1024 vertices) at a time; lane i
+// reads word i, so a tile without unvisited vertices costs one coalesced
+// load and one store of zero next-frontier words. A dense tile (at least
+// BU_DENSE unvisited vertices) is worked lane by word: lane i takes the
+// unvisited vertices of word i, U per round, and builds its next-frontier
+// word in a register. A sparse tile's unvisited vertices are first compacted
+// into a per-warp list in shared memory so that every lane has work; found
+// vertices then set their bit in the warp's next-frontier tile in shared
+// memory. Either way lane i finally writes next-frontier word i and ORs it
+// into visited word i (the paper's visited |= F_next, without atomics in
+// global memory).
+#define BU_WARPS 8
+#define BU_DENSE 384
+template <int REV, int U>
+__global__ void __launch_bounds__(32 * BU_WARPS, (U > 2 ? 4 : 5)) bu_tiles(
+    int32_t nb, int64_t nwords, uint32_t* visited, Bufs B, const int64_t* __restrict__ off,
+    const int32_t* __restrict__ col, const int2* __restrict__ nplus, PlOut plo, Ctrl* c) {
+  if (c->dir != G3_DIR_BU) return;
+  __shared__ uint16_t s_list[BU_WARPS][1024];
+  __shared__ uint32_t s_next[BU_WARPS][32];
+  const uint32_t* __restrict__ fcur = (c->fsel ? B.f[1] : B.f[0]);
+  uint32_t* __restrict__ fnext = (c->fsel ? B.f[0] : B.f[1]);
+  const int32_t lnext = c->level + 1;
+  const int32_t* __restrict__ o2n = B.o2n;
+  StatAcc acc;
+  acc.init();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint16_t* list = s_list[wib];
+  uint32_t* nx = s_next[wib];
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t ntiles = (nwords + 31) >> 5;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles;
+       t += nwarps) {
+    const int64_t w = t * 32 + lane;
+    const int64_t vbase = t * 1024;
+    uint32_t vis = 0xFFFFFFFFu, unv = 0u;
+    if (w < nwords) {
+      vis = visited[w];
+      const int64_t left = (int64_t)nb - w * 32;  // vertices of this word in the graph
+      const uint32_t valid = left >= 32 ? 0xFFFFFFFFu : ((1u << left) - 1u);
+      unv = ~vis & valid;
+    }
+    const unsigned cnt = __popc(unv);
+    const unsigned total = __reduce_add_sync(0xffffffffu, cnt);
+    if (total == 0) {
+      if (w < nwords) fnext[w] = 0u;
+      continue;
+    }
+    uint32_t nword = 0u;
+    if (total >= BU_DENSE) {
+      // lane by word: U of this word's unvisited vertices per round
+      uint32_t rem = unv;
+      while (__any_sync(0xffffffffu, rem != 0u)) {
+        int32_t v[U];
+        int bitpos[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          bitpos[u] = rem ? __ffs(rem) - 1 : -1;
+          v[u] = bitpos[u] >= 0 ? (int32_t)(w * 32 + bitpos[u]) : -1;
+          if (rem) rem &= rem - 1u;
+        }
+        bool found[U];
+        bu_round<REV, U>(v, found, off, col, nplus, fcur, o2n, plo, lnext, acc);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (found[u]) nword |= 1u << bitpos[u];
+      }
+    } else {
+      // compact the tile's unvisited vertices (offsets within the tile)
+      unsigned inc = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      unsigned pos = inc - cnt;
+      uint32_t bits = unv;
+      while (bits) {
+        const int bb = __ffs(bits) - 1;
+        list[pos++] = (uint16_t)(lane * 32 + bb);
+        bits &= bits - 1u;
+      }
+      nx[lane] = 0u;
+      __syncwarp();
+      for (unsigned base = 0; base < total; base += 32 * U) {
+        int32_t v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const unsigned j = base + u * 32 + lane;
+          v[u] = j < total ? (int32_t)(vbase + list[j]) : -1;
+        }
+        bool found[U];
+        bu_round<REV, U>(v, found, off, col, nplus, fcur, o2n, plo, lnext, acc);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (found[u]) {
+            const int32_t rel = v[u] - (int32_t)vbase;
+            atomicOr(&nx[rel >> 5], 1u << (rel & 31));
+          }
+      }
+      __syncwarp();
+      nword = nx[lane];
+      __syncwarp();
+    }
+    if (w < nwords) {
+      fnext[w] = nword;
+      if (nword) visited[w] = vis | nword;
+    }
+  }
+  acc.flush(c);
+}
+
+// The word-tile kernel for the options: bu_kernel 0 four rows in flight per
+// lane, 2 two rows (fewer registers, more resident warps).
+static void* bu_tiles_fn(int kernel, int rev) {
+  if (kernel == 2) return rev ? (void*)bu_tiles<1, 2> : (void*)bu_tiles<0, 2>;
+  return rev ? (void*)bu_tiles<1, 4> : (void*)bu_tiles<0, 4>;
 }
 
 // ------------------------------------------------------------ conversions
@@ -966,6 +1209,102 @@ __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int
   }
 }
 
+// The same mapping in two passes over label halves, for packed arrays too
+// large to stay in L2 beside the streamed arrays (at 2^26 vertices the
+// packed words take 131 MB, and one pass gathering from all of them misses
+// L2 on most 4-byte gathers, each costing a 32-byte sector). Pass 1 streams
+// new_of_old and resolves the vertices labelled below `split`, gathering only
+// from that half of the packed array; for every original ID it writes one
+// 4-byte record into parent[] (used as scratch): the packed word itself
+// (parent, level code) when resolved, or a marker. Pass 2 streams those
+// records, resolves the rest from the other half, and writes parent[] and
+// level[]. Records use the packed format with three reserved level codes
+// (lmax = 2^bits - 1): lmax - 1 unreached or isolated, lmax pending with the
+// label in the parent field; resolved levels are below lmax - 1 (higher
+// levels, and those in the side table, are left pending for pass 2, which
+// decodes them from the packed word). Needs bits >= 4 and 16-byte aligned
+// outputs.
+__device__ __forceinline__ uint32_t tr_pass1_one(int32_t x, int32_t nb, int32_t split,
+                                                 const uint32_t* __restrict__ visited,
+                                                 const PlOut& plo, uint32_t lmax) {
+  const bool reached = x < nb && ((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u);
+  if (!reached) return lmax - 1u;
+  const uint32_t pend = ((uint32_t)x << plo.bits) | lmax;
+  if (x >= split) return pend;
+  const uint32_t w = __ldg(&plo.pl[x]);
+  return (w & lmax) < lmax - 1u ? w : pend;
+}
+
+__global__ void __launch_bounds__(256) bfs_translate_p1(int32_t n, int32_t nb, int32_t split,
+                                                        const int32_t* __restrict__ new_of_old,
+                                                        const uint32_t* __restrict__ visited,
+                                                        PlOut plo, uint32_t* rec) {
+  const uint32_t lmax = (1u << plo.bits) - 1u;
+  const int64_t n4 = n >> 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 xs = __ldcs(reinterpret_cast<const int4*>(new_of_old) + i);
+    uint4 r;
+    r.x = tr_pass1_one(xs.x, nb, split, visited, plo, lmax);
+    r.y = tr_pass1_one(xs.y, nb, split, visited, plo, lmax);
+    r.z = tr_pass1_one(xs.z, nb, split, visited, plo, lmax);
+    r.w = tr_pass1_one(xs.w, nb, split, visited, plo, lmax);
+    __stcs(reinterpret_cast<uint4*>(rec) + i, r);
+  }
+  const int64_t v = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v < n) rec[v] = tr_pass1_one(new_of_old[v], nb, split, visited, plo, lmax);
+}
+
+__device__ __forceinline__ int2 tr_pass2_one(uint32_t r, const PlOut& plo, uint32_t lmax) {
+  const uint32_t code = r & lmax;
+  if (code == lmax - 1u) return make_int2(-1, -1);
+  if (code == lmax) {
+    const int32_t x = (int32_t)(r >> plo.bits);
+    return pl_decode(plo, __ldg(&plo.pl[x]), x);
+  }
+  return make_int2((int32_t)(r >> plo.bits), (int32_t)code);
+}
+
+__global__ void __launch_bounds__(256) bfs_translate_p2(int32_t n, int32_t root, PlOut plo,
+                                                        int32_t* parent, int32_t* level) {
+  const uint32_t lmax = (1u << plo.bits) - 1u;
+  const int64_t n4 = n >> 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 r = __ldcs(reinterpret_cast<const uint4*>(parent) + i);
+    const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+    // the pending ones first, so that their gathers are in flight together
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      w[k] = (rr[k] & lmax) == lmax ? __ldg(&plo.pl[rr[k] >> plo.bits]) : 0u;
+    int p[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t code = rr[k] & lmax;
+      int2 t;
+      if (code == lmax) t = pl_decode(plo, w[k], (int32_t)(rr[k] >> plo.bits));
+      else if (code == lmax - 1u) t = make_int2(-1, -1);
+      else t = make_int2((int32_t)(rr[k] >> plo.bits), (int32_t)code);
+      p[k] = t.x;
+      l[k] = t.y;
+    }
+    if ((root >> 2) == i) {
+      p[root & 3] = root;
+      l[root & 3] = 0;
+    }
+    __stcs(reinterpret_cast<int4*>(parent) + i, make_int4(p[0], p[1], p[2], p[3]));
+    __stcs(reinterpret_cast<int4*>(level) + i, make_int4(l[0], l[1], l[2], l[3]));
+  }
+  const int64_t v = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v < n) {
+    int2 t = tr_pass2_one((uint32_t)parent[v], plo, lmax);
+    if (v == root) t = make_int2(root, 0);
+    parent[v] = t.x;
+    level[v] = t.y;
+  }
+}
+
 __global__ void build_nplus(int32_t nb, const int64_t* __restrict__ off,
                             const int32_t* __restrict__ col, int2* nplus) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nb;
@@ -1024,7 +1363,8 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
       {(void**)&ws->log, sizeof(LevelLog) * LOG_MAX},
   };
   for (auto& r : req) {
-    cudaError_t e = cudaMalloc(r.p, r.bytes);
+    cudaError_t e = g3_alloc_should_fail() ? cudaErrorMemoryAllocation
+                                            : cudaMalloc(r.p, r.bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       g3_set_error("g3_bfs workspace: cudaMalloc(%zu): %s", r.bytes, cudaGetErrorString(e));
@@ -1058,6 +1398,12 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
   ws->grid_bu = resident_grid(bu_pull<1>, 256);
   int g0 = resident_grid(bu_pull<0>, 256);
   if (g0 < ws->grid_bu) ws->grid_bu = g0;
+  ws->grid_tiles = resident_grid(bu_tiles<1, 4>, 32 * BU_WARPS);
+  g0 = resident_grid(bu_tiles<0, 4>, 32 * BU_WARPS);
+  if (g0 < ws->grid_tiles) ws->grid_tiles = g0;
+  ws->grid_tiles2 = resident_grid(bu_tiles<1, 2>, 32 * BU_WARPS);
+  g0 = resident_grid(bu_tiles<0, 2>, 32 * BU_WARPS);
+  if (g0 < ws->grid_tiles2) ws->grid_tiles2 = g0;
   ws->grid_conv = resident_grid(bitmap_to_q, 256);
   ws->grid_tr = resident_grid(bfs_translate, 256);
   ws->grid_tr4 = resident_grid(bfs_translate4, 256);
@@ -1069,16 +1415,22 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
 // memory, the device alias of page-locked host memory (the output pass then
 // writes straight into host memory over the chip-to-chip link), NULL for
 // pageable host memory (which goes through a device staging buffer).
-static int32_t* device_view(int32_t* p) {
+static int32_t* device_view(int32_t* p, bool* in_hbm = nullptr) {
   cudaPointerAttributes at;
+  if (in_hbm) *in_hbm = false;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeDevice) {
+    if (in_hbm) *in_hbm = true;
+    return p;
+  }
+  if (at.type == cudaMemoryTypeManaged) return p;
   if (at.type == cudaMemoryTypeHost && at.devicePointer) return (int32_t*)at.devicePointer;
   return nullptr;
 }
+
 
 static inline int cap_grid(int64_t items, int per_block, int resident) {
   int64_t b = (items + per_block - 1) / per_block;
@@ -1128,6 +1480,18 @@ static g3_status launch_level(const Launch& S, int mode, int64_t nf, cudaEvent_t
     td_bins<<<ws->grid_bins, 256, 0, s>>>(S.g->off, S.g->col, ws->visited, ws->plo, S.B,
                                           ws->bins, ws->goff, S.nb1, c);
     G3_CHECK_LAUNCH();
+  } else if (S.o->bu_kernel != 1) {
+    const int grid = cap_grid((ws->nwords + 31) / 32, BU_WARPS,
+                              S.o->bu_kernel == 2 ? ws->grid_tiles2 : ws->grid_tiles);
+    void* fn = bu_tiles_fn(S.o->bu_kernel, S.o->bu_reverse);
+    int64_t nwords = ws->nwords;
+    int32_t nb = ws->nb;
+    const int64_t* off = S.g->off;
+    const int32_t* col = S.g->col;
+    Bufs B = S.B;
+    void* args[] = {&nb, &nwords, &ws->visited, &B, &off, &col, &ws->nplus, &ws->plo, &c};
+    G3_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(32 * BU_WARPS), args, 0, s));
+    g3_count_launch();
   } else {
     const int grid = cap_grid(ws->nwords, 16, ws->grid_bu);
     if (S.o->bu_reverse)
@@ -1166,7 +1530,7 @@ static bool same_opts(const g3_bfs_opts& a, const g3_bfs_opts& b) {
   return a.controller == b.controller && a.alpha == b.alpha && a.beta == b.beta &&
          a.t1 == b.t1 && a.t2 == b.t2 && a.t3 == b.t3 && a.bu_reverse == b.bu_reverse &&
          a.mlp_params == b.mlp_params && a.mlp_margin == b.mlp_margin &&
-         a.mlp_bins == b.mlp_bins;
+         a.mlp_bins == b.mlp_bins && a.bu_kernel == b.bu_kernel;
 }
 
 // Builds the level loop: WHILE(h_loop) { bfs_select -> SWITCH(h_mode) {
@@ -1184,11 +1548,16 @@ static g3_status build_graph(Launch& S) {
   int64_t nwords = ws->nwords;
   int32_t nb = ws->nb;
   int gconv = ws->grid_conv, gfront = ws->grid_front, gbins = ws->grid_bins;
-  int gbu = cap_grid(ws->nwords, 16, ws->grid_bu);
+  const bool tiles = S.o->bu_kernel != 1;
+  int gbu = tiles ? cap_grid((ws->nwords + 31) / 32, BU_WARPS,
+                             S.o->bu_kernel == 2 ? ws->grid_tiles2 : ws->grid_tiles)
+                  : cap_grid(ws->nwords, 16, ws->grid_bu);
+  const int bbu = tiles ? 32 * BU_WARPS : 256;
   int gclear = g3_grid_for(ws->nwords, 256), gq2b = g3_grid_for(ws->nb, 256);
   const int64_t* off = S.g->off;
   const int32_t* col = S.g->col;
-  void* bu_fn = S.o->bu_reverse ? (void*)bu_pull<1> : (void*)bu_pull<0>;
+  void* bu_fn = tiles ? bu_tiles_fn(S.o->bu_kernel, S.o->bu_reverse)
+                      : (S.o->bu_reverse ? (void*)bu_pull<1> : (void*)bu_pull<0>);
   void* a_conv[] = {&S.B, &nwords, &c};
   void* a_clear[] = {&S.B, &nwords, &c};
   void* a_q2b[] = {&S.B, &c};
@@ -1236,12 +1605,12 @@ static g3_status build_graph(Launch& S) {
     if ((st = add_kernel(br[MODE_TD_B], &n1, &n0, (void*)td_front, gfront, 256, a_td))) break;
     if ((st = add_kernel(br[MODE_TD_B], &n2, &n1, (void*)td_bins, gbins, 256, a_td))) break;
     // MODE_BU_B
-    if ((st = add_kernel(br[MODE_BU_B], &n0, nullptr, bu_fn, gbu, 256, a_bu))) break;
+    if ((st = add_kernel(br[MODE_BU_B], &n0, nullptr, bu_fn, gbu, bbu, a_bu))) break;
     // MODE_BU_Q
     if ((st = add_kernel(br[MODE_BU_Q], &n0, nullptr, (void*)bm_clear, gclear, 256, a_clear)))
       break;
     if ((st = add_kernel(br[MODE_BU_Q], &n1, &n0, (void*)q_to_bitmap, gq2b, 256, a_q2b))) break;
-    if ((st = add_kernel(br[MODE_BU_Q], &n2, &n1, bu_fn, gbu, 256, a_bu))) break;
+    if ((st = add_kernel(br[MODE_BU_Q], &n2, &n1, bu_fn, gbu, bbu, a_bu))) break;
     ca = ctrl_args(S, 1, h_loop);
     if ((st = add_kernel(body, &ctl, &sw, (void*)bfs_control, 1, 32, a_ctl))) break;
     cudaGraphExec_t ex = nullptr;
@@ -1367,13 +1736,24 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
 
   // outputs in original IDs: device (or device-visible host) buffers, else
   // staging buffers copied to the host at the end
-  int32_t* vp = device_view(parent);
-  int32_t* vl = device_view(level);
+  bool hbm_p = false, hbm_l = false;
+  int32_t* vp = device_view(parent, &hbm_p);
+  int32_t* vl = device_view(level, &hbm_l);
   const bool dev_p = vp != nullptr, dev_l = vl != nullptr;
   int32_t* op = dev_p ? vp : ws->out_parent;
   int32_t* ol = dev_l ? vl : ws->out_level;
+  const bool aligned = (((uintptr_t)op | (uintptr_t)ol) & 15) == 0;
+  const bool split_ok = aligned && g->relabelled && hbm_p && hbm_l && ws->plo.bits >= 4 &&
+                        nb > 1;
+  const bool split = split_ok && o->out_split == 2;
   auto translate = [&]() -> g3_status {
-    if ((((uintptr_t)op | (uintptr_t)ol) & 15) == 0) {
+    if (split) {
+      const int grid = cap_grid((g->n + 3) / 4, 256, ws->grid_tr4);
+      bfs_translate_p1<<<grid, 256, 0, s>>>(g->n, nb, nb / 2, g->new_of_old, ws->visited,
+                                            ws->plo, (uint32_t*)op);
+      G3_CHECK_LAUNCH();
+      bfs_translate_p2<<<grid, 256, 0, s>>>(g->n, root, ws->plo, op, ol);
+    } else if (aligned) {
       bfs_translate4<<<cap_grid((g->n + 3) / 4, 256, ws->grid_tr4), 256, 0, s>>>(
           g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op,
           ol);
@@ -1473,7 +1853,8 @@ extern "C" g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, 
   g3_bfs_opts o;
   if (opts) o = *opts; else g3_bfs_opts_default(&o);
   if (o.controller < 0 || o.controller > 3 || o.alpha <= 0 || o.beta <= 0 || o.t1 < 1 ||
-      o.t2 <= o.t1 || o.t3 <= o.t2 || o.mlp_margin < 0) {
+      o.t2 <= o.t1 || o.t3 <= o.t2 || o.mlp_margin < 0 || o.out_split < 0 || o.out_split > 2 ||
+      o.bu_kernel < 0 || o.bu_kernel > 2) {
     g3_set_error("g3_bfs: bad options");
     return G3_EINVAL;
   }

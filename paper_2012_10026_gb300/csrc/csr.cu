@@ -75,28 +75,43 @@ __global__ void csr_max_degree(const int64_t* __restrict__ off, int32_t n,
 g3_status g3_graph_max_degree(g3_graph* g, cudaStream_t s) {
   unsigned long long* d;
   G3_TRY(g3_alloc(&d, 1, s));
-  G3_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(*d), s));
-  if (g->n_bfs > 0) {
-    csr_max_degree<<<g3_grid_for(g->n_bfs, 256), 256, 0, s>>>(g->off, g->n_bfs, d);
-    G3_CHECK_LAUNCH();
-  }
   unsigned long long h = 0;
-  G3_TRY_CUDA(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
-  G3_TRY_CUDA(cudaStreamSynchronize(s));
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(*d), s);
+  if (e == cudaSuccess && g->n_bfs > 0) {
+    csr_max_degree<<<g3_grid_for(g->n_bfs, 256), 256, 0, s>>>(g->off, g->n_bfs, d);
+    g3_count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   g3_free(d, s);
+  if (e != cudaSuccess) {
+    g3_set_error("g3_graph_max_degree: %s", cudaGetErrorString(e));
+    return G3_ECUDA;
+  }
   g->max_degree = (int64_t)h;
   return G3_OK;
 }
 
-static g3_status build_impl(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
-                            cudaStream_t s, g3_graph* g) {
-  const int bits = g3_bits_for(n);
-  const int64_t nk = 2 * m;
-  uint64_t *ka = nullptr, *kb = nullptr, *sorted = nullptr;
+// Temporaries of the build, released on every path (a failure part-way
+// leaves nothing allocated but what the graph itself owns, which
+// g3_build_csr frees with the graph).
+struct BuildBufs {
+  uint64_t *ka = nullptr, *kb = nullptr;
   int64_t* partial = nullptr;
   int* err = nullptr;
   unsigned long long* deg = nullptr;
-  g3_status st = G3_OK;
+  void release(cudaStream_t s) {
+    void* all[] = {ka, kb, partial, err, deg};
+    for (void* x : all) g3_free(x, s);
+  }
+};
+
+static g3_status build_impl(const int32_t* src, const int32_t* dst, int64_t m, int32_t n,
+                            cudaStream_t s, g3_graph* g, BuildBufs& B) {
+  const int bits = g3_bits_for(n);
+  const int64_t nk = 2 * m;
+  uint64_t* sorted = nullptr;
   int64_t host[2] = {0, 0};
 
   g->n = n;
@@ -108,43 +123,38 @@ static g3_status build_impl(const int32_t* src, const int32_t* dst, int64_t m, i
     g->nnz = 0;
     return g3_graph_max_degree(g, s);
   }
-  G3_TRY(g3_alloc(&ka, nk, s));
-  G3_TRY(g3_alloc(&kb, nk, s));
-  G3_TRY(g3_alloc(&err, 2, s));
-  G3_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-  csr_make_keys<<<g3_grid_for(m, 256), 256, 0, s>>>(src, dst, m, n, bits, ka, err);
+  G3_TRY(g3_alloc(&B.ka, nk, s));
+  G3_TRY(g3_alloc(&B.kb, nk, s));
+  G3_TRY(g3_alloc(&B.err, 2, s));
+  G3_TRY_CUDA(cudaMemsetAsync(B.err, 0, sizeof(int), s));
+  csr_make_keys<<<g3_grid_for(m, 256), 256, 0, s>>>(src, dst, m, n, bits, B.ka, B.err);
   G3_CHECK_LAUNCH();
-  G3_TRY(g3_radix_sort_u64(ka, kb, nk, 2 * bits, &sorted, s));
-  uint64_t* other = sorted == ka ? kb : ka;
-  G3_TRY(g3_alloc(&partial, g3_compact_partials(nk), s));
-  G3_TRY(g3_compact(nk, KeepFirstOfRun{sorted}, CopyKey{sorted, other}, partial, s));
+  G3_TRY(g3_radix_sort_u64(B.ka, B.kb, nk, 2 * bits, &sorted, s));
+  uint64_t* other = sorted == B.ka ? B.kb : B.ka;
+  G3_TRY(g3_alloc(&B.partial, g3_compact_partials(nk), s));
+  G3_TRY(g3_compact(nk, KeepFirstOfRun{sorted}, CopyKey{sorted, other}, B.partial, s));
   int64_t nbk = (nk + CP_TILE - 1) / CP_TILE;
-  G3_TRY_CUDA(cudaMemcpyAsync(&host[0], partial + nbk, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  G3_TRY_CUDA(cudaMemcpyAsync(&host[0], B.partial + nbk, sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, s));
   int herr = 0;
-  G3_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  G3_TRY_CUDA(cudaMemcpyAsync(&herr, B.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   G3_TRY_CUDA(cudaStreamSynchronize(s));
   if (herr) {
     g3_set_error("g3_build_csr: an endpoint lies outside [0, %d)", n);
-    st = G3_EINVAL;
+    return G3_EINVAL;
   }
   const int64_t nnz = host[0];
   g->nnz = nnz;
-  if (st == G3_OK) st = g3_alloc(&g->col, nnz > 0 ? nnz : 1, s);
-  if (st == G3_OK) st = g3_alloc(&deg, (size_t)n + 1, s);
-  if (st == G3_OK) {
-    cudaMemsetAsync(deg, 0, ((size_t)n + 1) * sizeof(*deg), s);
-    if (nnz > 0) {
-      csr_rows<<<g3_grid_for(nnz, 256), 256, 0, s>>>(other, nnz, bits, g->col, deg);
-      if (cudaGetLastError() != cudaSuccess) st = G3_ECUDA;
-    }
+  G3_TRY(g3_alloc(&g->col, nnz > 0 ? nnz : 1, s));
+  G3_TRY(g3_alloc(&B.deg, (size_t)n + 1, s));
+  G3_TRY_CUDA(cudaMemsetAsync(B.deg, 0, ((size_t)n + 1) * sizeof(*B.deg), s));
+  if (nnz > 0) {
+    csr_rows<<<g3_grid_for(nnz, 256), 256, 0, s>>>(other, nnz, bits, g->col, B.deg);
+    G3_CHECK_LAUNCH();
   }
-  if (st == G3_OK) st = g3_exclusive_scan_i64((const int64_t*)deg, g->off, n, s);
-  g3_free(ka, s);
-  g3_free(kb, s);
-  g3_free(partial, s);
-  g3_free(err, s);
-  g3_free(deg, s);
-  if (st != G3_OK) return st;
+  G3_TRY(g3_exclusive_scan_i64((const int64_t*)B.deg, g->off, n, s));
+  B.release(s);
+  B = BuildBufs();
   return g3_graph_max_degree(g, s);
 }
 
@@ -162,7 +172,9 @@ extern "C" g3_status g3_build_csr(const int32_t* src, const int32_t* dst, int64_
   cudaStream_t s = (cudaStream_t)stream;
   g3_graph* g = (g3_graph*)calloc(1, sizeof(g3_graph));
   if (!g) return G3_ENOMEM;
-  g3_status st = build_impl(src, dst, m, n, s, g);
+  BuildBufs B;
+  g3_status st = build_impl(src, dst, m, n, s, g, B);
+  B.release(s);
   if (st != G3_OK) {
     cudaStreamSynchronize(s);
     g3_graph_free(g);

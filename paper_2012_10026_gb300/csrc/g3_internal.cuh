@@ -41,6 +41,10 @@ void g3_count_launch();
 // Stream-ordered device allocation that reports G3_ENOMEM.
 g3_status g3_malloc(void** p, size_t bytes, cudaStream_t s);
 void g3_free(void* p, cudaStream_t s);
+// Fault-injection test hooks (g3_debug_inject): every device allocation
+// site asks g3_alloc_should_fail() first and reports G3_ENOMEM when told to.
+bool g3_alloc_should_fail();
+int g3_rcm_hook_cap();
 
 template <typename T>
 static inline g3_status g3_alloc(T** p, size_t count, cudaStream_t s) {

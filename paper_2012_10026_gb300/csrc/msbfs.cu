@@ -70,7 +70,8 @@ static g3_status ms_ws_create(g3_graph* g, g3_ms_ws** out) {
              {(void**)&w->pend, nb1 * 4}, {(void**)&w->items, (size_t)w->items_cap * 8},
              {(void**)&w->d_roots, 64 * 4}};
   for (auto& r : req) {
-    cudaError_t e = cudaMalloc(r.p, r.bytes);
+    cudaError_t e = g3_alloc_should_fail() ? cudaErrorMemoryAllocation
+                                            : cudaMalloc(r.p, r.bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       g3_set_error("g3_msbfs workspace: cudaMalloc(%zu): %s", r.bytes, cudaGetErrorString(e));

@@ -11,15 +11,18 @@
 //
 // Limits and sharing:
 //   * at most G3_NOALLOC_MAX_N vertices; larger graphs are rejected with
-//     G3_EINVAL before anything runs. The array takes about 8.4 MB of device
-//     memory on every GPU that loads the library, until the process exits.
+//     G3_EINVAL before anything runs. The array takes 8,519,936 bytes (about
+//     8.5 MB) of device memory on every GPU that loads the library, until
+//     the process exits.
 //   * every call on a device uses the same array, and the array keeps the
 //     last call's contents; each call clears the parts that must start at
 //     zero. Calls whose GPU work overlaps (other streams, other host threads)
 //     race on the array: serialise them.
 //   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current) and caches it; make that
-//     first call before any stream capture.
+//     cudaGetSymbolAddress (with that device current) and caches it for the
+//     life of the process; make that first call before any stream capture.
+//     The cached address belongs to the device's context at that time: after
+//     cudaDeviceReset on that device, do not call this entry point again.
 #include <mutex>
 
 #include "g3_internal.cuh"

@@ -326,6 +326,9 @@ static g3_status rcm_impl(g3_graph* g, int32_t p_permille, cudaStream_t s, RcmBu
   G3_TRY(g3_alloc(&B.partial, g3_compact_partials(n) + 4, s));
   G3_TRY(g3_alloc(&B.ka, n, s));
   G3_TRY(g3_alloc(&B.kb, n, s));
+  g3_free(g->new_of_old, s);
+  g3_free(g->old_of_new, s);
+  g->new_of_old = g->old_of_new = nullptr;
   G3_TRY(g3_alloc(&g->new_of_old, n, s));
   G3_TRY(g3_alloc(&g->old_of_new, n, s));
   G3_TRY(g3_alloc(&B.counters, 2, s));
@@ -364,7 +367,7 @@ static g3_status rcm_impl(g3_graph* g, int32_t p_permille, cudaStream_t s, RcmBu
     G3_TRY_CUDA(cudaMemcpyAsync(&changed, B.counters, sizeof(int), cudaMemcpyDeviceToHost, s));
     G3_TRY_CUDA(cudaStreamSynchronize(s));
     if (!changed) break;
-    if (it > 4096) {
+    if (it >= g3_rcm_hook_cap()) {
       g3_set_error("g3_rcm_relabel: component hooking did not converge");
       return G3_ETIMEOUT;
     }
@@ -437,7 +440,13 @@ static g3_status rcm_impl(g3_graph* g, int32_t p_permille, cudaStream_t s, RcmBu
   G3_CHECK_LAUNCH();
   int64_t* off_new;
   G3_TRY(g3_alloc(&off_new, (size_t)n_plus + 1, s));
-  G3_TRY(g3_exclusive_scan_i64(B.deg_new, off_new, n_plus, s));
+  {
+    const g3_status sc = g3_exclusive_scan_i64(B.deg_new, off_new, n_plus, s);
+    if (sc != G3_OK) {
+      g3_free(off_new, s);
+      return sc;
+    }
+  }
   B.ka = (g3_free(B.ka, s), nullptr);
   B.kb = (g3_free(B.kb, s), nullptr);
   int32_t* col_new;
@@ -456,10 +465,20 @@ static g3_status rcm_impl(g3_graph* g, int32_t p_permille, cudaStream_t s, RcmBu
       return st;
     }
     rcm_perm_keys<<<grid, 256, 0, s>>>(g->off, n, PermKey{g->col, g->new_of_old, B.ka, bits_n});
-    G3_CHECK_LAUNCH();
-    G3_TRY(g3_radix_sort_u64(B.ka, B.kb, nnz, 2 * bits_n, &sorted, s));
-    rcm_take_col<<<g3_grid_for(nnz, 256), 256, 0, s>>>(sorted, nnz, bits_n, col_new);
-    G3_CHECK_LAUNCH();
+    g3_count_launch();
+    st = cudaGetLastError() == cudaSuccess ? G3_OK : G3_ECUDA;
+    if (st == G3_OK) st = g3_radix_sort_u64(B.ka, B.kb, nnz, 2 * bits_n, &sorted, s);
+    if (st == G3_OK) {
+      rcm_take_col<<<g3_grid_for(nnz, 256), 256, 0, s>>>(sorted, nnz, bits_n, col_new);
+      g3_count_launch();
+      if (cudaGetLastError() != cudaSuccess) st = G3_ECUDA;
+    }
+    if (st != G3_OK) {
+      if (st == G3_ECUDA) g3_set_error("g3_rcm_relabel: relabelled CSR kernels failed");
+      g3_free(off_new, s);
+      g3_free(col_new, s);
+      return st;
+    }
   }
   g3_free(g->off, s);
   g3_free(g->col, s);
@@ -501,6 +520,11 @@ static g3_status relabel(g3_graph* g, int32_t p_permille, cudaStream_t s, const 
       return G3_ECUDA;
     }
   } else {
+    // the graph stays as it was (not relabelled, its CSR untouched); a
+    // half-made permutation is dropped
+    g3_free(g->new_of_old, s);
+    g3_free(g->old_of_new, s);
+    g->new_of_old = g->old_of_new = nullptr;
     cudaStreamSynchronize(s);
   }
   return st;

@@ -38,8 +38,58 @@ static std::atomic<unsigned long long> g_launches{0};
 void g3_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 extern "C" uint64_t g3_kernel_launches(void) { return g_launches.load(); }
 
+// ---------------------------------------------------- fault injection
+// Test hooks (g3_debug_inject): fail the k-th device allocation after arming
+// (one shot), and cap the component-hooking rounds of the RCM relabel.
+static std::atomic<long long> g_fail_at{0};
+static std::atomic<long long> g_alloc_seen{0};
+static std::atomic<int> g_hook_cap{4096};
+
+bool g3_alloc_should_fail() {
+  if (g_fail_at.load(std::memory_order_relaxed) <= 0) return false;
+  const long long c = g_alloc_seen.fetch_add(1) + 1;
+  long long k = c;
+  if (g_fail_at.compare_exchange_strong(k, 0)) {
+    g3_set_error("device allocation %lld failed (injected)", c);
+    return true;
+  }
+  return false;
+}
+
+int g3_rcm_hook_cap() { return g_hook_cap.load(std::memory_order_relaxed); }
+
+extern "C" g3_status g3_debug_inject(int32_t kind, int64_t value) {
+  if (kind == G3_INJECT_ALLOC) {
+    g_alloc_seen = 0;
+    g_fail_at = value > 0 ? value : 0;
+    return G3_OK;
+  }
+  if (kind == G3_INJECT_RCM_ROUNDS) {
+    g_hook_cap = value > 0 ? (int)(value < (1 << 30) ? value : (1 << 30)) : 4096;
+    return G3_OK;
+  }
+  g3_set_error("g3_debug_inject: unknown kind %d", kind);
+  return G3_EINVAL;
+}
+
+extern "C" g3_status g3_debug_pool_used(int64_t* bytes) {
+  if (!bytes) {
+    g3_set_error("g3_debug_pool_used: null argument");
+    return G3_EINVAL;
+  }
+  int dev = 0;
+  cudaMemPool_t pool;
+  G3_TRY_CUDA(cudaGetDevice(&dev));
+  G3_TRY_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t used = 0;
+  G3_TRY_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  *bytes = (int64_t)used;
+  return G3_OK;
+}
+
 g3_status g3_malloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
+  if (g3_alloc_should_fail()) return G3_ENOMEM;
   cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, s);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -118,10 +118,17 @@ def test_bfs_small_cases(case, relabel):
     g = gpu_pipeline(src, dst, n, relabel)
     rng = np.random.default_rng(n)
     roots = sorted(set([0, n - 1] + rng.integers(0, n, 6).tolist()))
-    for ctrl, rev in ((g3.G3_CTRL_HEURISTIC, 1), (g3.G3_CTRL_TOPDOWN, 1),
-                      (g3.G3_CTRL_BOTTOMUP, 1), (g3.G3_CTRL_BOTTOMUP, 0)):
+    # bottom-up in both kernels (word tiles, word pairs) and scan orders; the
+    # output pass in one pass and split over label halves
+    for ctrl, rev, kern, split in ((g3.G3_CTRL_HEURISTIC, 1, 0, 0),
+                                   (g3.G3_CTRL_HEURISTIC, 1, 0, 2),
+                                   (g3.G3_CTRL_TOPDOWN, 1, 0, 1),
+                                   (g3.G3_CTRL_BOTTOMUP, 1, 0, 0), (g3.G3_CTRL_BOTTOMUP, 0, 0, 0),
+                                   (g3.G3_CTRL_BOTTOMUP, 1, 1, 0), (g3.G3_CTRL_BOTTOMUP, 0, 1, 2),
+                                   (g3.G3_CTRL_BOTTOMUP, 1, 2, 0)):
         for root in roots:
-            parent, level, _ = run_bfs(g, root, n, controller=ctrl, bu_reverse=rev)
+            parent, level, _ = run_bfs(g, root, n, controller=ctrl, bu_reverse=rev,
+                                       bu_kernel=kern, out_split=split)
             _, lref = oracle.bfs(off_o, col_o, root)
             assert np.array_equal(level, lref), (name, root, ctrl)
             assert oracle.validate(off_o, col_o, root, parent, level) == 0, (name, root, ctrl)
@@ -146,9 +153,15 @@ def _levels_new(ref, level_orig):
 @pytest.mark.parametrize("kw", [dict(), dict(controller=g3.G3_CTRL_TOPDOWN),
                                 dict(controller=g3.G3_CTRL_BOTTOMUP), dict(bu_reverse=0),
                                 dict(controller=g3.G3_CTRL_BOTTOMUP, bu_reverse=0),
-                                dict(t1=2, t2=4, t3=8), dict(alpha=64, beta=8)],
+                                dict(t1=2, t2=4, t3=8), dict(alpha=64, beta=8),
+                                dict(bu_kernel=1),
+                                dict(controller=g3.G3_CTRL_BOTTOMUP, bu_kernel=1, bu_reverse=0),
+                                dict(out_split=2), dict(out_split=1),
+                                dict(controller=g3.G3_CTRL_BOTTOMUP, bu_kernel=2)],
                          ids=["heuristic", "topdown", "bottomup", "forward_scan",
-                              "bottomup_forward", "tiny_bins", "alpha64_beta8"])
+                              "bottomup_forward", "tiny_bins", "alpha64_beta8", "word_pairs",
+                              "word_pairs_forward", "out_split", "out_one_pass",
+                              "bottomup_tiles_two_rows"])
 def test_bfs_kron16_all_roots(kron16, kw):
     K = kron16
     ref = K["ref"]
@@ -274,8 +287,8 @@ def test_kron22_permutation_and_levels():
     off_g, col_g = gpu_csr(g)
     assert np.array_equal(off_g, ref["off_r"]) and np.array_equal(col_g, ref["col_r"])
     roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), 64, seed=2)
-    for root in roots[:4].tolist():
-        parent, level, _ = run_bfs(g, root, n)
+    for i, root in enumerate(roots[:4].tolist()):
+        parent, level, _ = run_bfs(g, root, n, out_split=1 + i % 2, bu_kernel=i // 2)
         _, lref = oracle.bfs(ref["off"], ref["col"], root)
         assert np.array_equal(level, lref)
         assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
@@ -326,9 +339,9 @@ def test_deep_graph_beyond_graph_level_cap():
         g.free()
 
 
-@pytest.mark.parametrize("relabel", [True, False])
+@pytest.mark.parametrize("relabel,split", [(True, 1), (True, 2), (False, 0)])
 @pytest.mark.parametrize("ctrl", ["heuristic", "topdown", "bottomup"])
-def test_levels_past_the_packed_word(relabel, ctrl):
+def test_levels_past_the_packed_word(relabel, split, ctrl):
     # n = 2^26 leaves 6 level bits in the packed (parent, level) word, so
     # levels from 63 on come from the side table; a 300-vertex path spread
     # over the ID range, searched from its 101st vertex, reaches level 199
@@ -337,7 +350,7 @@ def test_levels_past_the_packed_word(relabel, ctrl):
     g = gpu_pipeline(ids[:-1], ids[1:], n, relabel)
     c = {"heuristic": g3.G3_CTRL_HEURISTIC, "topdown": g3.G3_CTRL_TOPDOWN,
          "bottomup": g3.G3_CTRL_BOTTOMUP}[ctrl]
-    parent, level, _ = run_bfs(g, int(ids[mid]), n, controller=c)
+    parent, level, _ = run_bfs(g, int(ids[mid]), n, controller=c, out_split=split)
     want = np.full(n, -1, np.int32)
     want[ids] = np.abs(np.arange(k) - mid)
     assert np.array_equal(level, want)

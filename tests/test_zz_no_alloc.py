@@ -38,6 +38,29 @@ def test_noalloc_matches_g3_bfs_on_two_calls_in_a_row():
     g.free()
 
 
+def test_noalloc_at_its_largest_size():
+    # n == G3_NOALLOC_MAX_N exactly: the visited bitmap and both queues of the
+    # static array are used to their full extent
+    n = g3.NOALLOC_MAX_N
+    scale = n.bit_length() - 1
+    src, dst = graphgen.kronecker_edges(scale, 16, seed=5)
+    g = g3.g3_build_csr(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
+    off, col = g.csr()
+    off_h, col_h = off.cpu().numpy(), col.cpu().numpy()
+    root = int(graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), 1, seed=6)[0])
+    p = torch.empty(n, dtype=torch.int32, device="cuda")
+    l = torch.empty(n, dtype=torch.int32, device="cuda")
+    g3.g3_bfs_noalloc(off, col, n, root, p, l)
+    p_ref = torch.empty(n, dtype=torch.int32, device="cuda")
+    l_ref = torch.empty(n, dtype=torch.int32, device="cuda")
+    g3.g3_bfs(g, root, p_ref, l_ref)
+    torch.cuda.synchronize()
+    lv, pv = l.cpu().numpy(), p.cpu().numpy()
+    assert np.array_equal(lv, l_ref.cpu().numpy())
+    assert oracle.validate(off_h, col_h, root, pv, lv) == 0
+    g.free()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     L = g3.lib()
     dummy = ctypes.c_void_p(16)  # never dereferenced: rejected on the host
