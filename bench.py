@@ -71,6 +71,10 @@ def parse_args():
                          "are the CPU baseline")
     ap.add_argument("--cpu-timeout", type=float, default=600.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--configs", type=int, default=1,
+                    help="kron at SCALE 26: also run the SCALE 22 RCM comparison, the "
+                         "Chung-Lu MS-BFS and the small-graph batch, each with an oracle "
+                         "spot check, and report them in the line")
     ap.add_argument("--host-bfs", type=int, default=1,
                     help="kron, with the oracle leg: also time the paper's multithreaded "
                          "hybrid BFS on the host cores")
@@ -416,6 +420,265 @@ def host_hybrid_leg(g, roots, m_r, gpu_level):
             "levels_equal_gpu": same, "per_root_ms_median": statistics.median(ts)}
 
 
+# ------------------------------------------ secondary configurations
+class Background:
+    """Runs fn() on a host thread (the oracle's C calls release the GIL);
+    result() waits and returns its value or {"error": ...}."""
+
+    def __init__(self, fn):
+        import threading
+        self.val = None
+        self.th = threading.Thread(target=self._run, args=(fn,), daemon=True)
+        self.th.start()
+
+    def _run(self, fn):
+        try:
+            self.val = fn()
+        except Exception as e:  # reported in the line, never fatal
+            self.val = {"error": repr(e)}
+
+    def result(self, timeout=1800.0):
+        self.th.join(timeout)
+        return self.val if not self.th.is_alive() else {"error": "timeout"}
+
+
+def _time_roots(g3, g, roots, parent, level, opts, flush, reps=2):
+    """Per-root device time of g3_bfs (the best of `reps` runs after one
+    warm-up pass), an L2 flush before each search."""
+    import torch
+    ev_s = torch.cuda.Event(enable_timing=True)
+    ev_e = torch.cuda.Event(enable_timing=True)
+    best = [float("inf")] * len(roots)
+    for rep in range(reps + 1):
+        for i, r in enumerate(roots):
+            flush.fill_(1)
+            ev_s.record()
+            g3.g3_bfs(g, r, parent, level, opts)
+            ev_e.record()
+            ev_e.synchronize()
+            if rep:
+                best[i] = min(best[i], ev_s.elapsed_time(ev_e))
+    return best
+
+
+def c2_leg(flush, scale=22, spot=2):
+    """Kronecker SCALE 22, 64 roots, the alpha = 14 / beta = 24 rule with the
+    library defaults, searched on the RCM-relabelled graph and on the graph
+    in its generated labelling (isolated vertices kept): the locality effect
+    of RCM (the paper's Table 5 / Fig. 5 comparison, on the GPU). Oracle
+    spot check: the permutation equals Algorithm 3's (orc_rcm) and `spot`
+    roots' levels are exact and parents valid on both graphs."""
+    import torch
+    import graphgen
+    import oracle
+    import paper_2012_10026_gb300 as g3
+    n = 1 << scale
+    src, dst = graphgen.kronecker_edges_dev(scale, 16, seed=1)
+    flags = graphgen.nonisolated_flags_dev(src, dst, n).cpu().numpy()
+    roots = graphgen.pick_roots(flags, 64, 2).tolist()
+
+    def orc():
+        hs, hd = graphgen.kronecker_edges(scale, 16, seed=1)
+        off, col = oracle.build_csr(hs, hd, n)
+        P, _ = oracle.rcm(off, col)
+        return off, col, P, [oracle.bfs(off, col, r)[1] for r in roots[:spot]]
+
+    bg = Background(orc)
+    cnt = torch.bincount(src.long(), minlength=n)
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    out, keep = {}, {}
+    for rcm in (1, 0):
+        g = g3.g3_build_csr(src, dst, n)
+        if rcm:
+            g3.g3_rcm_relabel(g)
+            keep["perm"] = g.perm()[0].cpu().numpy()
+        m_r = []
+        for i, r in enumerate(roots):
+            g3.g3_bfs(g, r, parent, level)
+            m_r.append(int(cnt[level >= 0].sum().item()))
+            if i < spot:
+                keep[(rcm, i)] = (parent.cpu().numpy(), level.cpu().numpy())
+        t = _time_roots(g3, g, roots, parent, level, g3.opts(), flush)
+        out["rcm" if rcm else "generated_labels"] = {
+            "value": harmonic_gteps(m_r, t), "unit": "GTEPS",
+            "per_root_ms_median": statistics.median(t)}
+        g.free()
+    del src, dst, cnt
+    o = bg.result()
+    if isinstance(o, dict):
+        out["parity"] = o
+        return out
+    off, col, P, lref = o
+    import numpy as np
+    lv_ok = sum(int(np.array_equal(keep[(rc, i)][1], lref[i])) for rc in (1, 0)
+                for i in range(spot))
+    pv_ok = sum(int(oracle.validate(off, col, roots[i], *keep[(rc, i)]) == 0)
+                for rc in (1, 0) for i in range(spot))
+    out["parity"] = {"roots_checked": 2 * spot, "level_exact": lv_ok, "parent_valid": pv_ok,
+                     "perm_exact": bool(np.array_equal(keep["perm"], P)),
+                     "ok": lv_ok == 2 * spot and pv_ok == 2 * spot and
+                     bool(np.array_equal(keep["perm"], P))}
+    out["workload"] = f"kronecker_scale{scale}_ef16_64roots_rule14_24_library_defaults"
+    return out
+
+
+def c3_leg(flush, tune_cache, log2n=24, nsrc=256, spot=2):
+    """Chung-Lu 2^24 (power law 2.1, mean degree 20, cap 2^16), RCM, 256
+    sources as 4 bit-sliced launches of 64: aggregate GTEPS, the roofline
+    fraction from the launches' own work counts, and an oracle spot check of
+    `spot` sources' levels."""
+    import numpy as np
+    import torch
+    import graphgen
+    import oracle
+    import paper_2012_10026_gb300 as g3
+    n = 1 << log2n
+    src, dst = graphgen.chunglu_edges_dev(n)
+    flags = graphgen.nonisolated_flags_dev(src, dst, n).cpu().numpy()
+    roots = graphgen.pick_roots(flags, nsrc, 2).tolist()
+
+    def orc():
+        hs, hd = graphgen.chunglu_edges(n)
+        off, col = oracle.build_csr(hs, hd, n)
+        return [oracle.bfs(off, col, r)[1] for r in roots[:spot]]
+
+    bg = Background(orc)
+    g = g3.g3_build_csr(src, dst, n)
+    g3.g3_rcm_relabel(g)
+    cnt = torch.bincount(src.long(), minlength=n)
+    del src, dst
+    batches = [roots[i:i + 64] for i in range(0, len(roots), 64)]
+    lv = torch.empty((64, n), dtype=torch.int8, device="cuda")
+    mopts, _ = g3.autotune_msbfs(g, batches[0], lv[:len(batches[0])], tune_cache or None)
+    m_s, spot_lv = [], []
+    for b in batches:
+        g3.g3_msbfs(g, b, lv[:len(b)], mopts)
+        for i in range(len(b)):
+            m_s.append(int(cnt[lv[i] >= 0].sum().item()))
+        if not spot_lv:
+            spot_lv = [lv[i].cpu().numpy() for i in range(spot)]
+    ev_s = torch.cuda.Event(enable_timing=True)
+    ev_e = torch.cuda.Event(enable_timing=True)
+    times, work = [], []
+    for rep in range(2):
+        for b in batches:
+            flush.fill_(1)
+            ev_s.record()
+            g3.g3_msbfs(g, b, lv[:len(b)], mopts)
+            ev_e.record()
+            ev_e.synchronize()
+            if rep:
+                times.append(ev_s.elapsed_time(ev_e))
+                work.append(g3.g3_msbfs_last_stats(g))
+    info = g.info
+    nb = info["n_bfs"]
+    comp = sum(8 * nb * w["pull_levels"] + 24 * w["pull_vertices"] + 12 * w["pull_entries"]
+               + 20 * w["push_entries"] + 64 * nb + 64 * n for w in work) / len(work)
+    avg_ms = sum(times) / len(times)
+    peak, _ = load_peaks()
+    g.free()
+    del lv, cnt
+    torch.cuda.empty_cache()
+    out = {"workload": f"chunglu_2^{log2n}_g2.1_d20_cap65536_rcm_{nsrc}sources_4x64",
+           "value": sum(m_s) / (sum(times) / 1e3) / 1e9, "unit": "GTEPS",
+           "ms_per_launch_median": statistics.median(times),
+           "roofline": {"achieved": comp / (avg_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": comp / (avg_ms / 1e3) / 1e9 / peak},
+           "push_alpha": mopts.push_alpha, "pull_warp_deg": mopts.pull_warp_deg}
+    o = bg.result()
+    if isinstance(o, dict):
+        out["parity"] = o
+        return out
+    ok = sum(int(np.array_equal(spot_lv[i], o[i].astype(np.int8))) for i in range(spot))
+    out["parity"] = {"sources_checked": spot, "level_exact": ok, "ok": ok == spot}
+    return out
+
+
+def c4_leg(flush, tune_cache, count=4096, spot=16):
+    """4096 Kronecker graphs (SCALE ~ U{8..14}, edge factor 16), each
+    RCM-relabelled with one root, packed and searched in one launch:
+    GTEPS = sum over graphs of m_g / launch time; oracle spot check of every
+    (count / spot)-th graph's levels and parents."""
+    import numpy as np
+    import torch
+    import graphgen
+    import oracle
+    import paper_2012_10026_gb300 as g3
+    specs = graphgen.small_graph_specs(count, seed=5)
+    graphs, roots_u, voff, srcs = [], [], [0], []
+    t0 = time.perf_counter()
+    for scale, gseed in specs:
+        n = 1 << scale
+        s, d = graphgen.kronecker_edges_dev(scale, 16, seed=gseed)
+        flags = graphgen.nonisolated_flags_dev(s, d, n).cpu().numpy()
+        r = int(graphgen.pick_roots(flags, 1, seed=gseed)[0])
+        g = g3.g3_build_csr(s, d, n)
+        g3.g3_rcm_relabel(g)
+        graphs.append(g)
+        roots_u.append(voff[-1] + r)
+        srcs.append(s.long() + voff[-1])
+        voff.append(voff[-1] + n)
+    b = g3.g3_batch_pack(graphs)
+    for g in graphs:
+        g.free()
+    setup_s = time.perf_counter() - t0
+    pick = list(range(0, count, max(1, count // spot)))[:spot]
+
+    def orc():
+        res = []
+        for i in pick:
+            sc, gs = specs[i]
+            hs, hd = graphgen.kronecker_edges(sc, 16, seed=gs)
+            off, col = oracle.build_csr(hs, hd, 1 << sc)
+            res.append((off, col, oracle.bfs(off, col, roots_u[i] - voff[i])[1]))
+        return res
+
+    bg = Background(orc)
+    N = voff[-1]
+    roots = torch.tensor(roots_u, dtype=torch.int32, device="cuda")
+    parent = torch.empty(N, dtype=torch.int32, device="cuda")
+    level = torch.empty(N, dtype=torch.int32, device="cuda")
+    o, _ = g3.autotune_batch(b, roots, parent, level, tune_cache or None)
+    g3.g3_bfs_batch(b, roots, parent, level, o)
+    src_all = torch.cat(srcs)
+    del srcs
+    m_total = int((level[src_all] >= 0).sum().item())
+    del src_all
+    ph, lh = parent.cpu().numpy(), level.cpu().numpy()
+    ev_s = torch.cuda.Event(enable_timing=True)
+    ev_e = torch.cuda.Event(enable_timing=True)
+    times = []
+    for rep in range(4):
+        flush.fill_(1)
+        ev_s.record()
+        g3.g3_bfs_batch(b, roots, parent, level, o, timed=False)
+        ev_e.record()
+        ev_e.synchronize()
+        if rep:
+            times.append(ev_s.elapsed_time(ev_e))
+    b.free()
+    out = {"workload": f"kronecker_batch{count}_scale8-14_ef16_rcm_1root",
+           "value": m_total / (statistics.median(times) / 1e3) / 1e9, "unit": "GTEPS",
+           "ms_per_launch_median": statistics.median(times), "graphs": count,
+           "mode": o.mode, "warp_max_n": o.warp_max_n, "setup_s": setup_s}
+    res = bg.result()
+    if isinstance(res, dict):
+        out["parity"] = res
+        return out
+    lv_ok = pv_ok = 0
+    for (off, col, lref), i in zip(res, pick):
+        a, e = voff[i], voff[i + 1]
+        # the batch reports union original IDs; shift back to the graph's own
+        pp = ph[a:e].copy()
+        pp[pp >= 0] -= a
+        lv_ok += int(np.array_equal(lh[a:e], lref))
+        pv_ok += int(oracle.validate(off, col, roots_u[i] - a, pp, lh[a:e]) == 0)
+    out["parity"] = {"graphs_checked": len(pick), "level_exact": lv_ok, "parent_valid": pv_ok,
+                     "ok": lv_ok == len(pick) and pv_ok == len(pick)}
+    return out
+
+
 def finish_oracle_leg(p, q, timeout):
     """Result of a spawned oracle process (None when it did not answer)."""
     try:
@@ -711,6 +974,23 @@ def gpu_arm(args, rank, world):
             prev = s["dir"]
     launches += graph_kernels * args.steps
 
+    # the other configurations of the workload family, each with its own
+    # oracle spot check (after the timed region; their oracle work runs on
+    # host threads while the GPU times them)
+    configs = None
+    if rank == 0 and args.configs and args.scale == 26:
+        configs = {}
+        for name, fn in (("c2_rcm_vs_generated_labels", lambda: c2_leg(flush)),
+                         ("c3_msbfs_chunglu", lambda: c3_leg(flush, args.tune_cache)),
+                         ("c4_batch_small_graphs", lambda: c4_leg(flush, args.tune_cache))):
+            t_leg = time.perf_counter()
+            try:
+                configs[name] = fn()
+            except Exception as e:  # reported, never fatal for the headline
+                configs[name] = {"error": repr(e)}
+            configs[name]["seconds"] = time.perf_counter() - t_leg
+            torch.cuda.empty_cache()
+
     # the oracle checks every root's result of the last timed step and the
     # permutation, on the host cores (before the end-to-end leg, whose host
     # wall time the busy cores would disturb)
@@ -785,6 +1065,7 @@ def gpu_arm(args, rank, world):
             "parity": parity_rec,
             "controller": controller_rec,
             "cpu_baseline": cpu, "cpu_baseline_parallel": host_par,
+            "configs": configs,
             "e2e": e2e, "gpu_launches": int(launches),
             "graph_launches": graph_launches,
             "instrumented_hm_gteps": harmonic_gteps([m_r[r] for r in roots], inst_t),

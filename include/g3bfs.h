@@ -162,16 +162,26 @@ typedef struct {
                                mlp_margin / 1000 (0, the default: always) */
   int32_t mlp_bins;         /* learned controller: 1 (default) the network also
                                picks the top-down bins; 0 t1..t3 stay */
-  int32_t out_split;        /* output pass (original IDs): 0 (default) and 1
-                               one pass; 2 two passes over label halves (each
+  int32_t out_split;        /* output pass (original IDs): 0 (default) one pass
+                               that starts at the first top-down level after a
+                               bottom-up one and runs beside the rest of the
+                               search (a second stream), followed by a pass
+                               that rewrites the vertices those last levels
+                               reached; 1 one pass after the search; 2 two
+                               passes after the search over label halves (each
                                gathers from half of the packed (parent, level)
                                array) when both outputs are device memory */
-  int32_t bu_kernel;        /* bottom-up kernel: 0 (default) word tiles -- a
-                               warp owns 32 bitmap words; dense tiles are
-                               worked lane by word, sparse ones as one compact
-                               list; four rows in flight per lane; 2 the same
-                               with two rows in flight; 1 word pairs -- a lane
-                               owns one vertex of each of two words */
+  int32_t bu_kernel;        /* bottom-up kernels: 0 (default) with bu_reverse,
+                               levels with at least a quarter of the graph
+                               unvisited run the staged kernel (each CTA's next
+                               tile of neighbors+ entries and visited words
+                               brought into shared memory by bulk copies while
+                               it works on the current one), the others the
+                               word-tile kernel; without bu_reverse, word
+                               pairs; 1 word pairs (a lane owns one vertex of
+                               each of two words) on every level; 2 word tiles
+                               (a warp owns 32 words; dense tiles lane by word,
+                               sparse ones as one compact list) on every level */
   int32_t reserved[3];
 } g3_bfs_opts;
 
@@ -229,7 +239,9 @@ typedef struct {
  * host instead and synchronises once per level (the controller's record is
  * read back). Searches deeper than 4096 levels continue on the host loop.
  * Errors: G3_EINVAL (root outside [0, n), null parent/level, learned
- * controller without parameters), G3_ENOMEM, G3_ECUDA. */
+ * controller without parameters), G3_ENOMEM, G3_ECUDA, G3_ETIMEOUT (a
+ * kernel's bounded wait for its staged data ran out; the search stopped and
+ * the outputs are not valid). */
 g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, int32_t* parent,
                  int32_t* level, g3_level_stats* stats, int32_t max_stats,
                  int32_t* n_levels, void* stream);
@@ -368,7 +380,8 @@ g3_status g3_tune_cache_store(const char* path, const g3_tune_entry* e);
  * in the caller's buffers. Synchronises.
  *   g3_autotune_bfs   : roots host (nroots original IDs), parent/level as for
  *                       g3_bfs; coordinate search, two passes, over alpha,
- *                       beta, (t1, t2, t3) and bu_reverse; the controller stays.
+ *                       beta, (t1, t2, t3), bu_reverse and bu_kernel (0 or 1);
+ *                       the controller stays.
  *   g3_autotune_msbfs : roots host (k <= 64), level as for g3_msbfs; full grid
  *                       over push_alpha x pull_warp_deg.
  *   g3_autotune_batch : roots/parent/level as for g3_bfs_batch; mode 0 with

@@ -77,6 +77,8 @@ struct Ctrl {
   int qsel, fsel, fmt_queue;
   int mode;  // MODE_* of the current level
   int cap;   // the controller ends the search at this level (graph launches)
+  unsigned int err;  // a kernel's bounded wait ran out (the search stops; G3_ETIMEOUT)
+  int tail_level;    // the first graph stopped at this level for the tail (-1: not)
 };
 
 // Per-level record written by the controller (and bfs_root for level 0).
@@ -148,10 +150,12 @@ struct g3_bfs_ws {
   LevelLog* log;
   cudaEvent_t ev[6];
   // resident-grid sizes (SMs x blocks per SM) per kernel
-  int grid_front, grid_bins, grid_bu, grid_tiles, grid_tiles2, grid_conv, grid_tr, grid_tr4;
+  int grid_front, grid_bins, grid_bu, grid_tiles, grid_staged, grid_conv, grid_tr, grid_tr4;
   // graph mode: instantiated level loop and the options it was built for
-  cudaGraphExec_t gexec;
+  cudaGraphExec_t gexec, gexec_tail;  // up to the tail; the tail (and full searches)
   g3_bfs_opts gopts;
+  cudaStream_t s_out;                  // the output pass that overlaps the tail
+  cudaEvent_t ev_fork, ev_out;
 };
 
 void g3_bfs_ws_free(g3_bfs_ws* ws) {
@@ -166,6 +170,10 @@ void g3_bfs_ws_free(g3_bfs_ws* ws) {
   for (int i = 0; i < 6; ++i)
     if (ws->ev[i]) cudaEventDestroy(ws->ev[i]);
   if (ws->gexec) cudaGraphExecDestroy(ws->gexec);
+  if (ws->gexec_tail) cudaGraphExecDestroy(ws->gexec_tail);
+  if (ws->ev_fork) cudaEventDestroy(ws->ev_fork);
+  if (ws->ev_out) cudaEventDestroy(ws->ev_out);
+  if (ws->s_out) cudaStreamDestroy(ws->s_out);
   free(ws);
 }
 
@@ -292,6 +300,7 @@ __global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, in
   int32_t r = new_of_old ? new_of_old[root] : root;
   memset(c, 0, sizeof(Ctrl));
   reset_next(c);
+  c->tail_level = -1;
   c->t1 = t1;
   c->t2 = t2;
   c->t3 = t3;
@@ -357,6 +366,7 @@ __global__ void __launch_bounds__(1024) bfs_roots_multi(
   if (threadIdx.x != 0) return;
   memset(c, 0, sizeof(Ctrl));
   reset_next(c);
+  c->tail_level = -1;
   c->t1 = t1;
   c->t2 = t2;
   c->t3 = t3;
@@ -400,38 +410,63 @@ __device__ __forceinline__ int32_t orig_of(const int32_t* o2n, int32_t v) {
 }
 
 // Per-warp staging of the next queue in shared memory: claimed vertices are
-// compacted into the warp's buffer with a ballot and written to the global
-// queue in one coalesced burst, reserving space with one atomic per ~224
-// vertices instead of one per warp step (the queue counter is a single
-// address that every warp of the grid would otherwise hit).
-#define WQ_CAP 256
-#define WQ_FLUSH (WQ_CAP - 32)
+// compacted into the warp's buffer with ballots and written to the global
+// queue in one coalesced burst, reserving space with one atomic per few
+// hundred vertices instead of one per warp step (the queue counter is a
+// single address that every warp of the grid would otherwise hit). The
+// statistics of the claimed vertices (degree sum, histogram, label range)
+// are taken at flush time, when the lanes load the degrees of up to 16
+// staged vertices each at once, instead of inside each claim's dependent
+// chain.
+#define WQ_CAP 512
+#define WQ_FLUSH (WQ_CAP - 128)
 struct WarpQueue {
   int32_t* buf;  // this warp's WQ_CAP-entry shared buffer
   int cnt;       // warp-uniform fill level
 };
 
-__device__ __forceinline__ void wq_flush(WarpQueue& q, int32_t* gq, unsigned long long* glen) {
+__device__ __forceinline__ void wq_flush(WarpQueue& q, const TdArgs& a, StatAcc& acc) {
   if (q.cnt == 0) return;
   const int lane = threadIdx.x & 31;
   unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(glen, (unsigned long long)q.cnt);
+  if (lane == 0) base = atomicAdd(&a.c->q_len, (unsigned long long)q.cnt);
   base = __shfl_sync(0xffffffffu, base, 0);
   __syncwarp();
-  for (int i = lane; i < q.cnt; i += 32) gq[base + i] = q.buf[i];
+  for (int k0 = 0; k0 < q.cnt; k0 += 256) {  // eight entries per lane at a time
+    int32_t w[8], d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = k0 + lane + 32 * k;
+      w[k] = i < q.cnt ? q.buf[i] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) d[k] = w[k] >= 0 ? (int32_t)(a.off[w[k] + 1] - a.off[w[k]]) : 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (w[k] >= 0) {
+        a.qnext[base + k0 + lane + 32 * k] = w[k];
+        acc.add_vertex(w[k], d[k]);
+      }
+  }
   __syncwarp();
   q.cnt = 0;
 }
 
-// All 32 lanes call it together.
-__device__ __forceinline__ void wq_push(WarpQueue& q, bool want, int32_t item, int32_t* gq,
-                                        unsigned long long* glen) {
-  const unsigned bal = __ballot_sync(0xffffffffu, want);
-  if (bal == 0) return;
-  if (want) q.buf[q.cnt + __popc(bal & g3_lanemask_lt())] = item;
-  q.cnt += __popc(bal);
+// Appends up to four items per lane (want[k]); all 32 lanes call it together.
+__device__ __forceinline__ void wq_push4(WarpQueue& q, const bool want[4], const int32_t item[4],
+                                         const TdArgs& a, StatAcc& acc) {
+  const unsigned lt = g3_lanemask_lt();
+  int at = q.cnt;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const unsigned bal = __ballot_sync(0xffffffffu, want[k]);
+    if (want[k]) q.buf[at + __popc(bal & lt)] = item[k];
+    at += __popc(bal);
+  }
+  if (at == q.cnt) return;
+  q.cnt = at;
   __syncwarp();
-  if (q.cnt > WQ_FLUSH) wq_flush(q, gq, glen);
+  if (q.cnt > WQ_FLUSH) wq_flush(q, a, acc);
 }
 
 #define WQ_DECLARE(q)                                      \
@@ -441,9 +476,8 @@ __device__ __forceinline__ void wq_push(WarpQueue& q, bool want, int32_t item, i
 // Claims up to four neighbours w[k] (has[k]) for v at once: the four
 // visited-word reads, then the atomicOr of those still clear, are issued
 // together so that a lane keeps four claims in flight instead of one
-// dependent read-atomic pair at a time. The winners write (parent, level),
-// record their statistics and are appended to the next queue. All 32 lanes
-// must call it together.
+// dependent read-atomic pair at a time. The winners write (parent, level)
+// and are appended to the next queue. All 32 lanes must call it together.
 __device__ __forceinline__ void td_visit4(const TdArgs& a, WarpQueue& q, StatAcc& acc,
                                           const bool has[4], const int32_t w[4], int32_t v) {
   uint32_t word[4];
@@ -459,17 +493,10 @@ __device__ __forceinline__ void td_visit4(const TdArgs& a, WarpQueue& q, StatAcc
   bool claim[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) claim[k] = cand[k] && !((old[k] >> (w[k] & 31)) & 1u);
-  int64_t dg[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) dg[k] = claim[k] ? a.off[w[k] + 1] - a.off[w[k]] : 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k)
-    if (claim[k]) {
-      pl_put(a.plo, w[k], v, a.lnext);  // v: the parent's original ID
-      acc.add_vertex(w[k], dg[k]);
-    }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) wq_push(q, claim[k], w[k], a.qnext, &a.c->q_len);
+    if (claim[k]) pl_put(a.plo, w[k], v, a.lnext);  // v: the parent's original ID
+  wq_push4(q, claim, w, a, acc);
 }
 
 // Processes row entries [b, e) of vertex v with `nthr` cooperating threads
@@ -549,14 +576,14 @@ __global__ void __launch_bounds__(256) td_front(const int64_t* __restrict__ off,
       td_visit4(a, wq, acc, has, w, vo);
     }
   }
-  wq_flush(wq, a.qnext, &c->q_len);
+  wq_flush(wq, a, acc);
   acc.flush(c);
 }
 
 // The three bins in one launch: warp per warp-bin vertex, CTA per CTA-bin
 // vertex, and the grid bin as one flattened edge range split evenly over all
 // warps of the grid (Algorithm 4's even split, applied to every hub at once).
-__global__ void __launch_bounds__(256, 5) td_bins(const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(256, 4) td_bins(const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
                                                uint32_t* visited, PlOut plo, Bufs B,
                                                const int32_t* __restrict__ bins,
@@ -604,11 +631,18 @@ __global__ void __launch_bounds__(256, 5) td_bins(const int64_t* __restrict__ of
       }
     }
   }
-  wq_flush(wq, a.qnext, &c->q_len);
+  wq_flush(wq, a, acc);
   acc.flush(c);
 }
 
 // -------------------------------------------------------------- bottom-up
+// Bottom-up levels where at least a quarter of the graph is unvisited run
+// bu_staged (in the degree-aware scan order); the others run the word-tile
+// kernel. Both kernels of a level's pair check the same condition.
+__device__ __forceinline__ bool bu_dense(const Ctrl* c, int32_t nb) {
+  return c->nu * 4 >= (long long)nb;
+}
+
 __device__ __forceinline__ bool in_frontier(const uint32_t* __restrict__ f, int32_t w) {
   return (__ldg(&f[w >> 5]) >> (w & 31)) & 1u;
 }
@@ -845,8 +879,9 @@ __device__ __forceinline__ void bu_round(const int32_t (&v)[U], bool (&found)[U]
 template <int REV, int U>
 __global__ void __launch_bounds__(32 * BU_WARPS, (U > 2 ? 4 : 5)) bu_tiles(
     int32_t nb, int64_t nwords, uint32_t* visited, Bufs B, const int64_t* __restrict__ off,
-    const int32_t* __restrict__ col, const int2* __restrict__ nplus, PlOut plo, Ctrl* c) {
-  if (c->dir != G3_DIR_BU) return;
+    const int32_t* __restrict__ col, const int2* __restrict__ nplus, PlOut plo, Ctrl* c,
+    int skip_dense) {
+  if (c->dir != G3_DIR_BU || (skip_dense && bu_dense(c, nb))) return;
   __shared__ uint16_t s_list[BU_WARPS][1024];
   __shared__ uint32_t s_next[BU_WARPS][32];
   const uint32_t* __restrict__ fcur = (c->fsel ? B.f[1] : B.f[0]);
@@ -941,10 +976,198 @@ __global__ void __launch_bounds__(32 * BU_WARPS, (U > 2 ? 4 : 5)) bu_tiles(
   acc.flush(c);
 }
 
-// The word-tile kernel for the options: bu_kernel 0 four rows in flight per
-// lane, 2 two rows (fewer registers, more resident warps).
-static void* bu_tiles_fn(int kernel, int rev) {
-  if (kernel == 2) return rev ? (void*)bu_tiles<1, 2> : (void*)bu_tiles<0, 2>;
+// ------------------------------------------- bottom-up, staged tiles
+// Asynchronous bulk copies (the TMA unit's cp.async.bulk) into shared
+// memory, completed on an mbarrier.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false when it did not
+// complete within `spins` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned spins) {
+  for (unsigned i = 0; i < spins; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+#define BS_TILE 1024  // vertices per staged tile (32 bitmap words)
+#define BS_THREADS 256
+#define BS_SPINS (1u << 22)
+
+// Dense bottom-up level with the streamed inputs staged in shared memory
+// (Algorithms 5 and 6). A CTA walks tiles of 1024 vertices; while it works
+// on one tile, the bulk-copy engine brings the next tile's neighbors+
+// entries (8 KB) and visited words (128 B) into the other of two shared
+// buffers, so the only loads left in the threads' dependent chains are the
+// frontier-bitmap probes, the parents' original IDs and the rows of missed
+// vertices. Warp w takes words 4w..4w+3 of the tile, one vertex per lane and
+// word: the first probes of its four vertices are issued together, hits set
+// their word's bits by ballot, and misses with more neighbours go to a
+// per-CTA list that all threads then scan (rest of the row, four entries per
+// step), so that a long row does not hold a whole warp. Each wait on a
+// tile's barrier is bounded; if one runs out the CTA flags the controller
+// record (the search stops with G3_ETIMEOUT), waits once more for the copy it
+// issued and returns.
+__global__ void __launch_bounds__(BS_THREADS, 4) bu_staged(
+    int32_t nb, int64_t nwords, uint32_t* visited, Bufs B, const int64_t* __restrict__ off,
+    const int32_t* __restrict__ col, const int2* __restrict__ nplus, PlOut plo, Ctrl* c) {
+  if (c->dir != G3_DIR_BU || !bu_dense(c, nb)) return;
+  __shared__ __align__(16) int2 s_np[2][BS_TILE];
+  __shared__ __align__(16) uint32_t s_vis[2][32];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_next[32];
+  __shared__ uint16_t s_pend[BS_TILE];
+  __shared__ unsigned s_npend;
+  const uint32_t* __restrict__ fcur = (c->fsel ? B.f[1] : B.f[0]);
+  uint32_t* __restrict__ fnext = (c->fsel ? B.f[0] : B.f[1]);
+  const int32_t lnext = c->level + 1;
+  const int32_t* __restrict__ o2n = B.o2n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t ntiles = (nwords + 31) >> 5;
+  StatAcc acc;
+  acc.init();
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // bulk copies of tile t into buffer b (sizes rounded up to 16 bytes; the
+  // workspace arrays have padding past their ends)
+  auto issue = [&](int64_t t, int b) {
+    const int64_t v0 = t * BS_TILE, w0 = t * 32;
+    const int64_t nv = min((int64_t)BS_TILE, (int64_t)nb - v0);
+    const int64_t nw = min((int64_t)32, nwords - w0);
+    const unsigned bnp = (unsigned)(((nv * 8) + 15) & ~15ll);
+    const unsigned bvis = (unsigned)(((nw * 4) + 15) & ~15ll);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&s_bar[b], bnp + bvis);
+    bulk_g2s(&s_np[b][0], nplus + v0, bnp, &s_bar[b]);
+    bulk_g2s(&s_vis[b][0], visited + w0, bvis, &s_bar[b]);
+  };
+  unsigned phases = 0u;  // bit b: parity of the next phase of buffer b
+  int64_t t = blockIdx.x;
+  if (tid == 0 && t < ntiles) issue(t, 0);
+  for (int k = 0; t < ntiles; ++k, t += gridDim.x) {
+    const int b = k & 1;
+    const int64_t tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) issue(tn, b ^ 1);
+    const bool ok = mbar_wait(&s_bar[b], (phases >> b) & 1u, BS_SPINS);
+    phases ^= 1u << b;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(&c->err, 1u);
+        if (tn < ntiles) mbar_wait(&s_bar[b ^ 1], (phases >> (b ^ 1)) & 1u, BS_SPINS);
+      }
+      return;
+    }
+    if (tid < 32) s_next[tid] = 0u;
+    if (tid == 0) s_npend = 0u;
+    __syncthreads();
+    // first probes: warp w, words 4w .. 4w+3 of the tile, all four issued
+    // before any is used
+    const int64_t wbase = t * 32;
+    bool cand[4], hit[4];
+    int32_t x[4], d[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int wi = warp * 4 + u;
+      const int64_t gw = wbase + wi;
+      const int64_t v = gw * 32 + lane;
+      cand[u] = gw < nwords && v < nb && !((s_vis[b][wi] >> lane) & 1u);
+      x[u] = -1;
+      d[u] = 0;
+      if (cand[u]) {
+        const int2 e = s_np[b][wi * 32 + lane];
+        x[u] = e.x;
+        d[u] = e.y;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) hit[u] = x[u] >= 0 && in_frontier(fcur, x[u]);
+    int32_t po[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) po[u] = hit[u] ? (o2n ? __ldg(&o2n[x[u]]) : x[u]) : 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int wi = warp * 4 + u;
+      const int32_t v = (int32_t)((wbase + wi) * 32 + lane);
+      if (cand[u] && d[u] > 0) acc.ex += 1u;
+      if (hit[u]) {
+        pl_put(plo, v, po[u], lnext);
+        acc.add_vertex(v, d[u]);
+      }
+      const bool miss = cand[u] && !hit[u] && d[u] > 1;
+      const unsigned mb = __ballot_sync(0xffffffffu, miss);
+      unsigned base = 0;
+      if (lane == 0 && mb) base = atomicAdd(&s_npend, (unsigned)__popc(mb));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (miss) s_pend[base + __popc(mb & g3_lanemask_lt())] = (uint16_t)(wi * 32 + lane);
+      const unsigned hb = __ballot_sync(0xffffffffu, hit[u]);
+      if (lane == 0) s_next[wi] = hb;
+    }
+    __syncthreads();
+    // the rest of the missed rows, spread over all threads of the CTA
+    const unsigned npend = s_npend;
+    for (unsigned j = tid; j < npend; j += BS_THREADS) {
+      const int rel = s_pend[j];
+      const int64_t v = t * BS_TILE + rel;
+      const int64_t e = off[v + 1];
+      const int32_t d = s_np[b][rel].y;
+      int64_t kk = 1;
+      const int32_t p = bu_scan_rest4<1>(col, fcur, e - d, e, kk);
+      acc.ex += (unsigned)(kk - 1);
+      if (p >= 0) {
+        pl_put(plo, (int32_t)v, o2n ? __ldg(&o2n[p]) : p, lnext);
+        acc.add_vertex((int32_t)v, d);
+        atomicOr(&s_next[rel >> 5], 1u << (rel & 31));
+      }
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const int64_t gw = wbase + tid;
+      if (gw < nwords) {
+        const uint32_t nw = s_next[tid];
+        fnext[gw] = nw;
+        if (nw) visited[gw] = s_vis[b][tid] | nw;
+      }
+    }
+    __syncthreads();  // buffer b and the shared lists are reused
+  }
+  acc.flush(c);
+}
+
+// The word-tile kernel in the scan order of the options.
+static void* bu_tiles_fn(int rev) {
   return rev ? (void*)bu_tiles<1, 4> : (void*)bu_tiles<0, 4>;
 }
 
@@ -1026,6 +1249,7 @@ struct CtrlArgs {
   LevelLog* log;
   int graph_mode;
   cudaGraphConditionalHandle h_loop;
+  int stop_at_tail;  // end the loop at the first top-down level after a bottom-up one
 };
 
 // After the expansion of level L: record where the produced frontier lives,
@@ -1034,12 +1258,13 @@ struct CtrlArgs {
 // also ends the loop (done, or the launch's level cap reached).
 __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
   __shared__ float feat[12];
-  __shared__ int decide, active;
+  __shared__ int decide, active, prev;
   const int lane = threadIdx.x;
   if (lane == 0) {
     active = c->mode != MODE_DONE && c->nf > 0;
     if (active) {
       const int prev_dir = c->dir;
+      prev = prev_dir;
       const bool was_td = prev_dir == G3_DIR_TD;
       const long long prev_nf = c->nf;
       const long long nf = was_td ? (long long)c->q_len : (long long)c->nx_nf;
@@ -1105,14 +1330,23 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
   if (lane == 0) {
     if (active) {
       c->dir = decide;
-      c->mode = mode_of(c);
+      c->mode = c->err ? MODE_DONE : mode_of(c);
       if (c->mode != MODE_DONE) log_frontier(A.log, c);
     }
     if (A.graph_mode) {
-      const bool go = c->mode != MODE_DONE && c->level < c->cap;
+      bool go = c->mode != MODE_DONE && c->level < c->cap;
+      if (go && active && A.stop_at_tail && prev == G3_DIR_BU && c->dir == G3_DIR_TD) {
+        c->tail_level = c->level;  // the tail runs in the second graph
+        go = false;
+      }
       cudaGraphSetConditional(A.h_loop, go ? 1u : 0u);
     }
   }
+}
+
+// Graph mode: opens the level loop when the search is not done yet.
+__global__ void bfs_gate(const Ctrl* c, cudaGraphConditionalHandle h_loop) {
+  cudaGraphSetConditional(h_loop, (c->mode != MODE_DONE && c->nf > 0) ? 1u : 0u);
 }
 
 // Graph mode: picks the SWITCH body of the level about to run.
@@ -1305,6 +1539,28 @@ __global__ void __launch_bounds__(256) bfs_translate_p2(int32_t n, int32_t root,
   }
 }
 
+// After a search whose tail (the levels after the first graph stopped at
+// tail_level) ran while the output pass was already reading the packed
+// words: rewrites parent[] and level[] of every vertex the tail reached
+// (level above tail_level), whose words the output pass may have read before
+// they were final. Everything else the output pass wrote is final. Streams
+// the packed words once; the rewrites are few.
+__global__ void bfs_patch_tail(int32_t nb, const int32_t* __restrict__ old_of_new,
+                               const uint32_t* __restrict__ visited, PlOut plo, const Ctrl* c,
+                               int32_t* parent, int32_t* level) {
+  const int32_t tl = c->tail_level;
+  if (tl < 0) return;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nb;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    if (!((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u)) continue;
+    const int2 t = pl_decode(plo, __ldcs(&plo.pl[x]), (int32_t)x);
+    if (t.y <= tl) continue;
+    const int32_t v = old_of_new ? __ldg(&old_of_new[x]) : (int32_t)x;
+    parent[v] = t.x;
+    level[v] = t.y;
+  }
+}
+
 __global__ void build_nplus(int32_t nb, const int64_t* __restrict__ off,
                             const int32_t* __restrict__ col, int2* nplus) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nb;
@@ -1383,6 +1639,13 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
       g3_bfs_ws_free(ws);
       return G3_ECUDA;
     }
+  if (cudaStreamCreateWithFlags(&ws->s_out, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ws->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ws->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    g3_bfs_ws_free(ws);
+    return G3_ECUDA;
+  }
   if (ws->nb > 0) {  // neighbors+ (Algorithm 6): last row entry and degree
     build_nplus<<<g3_grid_for(ws->nb, 256), 256>>>(ws->nb, g->off, g->col, ws->nplus);
     g3_count_launch();
@@ -1401,9 +1664,7 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
   ws->grid_tiles = resident_grid(bu_tiles<1, 4>, 32 * BU_WARPS);
   g0 = resident_grid(bu_tiles<0, 4>, 32 * BU_WARPS);
   if (g0 < ws->grid_tiles) ws->grid_tiles = g0;
-  ws->grid_tiles2 = resident_grid(bu_tiles<1, 2>, 32 * BU_WARPS);
-  g0 = resident_grid(bu_tiles<0, 2>, 32 * BU_WARPS);
-  if (g0 < ws->grid_tiles2) ws->grid_tiles2 = g0;
+  ws->grid_staged = resident_grid(bu_staged, BS_THREADS);
   ws->grid_conv = resident_grid(bitmap_to_q, 256);
   ws->grid_tr = resident_grid(bfs_translate, 256);
   ws->grid_tr4 = resident_grid(bfs_translate4, 256);
@@ -1452,7 +1713,22 @@ static CtrlArgs ctrl_args(const Launch& S, int graph_mode, cudaGraphConditionalH
                   S.o->alpha,   S.o->beta,       S.o->mlp_params,
                   S.o->mlp_margin * 1e-3f,       S.o->mlp_bins,   S.o->t1,
                   S.o->t2,      S.o->t3,         S.ws->log,
-                  graph_mode,   h_loop};
+                  graph_mode,   h_loop,          0};
+}
+
+// Which bottom-up kernels the options select: bu_kernel 0 (default) runs
+// the staged kernel on dense levels and the word-tile kernel on the others
+// when rows are scanned in the degree-aware order (word pairs in CSR order);
+// 1 word pairs; 2 word tiles on every level.
+static bool bu_uses_staged(const g3_bfs_opts& o) { return o.bu_kernel == 0 && o.bu_reverse; }
+static bool bu_uses_tiles(const g3_bfs_opts& o) {
+  return o.bu_kernel == 2 || bu_uses_staged(o);
+}
+static int bu_tiles_grid(const g3_bfs_ws* ws) {
+  return cap_grid((ws->nwords + 31) / 32, BU_WARPS, ws->grid_tiles);
+}
+static int bu_staged_grid(const g3_bfs_ws* ws) {
+  return cap_grid((ws->nwords + 31) / 32, 1, ws->grid_staged);
 }
 
 // Host-driven launch of the kernels of one level of the given mode. Every
@@ -1480,17 +1756,21 @@ static g3_status launch_level(const Launch& S, int mode, int64_t nf, cudaEvent_t
     td_bins<<<ws->grid_bins, 256, 0, s>>>(S.g->off, S.g->col, ws->visited, ws->plo, S.B,
                                           ws->bins, ws->goff, S.nb1, c);
     G3_CHECK_LAUNCH();
-  } else if (S.o->bu_kernel != 1) {
-    const int grid = cap_grid((ws->nwords + 31) / 32, BU_WARPS,
-                              S.o->bu_kernel == 2 ? ws->grid_tiles2 : ws->grid_tiles);
-    void* fn = bu_tiles_fn(S.o->bu_kernel, S.o->bu_reverse);
+  } else if (bu_uses_tiles(*S.o)) {
     int64_t nwords = ws->nwords;
     int32_t nb = ws->nb;
     const int64_t* off = S.g->off;
     const int32_t* col = S.g->col;
     Bufs B = S.B;
-    void* args[] = {&nb, &nwords, &ws->visited, &B, &off, &col, &ws->nplus, &ws->plo, &c};
-    G3_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(32 * BU_WARPS), args, 0, s));
+    int skip = bu_uses_staged(*S.o);
+    void* args[] = {&nb, &nwords, &ws->visited, &B, &off, &col, &ws->nplus, &ws->plo, &c, &skip};
+    if (skip) {
+      G3_TRY_CUDA(cudaLaunchKernel((void*)bu_staged, dim3(bu_staged_grid(ws)), dim3(BS_THREADS),
+                                   args, 0, s));
+      g3_count_launch();
+    }
+    G3_TRY_CUDA(cudaLaunchKernel(bu_tiles_fn(S.o->bu_reverse), dim3(bu_tiles_grid(ws)),
+                                 dim3(32 * BU_WARPS), args, 0, s));
     g3_count_launch();
   } else {
     const int grid = cap_grid(ws->nwords, 16, ws->grid_bu);
@@ -1536,46 +1816,49 @@ static bool same_opts(const g3_bfs_opts& a, const g3_bfs_opts& b) {
 // Builds the level loop: WHILE(h_loop) { bfs_select -> SWITCH(h_mode) {
 // TD_Q, TD_B, BU_B, BU_Q } -> bfs_control }. Kernel arguments are baked in;
 // everything that changes per search lives in the controller record.
-static g3_status build_graph(Launch& S) {
+static g3_status build_graph(Launch& S, int stop_at_tail, cudaGraphExec_t* out) {
   g3_bfs_ws* ws = S.ws;
   cudaGraph_t top = nullptr;
   g3_status st = G3_OK;
   G3_TRY_CUDA(cudaGraphCreate(&top, 0));
   cudaGraphConditionalHandle h_loop, h_mode;
-  cudaGraphNode_t wnode, sel, sw, ctl, n0, n1, n2;
+  cudaGraphNode_t gate, wnode, sel, sw, ctl, n0, n1, n2;
   cudaGraph_t body, br[4];
   Ctrl* c = ws->ctrl;
   int64_t nwords = ws->nwords;
   int32_t nb = ws->nb;
   int gconv = ws->grid_conv, gfront = ws->grid_front, gbins = ws->grid_bins;
-  const bool tiles = S.o->bu_kernel != 1;
-  int gbu = tiles ? cap_grid((ws->nwords + 31) / 32, BU_WARPS,
-                             S.o->bu_kernel == 2 ? ws->grid_tiles2 : ws->grid_tiles)
-                  : cap_grid(ws->nwords, 16, ws->grid_bu);
+  const bool tiles = bu_uses_tiles(*S.o), staged = bu_uses_staged(*S.o);
+  int gbu = tiles ? bu_tiles_grid(ws) : cap_grid(ws->nwords, 16, ws->grid_bu);
   const int bbu = tiles ? 32 * BU_WARPS : 256;
+  const int gst = bu_staged_grid(ws);
+  int skip = staged ? 1 : 0;
   int gclear = g3_grid_for(ws->nwords, 256), gq2b = g3_grid_for(ws->nb, 256);
   const int64_t* off = S.g->off;
   const int32_t* col = S.g->col;
-  void* bu_fn = tiles ? bu_tiles_fn(S.o->bu_kernel, S.o->bu_reverse)
+  void* bu_fn = tiles ? bu_tiles_fn(S.o->bu_reverse)
                       : (S.o->bu_reverse ? (void*)bu_pull<1> : (void*)bu_pull<0>);
   void* a_conv[] = {&S.B, &nwords, &c};
   void* a_clear[] = {&S.B, &nwords, &c};
   void* a_q2b[] = {&S.B, &c};
   void* a_td[] = {&off, &col, &ws->visited, &ws->plo, &S.B, &ws->bins, &ws->goff, &S.nb1, &c};
-  void* a_bu[] = {&nb, &nwords, &ws->visited, &S.B, &off, &col, &ws->nplus, &ws->plo, &c};
+  void* a_bu[] = {&nb, &nwords, &ws->visited, &S.B, &off, &col, &ws->nplus, &ws->plo, &c,
+                  &skip};
   CtrlArgs ca;
   void* a_ctl[] = {&c, &ca};
   void* a_sel[] = {&c, &h_mode};
+  void* a_gate[] = {&c, &h_loop};
   do {
-    if (cudaGraphConditionalHandleCreate(&h_loop, top, 1, cudaGraphCondAssignDefault) !=
+    if (cudaGraphConditionalHandleCreate(&h_loop, top, 0, cudaGraphCondAssignDefault) !=
         cudaSuccess) { st = G3_ECUDA; break; }
+    if ((st = add_kernel(top, &gate, nullptr, (void*)bfs_gate, 1, 1, a_gate)) != G3_OK) break;
     NodeParams wbuf;
     cudaGraphNodeParams& wp = wbuf.get();
     wp.type = cudaGraphNodeTypeConditional;
     wp.conditional.handle = h_loop;
     wp.conditional.type = cudaGraphCondTypeWhile;
     wp.conditional.size = 1;
-    if (cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp) != cudaSuccess) {
+    if (cudaGraphAddNode(&wnode, top, &gate, nullptr, 1, &wp) != cudaSuccess) {
       st = G3_ECUDA;
       break;
     }
@@ -1605,22 +1888,36 @@ static g3_status build_graph(Launch& S) {
     if ((st = add_kernel(br[MODE_TD_B], &n1, &n0, (void*)td_front, gfront, 256, a_td))) break;
     if ((st = add_kernel(br[MODE_TD_B], &n2, &n1, (void*)td_bins, gbins, 256, a_td))) break;
     // MODE_BU_B
-    if ((st = add_kernel(br[MODE_BU_B], &n0, nullptr, bu_fn, gbu, bbu, a_bu))) break;
+    if (staged) {
+      if ((st = add_kernel(br[MODE_BU_B], &n0, nullptr, (void*)bu_staged, gst, BS_THREADS,
+                           a_bu)))
+        break;
+      if ((st = add_kernel(br[MODE_BU_B], &n1, &n0, bu_fn, gbu, bbu, a_bu))) break;
+    } else if ((st = add_kernel(br[MODE_BU_B], &n0, nullptr, bu_fn, gbu, bbu, a_bu))) {
+      break;
+    }
     // MODE_BU_Q
     if ((st = add_kernel(br[MODE_BU_Q], &n0, nullptr, (void*)bm_clear, gclear, 256, a_clear)))
       break;
     if ((st = add_kernel(br[MODE_BU_Q], &n1, &n0, (void*)q_to_bitmap, gq2b, 256, a_q2b))) break;
-    if ((st = add_kernel(br[MODE_BU_Q], &n2, &n1, bu_fn, gbu, bbu, a_bu))) break;
+    if (staged) {
+      cudaGraphNode_t n3;
+      if ((st = add_kernel(br[MODE_BU_Q], &n2, &n1, (void*)bu_staged, gst, BS_THREADS, a_bu)))
+        break;
+      if ((st = add_kernel(br[MODE_BU_Q], &n3, &n2, bu_fn, gbu, bbu, a_bu))) break;
+    } else if ((st = add_kernel(br[MODE_BU_Q], &n2, &n1, bu_fn, gbu, bbu, a_bu))) {
+      break;
+    }
     ca = ctrl_args(S, 1, h_loop);
+    ca.stop_at_tail = stop_at_tail;
     if ((st = add_kernel(body, &ctl, &sw, (void*)bfs_control, 1, 32, a_ctl))) break;
     cudaGraphExec_t ex = nullptr;
     if (cudaGraphInstantiate(&ex, top, 0) != cudaSuccess) {
       st = G3_ECUDA;
       break;
     }
-    if (ws->gexec) cudaGraphExecDestroy(ws->gexec);
-    ws->gexec = ex;
-    ws->gopts = *S.o;
+    if (*out) cudaGraphExecDestroy(*out);
+    *out = ex;
   } while (0);
   if (st != G3_OK) {
     cudaError_t e = cudaGetLastError();
@@ -1746,19 +2043,19 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   const bool split_ok = aligned && g->relabelled && hbm_p && hbm_l && ws->plo.bits >= 4 &&
                         nb > 1;
   const bool split = split_ok && o->out_split == 2;
-  auto translate = [&]() -> g3_status {
+  auto translate = [&](cudaStream_t ts) -> g3_status {
     if (split) {
       const int grid = cap_grid((g->n + 3) / 4, 256, ws->grid_tr4);
-      bfs_translate_p1<<<grid, 256, 0, s>>>(g->n, nb, nb / 2, g->new_of_old, ws->visited,
-                                            ws->plo, (uint32_t*)op);
+      bfs_translate_p1<<<grid, 256, 0, ts>>>(g->n, nb, nb / 2, g->new_of_old, ws->visited,
+                                             ws->plo, (uint32_t*)op);
       G3_CHECK_LAUNCH();
-      bfs_translate_p2<<<grid, 256, 0, s>>>(g->n, root, ws->plo, op, ol);
+      bfs_translate_p2<<<grid, 256, 0, ts>>>(g->n, root, ws->plo, op, ol);
     } else if (aligned) {
-      bfs_translate4<<<cap_grid((g->n + 3) / 4, 256, ws->grid_tr4), 256, 0, s>>>(
+      bfs_translate4<<<cap_grid((g->n + 3) / 4, 256, ws->grid_tr4), 256, 0, ts>>>(
           g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op,
           ol);
     } else {  // outputs not 16-byte aligned
-      bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, s>>>(
+      bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, ts>>>(
           g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op,
           ol);
     }
@@ -1767,12 +2064,32 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   };
   bool translated = false;
   if (!host_driven) {
-    if (!ws->gexec || !same_opts(ws->gopts, *o)) G3_TRY(build_graph(S));
-    G3_TRY_CUDA(cudaGraphLaunch(ws->gexec, s));
-    // the output pass goes right behind the level loop, without waiting for
-    // the host to read the controller; it is repeated below in the rare case
-    // of a search deeper than one graph launch runs
-    G3_TRY(translate());
+    if (!ws->gexec || !ws->gexec_tail || !same_opts(ws->gopts, *o)) {
+      G3_TRY(build_graph(S, 1, &ws->gexec));
+      G3_TRY(build_graph(S, 0, &ws->gexec_tail));
+      ws->gopts = *o;
+    }
+    if (o->out_split == 0) {
+      // The first graph stops at the first top-down level after a bottom-up
+      // one. From there the output pass (on a second stream) and the tail of
+      // the search (the second graph) run together: the tail's small levels
+      // are latency-bound and the output pass is bandwidth-bound. The patch
+      // pass then rewrites the outputs of the vertices the tail reached.
+      G3_TRY_CUDA(cudaGraphLaunch(ws->gexec, s));
+      G3_TRY_CUDA(cudaEventRecord(ws->ev_fork, s));
+      G3_TRY_CUDA(cudaStreamWaitEvent(ws->s_out, ws->ev_fork, 0));
+      G3_TRY(translate(ws->s_out));
+      G3_TRY_CUDA(cudaEventRecord(ws->ev_out, ws->s_out));
+      G3_TRY_CUDA(cudaGraphLaunch(ws->gexec_tail, s));
+      G3_TRY_CUDA(cudaStreamWaitEvent(s, ws->ev_out, 0));
+      bfs_patch_tail<<<cap_grid(nb, 256, ws->grid_tr), 256, 0, s>>>(
+          nb, g->relabelled ? g->old_of_new : nullptr, ws->visited, ws->plo, ws->ctrl, op, ol);
+      G3_CHECK_LAUNCH();
+    } else {
+      // the whole search in the second graph, then the output pass
+      G3_TRY_CUDA(cudaGraphLaunch(ws->gexec_tail, s));
+      G3_TRY(translate(s));
+    }
     translated = true;
   }
   // Host-driven levels: everything in host-driven mode, and what a graph
@@ -1784,6 +2101,10 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
     if (host_driven && o->timing && L > 0 && stats && L - 1 < max_stats) {
       cudaEventElapsedTime(&stats[L - 1].ms, ws->ev[0], ws->ev[3]);
       cudaEventElapsedTime(&stats[L - 1].ms_expand, ws->ev[1], ws->ev[2]);
+    }
+    if (h->err) {
+      g3_set_error("g3_bfs: a bottom-up kernel's wait for its staged tile ran out");
+      return G3_ETIMEOUT;
     }
     if (h->mode == MODE_DONE) break;
     translated = false;
@@ -1801,7 +2122,7 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   const int32_t nrec = h->level;  // non-empty frontiers F_0 .. F_{nrec-1}
   if (n_levels) *n_levels = nrec;
 
-  if (!translated) G3_TRY(translate());
+  if (!translated) G3_TRY(translate(s));
   if (!dev_p)
     G3_TRY_CUDA(cudaMemcpyAsync(parent, op, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s));
   if (!dev_l)

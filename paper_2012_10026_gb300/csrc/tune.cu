@@ -212,7 +212,7 @@ void bfs_to_entry(const g3_bfs_opts& o, g3_tune_entry* e) {
   e->p[2] = o.t1;
   e->p[3] = o.t2;
   e->p[4] = o.t3;
-  e->p[5] = o.bu_reverse;
+  e->p[5] = o.bu_reverse | (o.bu_kernel << 1);  // scan order, bottom-up kernels
 }
 
 void entry_to_bfs(const g3_tune_entry& e, g3_bfs_opts* o) {
@@ -221,7 +221,8 @@ void entry_to_bfs(const g3_tune_entry& e, g3_bfs_opts* o) {
   o->t1 = e.p[2];
   o->t2 = e.p[3];
   o->t3 = e.p[4];
-  o->bu_reverse = e.p[5];
+  o->bu_reverse = e.p[5] & 1;
+  o->bu_kernel = e.p[5] >> 1;
 }
 
 }  // namespace
@@ -262,7 +263,7 @@ extern "C" g3_status g3_autotune_bfs(g3_graph* g, const int32_t* roots, int32_t 
   static const int32_t bins[][3] = {{32, 1024, 32768}, {16, 512, 16384}, {64, 2048, 65536},
                                     {32, 256, 8192},   {8, 256, 32768},   {32, 2048, 262144}};
   for (int pass = 0; pass < 2; ++pass) {
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 5; ++c) {
       const int count = c == 0 ? 9 : c == 1 ? 6 : c == 2 ? 6 : 2;
       for (int i = 0; i < count; ++i) {
         g3_bfs_opts o = best;
@@ -274,6 +275,7 @@ extern "C" g3_status g3_autotune_bfs(g3_graph* g, const int32_t* roots, int32_t 
           o.t3 = bins[i][2];
         }
         if (c == 3) o.bu_reverse = i;
+        if (c == 4) o.bu_kernel = i;  // staged + word tiles, or word pairs
         if (!memcmp(&o, &best, sizeof(o))) continue;
         float ms = 0.f;
         G3_TRY(time_bfs(g, roots, nroots, o, parent, level, fl, ev, s, &ms));

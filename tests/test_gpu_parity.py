@@ -161,7 +161,7 @@ def _levels_new(ref, level_orig):
                          ids=["heuristic", "topdown", "bottomup", "forward_scan",
                               "bottomup_forward", "tiny_bins", "alpha64_beta8", "word_pairs",
                               "word_pairs_forward", "out_split", "out_one_pass",
-                              "bottomup_tiles_two_rows"])
+                              "bottomup_tiles"])
 def test_bfs_kron16_all_roots(kron16, kw):
     K = kron16
     ref = K["ref"]
