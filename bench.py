@@ -80,10 +80,12 @@ def parse_args():
                          "hybrid BFS on the host cores")
     ap.add_argument("--bu-reverse", type=int, default=1,
                     help="bottom-up scans rows from the highest label (degree-aware order)")
-    ap.add_argument("--bu-kernel", type=int, default=0,
-                    help="bottom-up kernel: 0 word tiles (compact per-warp lists), 1 word pairs")
-    ap.add_argument("--out-split", type=int, default=0,
-                    help="output pass: 0 auto, 1 one pass, 2 two passes over label halves")
+    ap.add_argument("--bu-kernel", type=int, default=-1,
+                    help="bottom-up kernels: 0 word pairs, 1 staged + word tiles, 2 word "
+                         "tiles (-1: the autotuner's choice, else the library default)")
+    ap.add_argument("--out-split", type=int, default=-1,
+                    help="output pass: 1 one pass, 2 two passes over label halves (-1: the "
+                         "library default)")
     ap.add_argument("--stats-out", default="")
     ap.add_argument("--workload", choices=["kron", "msbfs", "batch"], default="kron",
                     help="kron: the single-root headline; msbfs: bit-sliced multi-source "
@@ -186,31 +188,6 @@ def level_bytes(st, nb):
     if st["dir"] == 1:
         return 4 * words + 8 * st["n_u"] + 8 * st["examined"] + 8 * st["n_next"] + 8 * words
     return 4 * st["n_f"] + 16 * st["n_f"] + 8 * st["m_f"] + 16 * st["n_next"]
-
-
-def measured_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu launch-list
-    summary, when the kernel source is unchanged since that capture (the
-    summary records the source file's sha256); else None."""
-    import hashlib
-    import re
-    path = os.path.join(ROOT, "profiles", "launches_bfs_kron26.md")
-    try:
-        text = open(path).read()
-    except OSError:
-        return None, "no committed capture"
-    m = re.search(r"traffic: kernel=(\S+) bytes_per_launch=(\d+) source=(\S+) "
-                  r"sha256=([0-9a-f]+)", text)
-    if not m or m.group(1) != kernel:
-        return None, "no capture of this kernel"
-    src = os.path.join(ROOT, m.group(3))
-    try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
-        return None, "source missing"
-    if sha != m.group(4):
-        return None, "kernel source changed since the capture"
-    return int(m.group(2)), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {path[len(ROOT)+1:]}"
 
 
 def _max_over_ranks(dist, x):
@@ -804,7 +781,9 @@ def gpu_arm(args, rank, world):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     # autotuned alpha/beta, bins and scan order for this graph-size class
     # (untimed; 16 tuning roots drawn apart from the timed ones; cached)
-    base = dict(bu_reverse=args.bu_reverse, bu_kernel=args.bu_kernel, out_split=args.out_split)
+    forced = {k: v for k, v in (("bu_kernel", args.bu_kernel), ("out_split", args.out_split))
+              if v >= 0}
+    base = dict(bu_reverse=args.bu_reverse, **forced)
     tune_rec, t_tune = None, 0.0
     if args.tune_bfs:
         t_tune = time.perf_counter()
@@ -813,8 +792,8 @@ def gpu_arm(args, rank, world):
                                           g3.opts(bu_reverse=args.bu_reverse))
         t_tune = time.perf_counter() - t_tune
         base = dict(alpha=topts.alpha, beta=topts.beta, t1=topts.t1, t2=topts.t2, t3=topts.t3,
-                    bu_reverse=topts.bu_reverse, bu_kernel=args.bu_kernel,
-                    out_split=args.out_split)
+                    bu_reverse=topts.bu_reverse, bu_kernel=topts.bu_kernel)
+        base.update(forced)
     kw = dict(controller=ctrl, **base)
     mlp_t, learned_note = None, None
     if ctrl == g3.G3_CTRL_LEARNED:
@@ -833,8 +812,7 @@ def gpu_arm(args, rank, world):
     # the plain method: the alpha/beta rule on the same tuned options, and
     # with the library defaults
     plain_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, **base)
-    default_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, bu_reverse=args.bu_reverse,
-                           bu_kernel=args.bu_kernel, out_split=args.out_split)
+    default_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, bu_reverse=args.bu_reverse, **forced)
 
     # m_r per root (bookkeeping, outside any timed region)
     m_r = {}
@@ -958,7 +936,10 @@ def gpu_arm(args, rank, world):
     dom = 1 if agg[1][1] >= agg[0][1] else 0
     peak, peak_kind = load_peaks()
     bytes_, tms, launches_dom = agg[dom]
-    traffic, traffic_src = measured_traffic("bu_pull" if dom == 1 else "td_bins")
+    # DRAM bytes of this build's kernels are measured on a small case
+    # (SCALE 24, one kernel, a few launches) and kept with the profiles; a
+    # DRAM-counter capture of the full workload is not taken
+    traffic, traffic_src = None, "not captured at this size; see the SCALE 24 profiles"
     achieved = bytes_ / (tms / 1e3) / 1e9 if tms > 0 else 0.0
     # kernels run inside the level-loop graphs (not host launches): per level
     # the body selector and the controller, plus the SWITCH body's kernels
@@ -1103,8 +1084,10 @@ def gpu_arm(args, rank, world):
 
 def learned_check(args, flush, reps=3):
     """Harmonic-mean GTEPS of the trained controller and of the alpha/beta
-    rule (library defaults for both) over 64 roots of a Kronecker graph of a
-    size the controller was trained on; per root the best of `reps` runs."""
+    rule over 64 roots of a Kronecker graph of a size the controller was
+    trained on; both on the autotuned options of that graph (alpha, beta,
+    bins, scan order and kernels from the autotuner, the controller's own
+    bins when its file says so); per root the best of `reps` runs."""
     import torch
     import graphgen
     import paper_2012_10026_gb300 as g3
@@ -1122,12 +1105,18 @@ def learned_check(args, flush, reps=3):
         g3.g3_bfs(g, r, parent, level)
         m_r.append(int((level[src.long()] >= 0).sum().item()))
     del src, dst
-    lo, params, note = controller_opts(args.mlp, g.info["n_bfs"])
+    troots = graphgen.pick_roots(flags, 16, args.root_seed + 1000).tolist()
+    topts, _ = g3.autotune_bfs(g, troots, parent, level, args.tune_cache or None,
+                               g3.opts(bu_reverse=args.bu_reverse))
+    base = dict(alpha=topts.alpha, beta=topts.beta, t1=topts.t1, t2=topts.t2, t3=topts.t3,
+                bu_reverse=topts.bu_reverse, bu_kernel=topts.bu_kernel)
+    lo, params, note = controller_opts(args.mlp, g.info["n_bfs"], **base)
+    rule = g3.opts(controller=g3.G3_CTRL_HEURISTIC, **base)
     ev_s = torch.cuda.Event(enable_timing=True)
     ev_e = torch.cuda.Event(enable_timing=True)
     out = {"workload": f"kronecker_scale{scale}_ef{args.edgefactor}_rcm_64roots",
-           "controller": note}
-    for name, o in (("learned", lo), ("rule", g3.opts())):
+           "controller": note, "options": "autotuned for this graph, the same for both"}
+    for name, o in (("learned", lo), ("rule", rule)):
         best = [float("inf")] * len(roots)
         for _ in range(reps + 1):  # the first pass builds the level-loop graph
             for i, r in enumerate(roots):

@@ -162,26 +162,22 @@ typedef struct {
                                mlp_margin / 1000 (0, the default: always) */
   int32_t mlp_bins;         /* learned controller: 1 (default) the network also
                                picks the top-down bins; 0 t1..t3 stay */
-  int32_t out_split;        /* output pass (original IDs): 0 (default) one pass
-                               that starts at the first top-down level after a
-                               bottom-up one and runs beside the rest of the
-                               search (a second stream), followed by a pass
-                               that rewrites the vertices those last levels
-                               reached; 1 one pass after the search; 2 two
-                               passes after the search over label halves (each
+  int32_t out_split;        /* output pass (original IDs): 0 (default) and 1
+                               one pass; 2 two passes over label halves (each
                                gathers from half of the packed (parent, level)
                                array) when both outputs are device memory */
-  int32_t bu_kernel;        /* bottom-up kernels: 0 (default) with bu_reverse,
-                               levels with at least a quarter of the graph
-                               unvisited run the staged kernel (each CTA's next
-                               tile of neighbors+ entries and visited words
-                               brought into shared memory by bulk copies while
-                               it works on the current one), the others the
-                               word-tile kernel; without bu_reverse, word
-                               pairs; 1 word pairs (a lane owns one vertex of
-                               each of two words) on every level; 2 word tiles
-                               (a warp owns 32 words; dense tiles lane by word,
-                               sparse ones as one compact list) on every level */
+  int32_t bu_kernel;        /* bottom-up kernels: 0 (default) word pairs -- a
+                               lane owns one vertex of each of two bitmap words
+                               -- on every level; 1 with bu_reverse, levels
+                               with at least a quarter of the graph unvisited
+                               run the staged kernel (each CTA's next tile of
+                               neighbors+ entries and visited words brought into
+                               shared memory by bulk copies while it works on
+                               the current one) and the others the word-tile
+                               kernel; without bu_reverse, word pairs; 2 word
+                               tiles (a warp owns 32 words; dense tiles lane by
+                               word, sparse ones as one compact list) on every
+                               level */
   int32_t reserved[3];
 } g3_bfs_opts;
 
@@ -429,10 +425,11 @@ g3_status g3_mlp_train(float* params, const float* x, const float* y, const floa
 
 /* Feature rows x (count x 12 floats, device) of the level records `stats`
  * (host array as g3_bfs returns them, consecutive records of one search in
- * order), computed by the same device code the controller uses. n_bfs is the
- * searched graph's vertex count. Synchronises `stream`. */
-g3_status g3_mlp_features(const g3_level_stats* stats, int32_t count, int32_t n_bfs, float* x,
-                          void* stream);
+ * order), computed by the same device code the controller uses. n_bfs and
+ * nnz are the searched graph's vertex and directed-entry counts (the
+ * features are ratios to them). Synchronises `stream`. */
+g3_status g3_mlp_features(const g3_level_stats* stats, int32_t count, int32_t n_bfs, int64_t nnz,
+                          float* x, void* stream);
 
 /* ------------------------------------------------------ test hooks */
 
@@ -445,8 +442,14 @@ g3_status g3_mlp_features(const g3_level_stats* stats, int32_t count, int32_t n_
  * G3_INJECT_RCM_ROUNDS: caps the rounds of component hooking in the RCM
  * relabel (default 4096); a relabel that needs more returns G3_ETIMEOUT and
  * leaves the graph not relabelled. value <= 0 restores the default.
- * Process-wide; not for concurrent use. Errors: G3_EINVAL (unknown kind). */
-enum { G3_INJECT_ALLOC = 1, G3_INJECT_RCM_ROUNDS = 2 };
+ * G3_INJECT_STAGED_STALL: the staged bottom-up kernel (bu_kernel 1) leaves
+ * out the bulk copies of each CTA's first tile and polls that tile's barrier
+ * only `value` times, so its bounded wait runs out: the search stops and
+ * g3_bfs returns G3_ETIMEOUT, with the device left usable. value <= 0 turns
+ * it off (the wait limit returns to its default).
+ * Process-wide; not for concurrent use. Errors: G3_EINVAL (unknown kind),
+ * G3_ECUDA. */
+enum { G3_INJECT_ALLOC = 1, G3_INJECT_RCM_ROUNDS = 2, G3_INJECT_STAGED_STALL = 3 };
 g3_status g3_debug_inject(int32_t kind, int64_t value);
 
 /* Bytes currently allocated from the current device's default memory pool

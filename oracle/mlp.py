@@ -9,10 +9,13 @@ Loss over a batch of B samples with per-output weights w_k:
     L = 1/(2B) * sum_b sum_k w_k (o_bk - y_bk)^2
 ReLU derivative is taken as 0 at z == 0.
 
-Features of a level (inputs), computed from the frontier statistics:
-    0 log2(1+n_f)   1 log2(1+m_f)   2 log2(1+n_u)   3 log2(1+m_u)
+Features of a level (inputs), computed from the frontier statistics as
+ratios of counts of the same graph (n vertices, nnz directed entries):
+    0 log2((1+n_f)/(1+n))    1 log2((1+m_f)/(1+nnz))
+    2 log2((1+n_u)/(1+n))    3 log2((1+m_u)/(1+nnz))
     4 (max_id - min_id) / n   (0 for an empty frontier)
-    5 log2((1+m_f)/(1+m_u))  6 log2(1+n) (graph size)  7 previous direction (0 TD, 1 BU)
+    5 log2((1+m_f)/(1+m_u))  6 log2((1+n) / (32 (1+m_f)))
+    7 previous direction (0 TD, 1 BU)
     8..11 fraction of frontier vertices with degree in
           [0,32), [32,1024), [1024,32768), [32768, inf)
 Outputs: o0 ~ ln(t_BU / t_TD) (bottom-up when o0 < 0), o1..o3 ~ log2 of the
@@ -95,12 +98,14 @@ def train_adam(p, x, y, steps: int, lr: float = 1e-2, w=None, beta1: float = 0.9
     return p, np.array(losses)
 
 
-def features(n_f, m_f, n_u, m_u, id_min, id_max, n, level, prev_dir, hist4):
+def features(n_f, m_f, n_u, m_u, id_min, id_max, n, nnz, prev_dir, hist4):
     """Feature vector of one level (see the module docstring)."""
     span = (id_max - id_min) / n if n_f > 0 and n > 0 else 0.0
     tot = max(n_f, 1)
     return np.array([
-        np.log2(1.0 + n_f), np.log2(1.0 + m_f), np.log2(1.0 + n_u), np.log2(1.0 + m_u),
-        span, np.log2((1.0 + m_f) / (1.0 + m_u)), np.log2(1.0 + n), float(prev_dir),
+        np.log2((1.0 + n_f) / (1.0 + n)), np.log2((1.0 + m_f) / (1.0 + nnz)),
+        np.log2((1.0 + n_u) / (1.0 + n)), np.log2((1.0 + m_u) / (1.0 + nnz)),
+        span, np.log2((1.0 + m_f) / (1.0 + m_u)), np.log2((1.0 + n) / (32.0 * (1.0 + m_f))),
+        float(prev_dir),
         hist4[0] / tot, hist4[1] / tot, hist4[2] / tot, hist4[3] / tot,
     ], dtype=np.float64)

@@ -155,12 +155,12 @@ _SIGS = {
     "g3_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_float, _vp, _vp]),
     "g3_mlp_features": (ctypes.c_int, [ctypes.POINTER(g3_level_stats), ctypes.c_int32,
-                                       ctypes.c_int32, _vp, _vp]),
+                                       ctypes.c_int32, ctypes.c_int64, _vp, _vp]),
     "g3_debug_inject": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
     "g3_debug_pool_used": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
 }
 NOALLOC_MAX_N = 1 << 20
-G3_INJECT_ALLOC, G3_INJECT_RCM_ROUNDS = 1, 2
+G3_INJECT_ALLOC, G3_INJECT_RCM_ROUNDS, G3_INJECT_STAGED_STALL = 1, 2, 3
 
 
 def lib():
@@ -476,8 +476,9 @@ def g3_mlp_train(params, x, y, steps: int, lr: float = 1e-2, w=None, stream=None
     return losses[:steps]
 
 
-def g3_mlp_features(stats, n_bfs: int, device="cuda", stream=None):
-    """Feature rows (len(stats) x 12) of level records (dicts from g3_bfs)."""
+def g3_mlp_features(stats, n_bfs: int, nnz: int, device="cuda", stream=None):
+    """Feature rows (len(stats) x 12) of level records (dicts from g3_bfs) of a
+    search on a graph of n_bfs vertices and nnz directed entries."""
     import torch
     arr = (g3_level_stats * max(len(stats), 1))()
     for i, d in enumerate(stats):
@@ -489,7 +490,8 @@ def g3_mlp_features(stats, n_bfs: int, device="cuda", stream=None):
             else:
                 setattr(arr[i], k, v)
     x = torch.empty((max(len(stats), 1), 12), dtype=torch.float32, device=device)
-    _check(lib().g3_mlp_features(arr, len(stats), int(n_bfs), _ptr(x), _stream(stream)),
+    _check(lib().g3_mlp_features(arr, len(stats), int(n_bfs), int(nnz), _ptr(x),
+                                 _stream(stream)),
            "g3_mlp_features")
     return x[:len(stats)]
 

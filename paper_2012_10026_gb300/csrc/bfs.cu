@@ -78,7 +78,7 @@ struct Ctrl {
   int mode;  // MODE_* of the current level
   int cap;   // the controller ends the search at this level (graph launches)
   unsigned int err;  // a kernel's bounded wait ran out (the search stops; G3_ETIMEOUT)
-  int tail_level;    // the first graph stopped at this level for the tail (-1: not)
+  int full_stats;    // keep the degree histogram and label range of each frontier
 };
 
 // Per-level record written by the controller (and bfs_root for level 0).
@@ -110,8 +110,8 @@ struct PlOut {
 // The packed words are stored with an L2 evict-last policy: the output pass
 // gathers them after the search, so they should outlive the streamed rows.
 __device__ __forceinline__ void st_keep_l2(uint32_t* a, uint32_t v) {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  uint64_t pol;  // a constant: not volatile, so the compiler creates it once
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol)
                : "memory");
 }
@@ -152,10 +152,8 @@ struct g3_bfs_ws {
   // resident-grid sizes (SMs x blocks per SM) per kernel
   int grid_front, grid_bins, grid_bu, grid_tiles, grid_staged, grid_conv, grid_tr, grid_tr4;
   // graph mode: instantiated level loop and the options it was built for
-  cudaGraphExec_t gexec, gexec_tail;  // up to the tail; the tail (and full searches)
+  cudaGraphExec_t gexec;
   g3_bfs_opts gopts;
-  cudaStream_t s_out;                  // the output pass that overlaps the tail
-  cudaEvent_t ev_fork, ev_out;
 };
 
 void g3_bfs_ws_free(g3_bfs_ws* ws) {
@@ -170,10 +168,6 @@ void g3_bfs_ws_free(g3_bfs_ws* ws) {
   for (int i = 0; i < 6; ++i)
     if (ws->ev[i]) cudaEventDestroy(ws->ev[i]);
   if (ws->gexec) cudaGraphExecDestroy(ws->gexec);
-  if (ws->gexec_tail) cudaGraphExecDestroy(ws->gexec_tail);
-  if (ws->ev_fork) cudaEventDestroy(ws->ev_fork);
-  if (ws->ev_out) cudaEventDestroy(ws->ev_out);
-  if (ws->s_out) cudaStreamDestroy(ws->s_out);
   free(ws);
 }
 
@@ -184,16 +178,22 @@ __device__ __forceinline__ int deg_bucket(int64_t d) {
 
 // Per-thread statistics in 32-bit registers (a thread sees far fewer than
 // 2^32 vertices or edges per launch); reduced per block in 64 bits.
+// The degree histogram and the label range are kept only when the search
+// records its per-level statistics or the learned controller reads them
+// (Ctrl::full_stats); the direction rule needs only sizes and degree sums.
 struct StatAcc {
   unsigned nf, mf, ex, h0, h1, h2, h3, mn, mx;
-  __device__ void init() {
+  bool full;
+  __device__ void init(const Ctrl* c) {
     nf = mf = ex = h0 = h1 = h2 = h3 = 0;
     mn = 0xFFFFFFFFu;
     mx = 0;
+    full = c->full_stats != 0;
   }
   __device__ void add_vertex(int32_t v, int64_t d) {
     nf++;
     mf += (unsigned)d;
+    if (!full) return;
     int b = deg_bucket(d);
     h0 += b == 0;
     h1 += b == 1;
@@ -296,11 +296,11 @@ __device__ __forceinline__ void log_frontier(LevelLog* log, const Ctrl* c) {
 // visited bitmap has been cleared on the stream before.
 __global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, int64_t nnz,
                          const int64_t* off, uint32_t* visited, PlOut plo, int32_t* q, Ctrl* c,
-                         LevelLog* log, int t1, int t2, int t3, int cap) {
+                         LevelLog* log, int t1, int t2, int t3, int cap, int full_stats) {
   int32_t r = new_of_old ? new_of_old[root] : root;
   memset(c, 0, sizeof(Ctrl));
   reset_next(c);
-  c->tail_level = -1;
+  c->full_stats = full_stats;
   c->t1 = t1;
   c->t2 = t2;
   c->t3 = t3;
@@ -337,7 +337,8 @@ __global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, in
 __global__ void __launch_bounds__(1024) bfs_roots_multi(
     const int32_t* __restrict__ roots, int32_t count, const int32_t* __restrict__ lo,
     const int32_t* new_of_old, int32_t nb, int64_t nnz, const int64_t* off, uint32_t* visited,
-    PlOut plo, int32_t* q, Ctrl* c, LevelLog* log, int t1, int t2, int t3, int cap) {
+    PlOut plo, int32_t* q, Ctrl* c, LevelLog* log, int t1, int t2, int t3, int cap,
+    int full_stats) {
   __shared__ unsigned long long s_nf, s_mf, s_hist[4];
   __shared__ int s_min, s_max;
   if (threadIdx.x == 0) {
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(1024) bfs_roots_multi(
   if (threadIdx.x != 0) return;
   memset(c, 0, sizeof(Ctrl));
   reset_next(c);
-  c->tail_level = -1;
+  c->full_stats = full_stats;
   c->t1 = t1;
   c->t2 = t2;
   c->t3 = t3;
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(256) td_front(const int64_t* __restrict__ off,
   const int t1 = c->t1, t2 = c->t2, t3 = c->t3;
   WQ_DECLARE(wq);
   StatAcc acc;
-  acc.init();
+  acc.init(c);
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < qlen;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
@@ -596,7 +597,7 @@ __global__ void __launch_bounds__(256, 4) td_bins(const int64_t* __restrict__ of
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   WQ_DECLARE(wq);
   StatAcc acc;
-  acc.init();
+  acc.init(c);
   const int64_t len1 = (int64_t)c->bin_len[1];
   for (int64_t i = gw; i < len1; i += nwarps) {
     int32_t v = bins[i];
@@ -674,15 +675,17 @@ __global__ void __launch_bounds__(256, 6) bu_pull(int32_t nb, int64_t nwords, ui
   const int32_t lnext = c->level + 1;
   const int32_t* __restrict__ o2n = B.o2n;
   StatAcc acc;
-  acc.init();
+  acc.init(c);
   const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  for (int64_t w0 = 2 * wid; w0 < nwords; w0 += 2 * nwarps) {
-    const bool has1 = w0 + 1 < nwords;
+  // word and vertex indices fit 32 bits (nb < 2^31); row offsets stay 64-bit
+  const int32_t nw = (int32_t)nwords;
+  const int32_t nwarps = (int32_t)(((int64_t)gridDim.x * blockDim.x) >> 5);
+  const int32_t wid = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  for (int32_t w0 = 2 * wid; w0 < nw; w0 += 2 * nwarps) {
+    const bool has1 = w0 + 1 < nw;
     const uint32_t vis0 = visited[w0];
     const uint32_t vis1 = has1 ? visited[w0 + 1] : 0xFFFFFFFFu;
-    const int64_t v0 = w0 * 32 + lane, v1 = v0 + 32;
+    const int32_t v0 = w0 * 32 + lane, v1 = v0 + 32;
     const bool c0 = v0 < nb && !((vis0 >> lane) & 1u);
     const bool c1 = v1 < nb && !((vis1 >> lane) & 1u);
     if (!__any_sync(0xffffffffu, c0 || c1)) {
@@ -741,15 +744,17 @@ __global__ void __launch_bounds__(256, 6) bu_pull(int32_t nb, int64_t nwords, ui
       p1 = bu_scan_rest<REV>(col, fcur, b1, e1, k1);
     }
     acc.ex += (unsigned)(k0 + k1);
+    const int32_t q0 = p0 >= 0 && o2n ? __ldg(&o2n[p0]) : p0;
+    const int32_t q1 = p1 >= 0 && o2n ? __ldg(&o2n[p1]) : p1;
     const uint32_t n0 = __ballot_sync(0xffffffffu, p0 >= 0);
     const uint32_t n1 = __ballot_sync(0xffffffffu, p1 >= 0);
     if (p0 >= 0) {
-      pl_put(plo, (int32_t)v0, o2n ? __ldg(&o2n[p0]) : p0, lnext);
-      acc.add_vertex((int32_t)v0, d0);
+      pl_put(plo, v0, q0, lnext);
+      acc.add_vertex(v0, d0);
     }
     if (p1 >= 0) {
-      pl_put(plo, (int32_t)v1, o2n ? __ldg(&o2n[p1]) : p1, lnext);
-      acc.add_vertex((int32_t)v1, d1);
+      pl_put(plo, v1, q1, lnext);
+      acc.add_vertex(v1, d1);
     }
     if (lane == 0) {
       fnext[w0] = n0;
@@ -889,7 +894,7 @@ __global__ void __launch_bounds__(32 * BU_WARPS, (U > 2 ? 4 : 5)) bu_tiles(
   const int32_t lnext = c->level + 1;
   const int32_t* __restrict__ o2n = B.o2n;
   StatAcc acc;
-  acc.init();
+  acc.init(c);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   uint16_t* list = s_list[wib];
   uint32_t* nx = s_next[wib];
@@ -1023,6 +1028,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsign
 #define BS_THREADS 256
 #define BS_SPINS (1u << 22)
 
+// Test hook (g3_debug_inject, G3_INJECT_STAGED_STALL): when positive, the
+// staged kernel leaves out the bulk copies of each CTA's first tile, so that
+// its bounded wait on that tile's barrier runs out after this many polls.
+__device__ int g3_dbg_staged_stall;
+
+g3_status g3_bfs_set_staged_stall(int spins) {
+  G3_TRY_CUDA(cudaMemcpyToSymbol(g3_dbg_staged_stall, &spins, sizeof(int)));
+  return G3_OK;
+}
+
 // Dense bottom-up level with the streamed inputs staged in shared memory
 // (Algorithms 5 and 6). A CTA walks tiles of 1024 vertices; while it works
 // on one tile, the bulk-copy engine brings the next tile's neighbors+
@@ -1054,7 +1069,7 @@ __global__ void __launch_bounds__(BS_THREADS, 4) bu_staged(
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t ntiles = (nwords + 31) >> 5;
   StatAcc acc;
-  acc.init();
+  acc.init(c);
   if (tid == 0) {
     mbar_init(&s_bar[0], 1);
     mbar_init(&s_bar[1], 1);
@@ -1074,18 +1089,27 @@ __global__ void __launch_bounds__(BS_THREADS, 4) bu_staged(
     bulk_g2s(&s_np[b][0], nplus + v0, bnp, &s_bar[b]);
     bulk_g2s(&s_vis[b][0], visited + w0, bvis, &s_bar[b]);
   };
+  const int stall = g3_dbg_staged_stall;
+  const unsigned spins = stall > 0 ? (unsigned)stall : BS_SPINS;
   unsigned phases = 0u;  // bit b: parity of the next phase of buffer b
   int64_t t = blockIdx.x;
-  if (tid == 0 && t < ntiles) issue(t, 0);
+  if (tid == 0 && t < ntiles) {
+    if (stall > 0) {
+      mbar_expect_tx(&s_bar[0], 16);  // armed, but nothing will arrive
+    } else {
+      issue(t, 0);
+    }
+  }
   for (int k = 0; t < ntiles; ++k, t += gridDim.x) {
     const int b = k & 1;
     const int64_t tn = t + gridDim.x;
     if (tid == 0 && tn < ntiles) issue(tn, b ^ 1);
-    const bool ok = mbar_wait(&s_bar[b], (phases >> b) & 1u, BS_SPINS);
+    const bool ok = mbar_wait(&s_bar[b], (phases >> b) & 1u, spins);
     phases ^= 1u << b;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(&c->err, 1u);
+        // the copy of the next tile is in flight: wait for it (bounded)
         if (tn < ntiles) mbar_wait(&s_bar[b ^ 1], (phases >> (b ^ 1)) & 1u, BS_SPINS);
       }
       return;
@@ -1228,8 +1252,8 @@ __global__ void bitmap_to_q(Bufs B, int64_t nwords, Ctrl* c) {
 
 // ------------------------------------------------------------- controller
 // Learned controller: the 12-32-4 MLP of g3_mlp.cuh on the frontier record.
-__device__ void mlp_features(const Ctrl* c, int32_t nb, int prev_dir, float* f) {
-  mlp_features_raw(c->nf, c->mf, c->nu, c->mu, c->id_min, c->id_max, nb, prev_dir,
+__device__ void mlp_features(const Ctrl* c, int32_t nb, long long nnz, int prev_dir, float* f) {
+  mlp_features_raw(c->nf, c->mf, c->nu, c->mu, c->id_min, c->id_max, nb, nnz, prev_dir,
                    c->hist, f);
 }
 
@@ -1249,7 +1273,6 @@ struct CtrlArgs {
   LevelLog* log;
   int graph_mode;
   cudaGraphConditionalHandle h_loop;
-  int stop_at_tail;  // end the loop at the first top-down level after a bottom-up one
 };
 
 // After the expansion of level L: record where the produced frontier lives,
@@ -1258,13 +1281,12 @@ struct CtrlArgs {
 // also ends the loop (done, or the launch's level cap reached).
 __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
   __shared__ float feat[12];
-  __shared__ int decide, active, prev;
+  __shared__ int decide, active;
   const int lane = threadIdx.x;
   if (lane == 0) {
     active = c->mode != MODE_DONE && c->nf > 0;
     if (active) {
       const int prev_dir = c->dir;
-      prev = prev_dir;
       const bool was_td = prev_dir == G3_DIR_TD;
       const long long prev_nf = c->nf;
       const long long nf = was_td ? (long long)c->q_len : (long long)c->nx_nf;
@@ -1303,7 +1325,7 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
       c->t2 = A.t2;
       c->t3 = A.t3;
       decide = d;
-      if (A.controller == G3_CTRL_LEARNED) mlp_features(c, A.nb, prev_dir, feat);
+      if (A.controller == G3_CTRL_LEARNED) mlp_features(c, A.nb, A.nnz, prev_dir, feat);
       reset_next(c);
     }
   }
@@ -1334,19 +1356,10 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
       if (c->mode != MODE_DONE) log_frontier(A.log, c);
     }
     if (A.graph_mode) {
-      bool go = c->mode != MODE_DONE && c->level < c->cap;
-      if (go && active && A.stop_at_tail && prev == G3_DIR_BU && c->dir == G3_DIR_TD) {
-        c->tail_level = c->level;  // the tail runs in the second graph
-        go = false;
-      }
+      const bool go = c->mode != MODE_DONE && c->level < c->cap;
       cudaGraphSetConditional(A.h_loop, go ? 1u : 0u);
     }
   }
-}
-
-// Graph mode: opens the level loop when the search is not done yet.
-__global__ void bfs_gate(const Ctrl* c, cudaGraphConditionalHandle h_loop) {
-  cudaGraphSetConditional(h_loop, (c->mode != MODE_DONE && c->nf > 0) ? 1u : 0u);
 }
 
 // Graph mode: picks the SWITCH body of the level about to run.
@@ -1539,28 +1552,6 @@ __global__ void __launch_bounds__(256) bfs_translate_p2(int32_t n, int32_t root,
   }
 }
 
-// After a search whose tail (the levels after the first graph stopped at
-// tail_level) ran while the output pass was already reading the packed
-// words: rewrites parent[] and level[] of every vertex the tail reached
-// (level above tail_level), whose words the output pass may have read before
-// they were final. Everything else the output pass wrote is final. Streams
-// the packed words once; the rewrites are few.
-__global__ void bfs_patch_tail(int32_t nb, const int32_t* __restrict__ old_of_new,
-                               const uint32_t* __restrict__ visited, PlOut plo, const Ctrl* c,
-                               int32_t* parent, int32_t* level) {
-  const int32_t tl = c->tail_level;
-  if (tl < 0) return;
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nb;
-       x += (int64_t)gridDim.x * blockDim.x) {
-    if (!((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u)) continue;
-    const int2 t = pl_decode(plo, __ldcs(&plo.pl[x]), (int32_t)x);
-    if (t.y <= tl) continue;
-    const int32_t v = old_of_new ? __ldg(&old_of_new[x]) : (int32_t)x;
-    parent[v] = t.x;
-    level[v] = t.y;
-  }
-}
-
 __global__ void build_nplus(int32_t nb, const int64_t* __restrict__ off,
                             const int32_t* __restrict__ col, int2* nplus) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nb;
@@ -1639,13 +1630,6 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
       g3_bfs_ws_free(ws);
       return G3_ECUDA;
     }
-  if (cudaStreamCreateWithFlags(&ws->s_out, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ws->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ws->ev_out, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    g3_bfs_ws_free(ws);
-    return G3_ECUDA;
-  }
   if (ws->nb > 0) {  // neighbors+ (Algorithm 6): last row entry and degree
     build_nplus<<<g3_grid_for(ws->nb, 256), 256>>>(ws->nb, g->off, g->col, ws->nplus);
     g3_count_launch();
@@ -1713,14 +1697,14 @@ static CtrlArgs ctrl_args(const Launch& S, int graph_mode, cudaGraphConditionalH
                   S.o->alpha,   S.o->beta,       S.o->mlp_params,
                   S.o->mlp_margin * 1e-3f,       S.o->mlp_bins,   S.o->t1,
                   S.o->t2,      S.o->t3,         S.ws->log,
-                  graph_mode,   h_loop,          0};
+                  graph_mode,   h_loop};
 }
 
-// Which bottom-up kernels the options select: bu_kernel 0 (default) runs
-// the staged kernel on dense levels and the word-tile kernel on the others
-// when rows are scanned in the degree-aware order (word pairs in CSR order);
-// 1 word pairs; 2 word tiles on every level.
-static bool bu_uses_staged(const g3_bfs_opts& o) { return o.bu_kernel == 0 && o.bu_reverse; }
+// Which bottom-up kernels the options select: bu_kernel 0 (default) word
+// pairs on every level; 1 the staged kernel on dense levels and the
+// word-tile kernel on the others when rows are scanned in the degree-aware
+// order (word pairs in CSR order); 2 word tiles on every level.
+static bool bu_uses_staged(const g3_bfs_opts& o) { return o.bu_kernel == 1 && o.bu_reverse; }
 static bool bu_uses_tiles(const g3_bfs_opts& o) {
   return o.bu_kernel == 2 || bu_uses_staged(o);
 }
@@ -1816,13 +1800,13 @@ static bool same_opts(const g3_bfs_opts& a, const g3_bfs_opts& b) {
 // Builds the level loop: WHILE(h_loop) { bfs_select -> SWITCH(h_mode) {
 // TD_Q, TD_B, BU_B, BU_Q } -> bfs_control }. Kernel arguments are baked in;
 // everything that changes per search lives in the controller record.
-static g3_status build_graph(Launch& S, int stop_at_tail, cudaGraphExec_t* out) {
+static g3_status build_graph(Launch& S) {
   g3_bfs_ws* ws = S.ws;
   cudaGraph_t top = nullptr;
   g3_status st = G3_OK;
   G3_TRY_CUDA(cudaGraphCreate(&top, 0));
   cudaGraphConditionalHandle h_loop, h_mode;
-  cudaGraphNode_t gate, wnode, sel, sw, ctl, n0, n1, n2;
+  cudaGraphNode_t wnode, sel, sw, ctl, n0, n1, n2;
   cudaGraph_t body, br[4];
   Ctrl* c = ws->ctrl;
   int64_t nwords = ws->nwords;
@@ -1847,18 +1831,16 @@ static g3_status build_graph(Launch& S, int stop_at_tail, cudaGraphExec_t* out) 
   CtrlArgs ca;
   void* a_ctl[] = {&c, &ca};
   void* a_sel[] = {&c, &h_mode};
-  void* a_gate[] = {&c, &h_loop};
   do {
-    if (cudaGraphConditionalHandleCreate(&h_loop, top, 0, cudaGraphCondAssignDefault) !=
+    if (cudaGraphConditionalHandleCreate(&h_loop, top, 1, cudaGraphCondAssignDefault) !=
         cudaSuccess) { st = G3_ECUDA; break; }
-    if ((st = add_kernel(top, &gate, nullptr, (void*)bfs_gate, 1, 1, a_gate)) != G3_OK) break;
     NodeParams wbuf;
     cudaGraphNodeParams& wp = wbuf.get();
     wp.type = cudaGraphNodeTypeConditional;
     wp.conditional.handle = h_loop;
     wp.conditional.type = cudaGraphCondTypeWhile;
     wp.conditional.size = 1;
-    if (cudaGraphAddNode(&wnode, top, &gate, nullptr, 1, &wp) != cudaSuccess) {
+    if (cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp) != cudaSuccess) {
       st = G3_ECUDA;
       break;
     }
@@ -1909,15 +1891,15 @@ static g3_status build_graph(Launch& S, int stop_at_tail, cudaGraphExec_t* out) 
       break;
     }
     ca = ctrl_args(S, 1, h_loop);
-    ca.stop_at_tail = stop_at_tail;
     if ((st = add_kernel(body, &ctl, &sw, (void*)bfs_control, 1, 32, a_ctl))) break;
     cudaGraphExec_t ex = nullptr;
     if (cudaGraphInstantiate(&ex, top, 0) != cudaSuccess) {
       st = G3_ECUDA;
       break;
     }
-    if (*out) cudaGraphExecDestroy(*out);
-    *out = ex;
+    if (ws->gexec) cudaGraphExecDestroy(ws->gexec);
+    ws->gexec = ex;
+    ws->gopts = *S.o;
   } while (0);
   if (st != G3_OK) {
     cudaError_t e = cudaGetLastError();
@@ -2018,16 +2000,18 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
 
   G3_TRY_CUDA(cudaMemsetAsync(ws->visited, 0, (size_t)(ws->nwords + 1) * 4, s));
   const int cap = host_driven ? 0x7fffffff : GRAPH_LEVEL_CAP;
+  const int full_stats = o->controller == G3_CTRL_LEARNED || o->record_both ||
+                         (stats && max_stats > 0);
   if (mr) {
     bfs_roots_multi<<<1, 1024, 0, s>>>(mr->roots, mr->count, mr->lo,
                                        g->relabelled ? g->new_of_old : nullptr, nb, g->nnz,
                                        g->off, ws->visited, ws->plo, ws->qa, ws->ctrl, ws->log,
-                                       o->t1, o->t2, o->t3, cap);
+                                       o->t1, o->t2, o->t3, cap, full_stats);
     root = -1;  // the output pass has no single root to patch
   } else {
     bfs_root<<<1, 1, 0, s>>>(g->relabelled ? g->new_of_old : nullptr, root, nb, g->nnz, g->off,
                              ws->visited, ws->plo, ws->qa, ws->ctrl, ws->log, o->t1, o->t2,
-                             o->t3, cap);
+                             o->t3, cap, full_stats);
   }
   G3_CHECK_LAUNCH();
 
@@ -2064,32 +2048,12 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   };
   bool translated = false;
   if (!host_driven) {
-    if (!ws->gexec || !ws->gexec_tail || !same_opts(ws->gopts, *o)) {
-      G3_TRY(build_graph(S, 1, &ws->gexec));
-      G3_TRY(build_graph(S, 0, &ws->gexec_tail));
-      ws->gopts = *o;
-    }
-    if (o->out_split == 0) {
-      // The first graph stops at the first top-down level after a bottom-up
-      // one. From there the output pass (on a second stream) and the tail of
-      // the search (the second graph) run together: the tail's small levels
-      // are latency-bound and the output pass is bandwidth-bound. The patch
-      // pass then rewrites the outputs of the vertices the tail reached.
-      G3_TRY_CUDA(cudaGraphLaunch(ws->gexec, s));
-      G3_TRY_CUDA(cudaEventRecord(ws->ev_fork, s));
-      G3_TRY_CUDA(cudaStreamWaitEvent(ws->s_out, ws->ev_fork, 0));
-      G3_TRY(translate(ws->s_out));
-      G3_TRY_CUDA(cudaEventRecord(ws->ev_out, ws->s_out));
-      G3_TRY_CUDA(cudaGraphLaunch(ws->gexec_tail, s));
-      G3_TRY_CUDA(cudaStreamWaitEvent(s, ws->ev_out, 0));
-      bfs_patch_tail<<<cap_grid(nb, 256, ws->grid_tr), 256, 0, s>>>(
-          nb, g->relabelled ? g->old_of_new : nullptr, ws->visited, ws->plo, ws->ctrl, op, ol);
-      G3_CHECK_LAUNCH();
-    } else {
-      // the whole search in the second graph, then the output pass
-      G3_TRY_CUDA(cudaGraphLaunch(ws->gexec_tail, s));
-      G3_TRY(translate(s));
-    }
+    if (!ws->gexec || !same_opts(ws->gopts, *o)) G3_TRY(build_graph(S));
+    G3_TRY_CUDA(cudaGraphLaunch(ws->gexec, s));
+    // the output pass goes right behind the level loop, without waiting for
+    // the host to read the controller; it is repeated below in the rare case
+    // of a search deeper than one graph launch runs
+    G3_TRY(translate(s));
     translated = true;
   }
   // Host-driven levels: everything in host-driven mode, and what a graph

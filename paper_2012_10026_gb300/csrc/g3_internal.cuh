@@ -45,6 +45,7 @@ void g3_free(void* p, cudaStream_t s);
 // site asks g3_alloc_should_fail() first and reports G3_ENOMEM when told to.
 bool g3_alloc_should_fail();
 int g3_rcm_hook_cap();
+g3_status g3_bfs_set_staged_stall(int spins);
 
 template <typename T>
 static inline g3_status g3_alloc(T** p, size_t count, cudaStream_t s) {

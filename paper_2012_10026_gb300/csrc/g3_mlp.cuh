@@ -14,21 +14,29 @@
 #define MLP_W2 (MLP_B1 + MLP_HID)
 #define MLP_B2 (MLP_W2 + MLP_OUT * MLP_HID)
 
-// Features of the frontier F_L (see the controller's documentation):
-//  0 log2(1+n_f) 1 log2(1+m_f) 2 log2(1+n_u) 3 log2(1+m_u)
-//  4 (id_max-id_min)/n  5 log2((1+m_f)/(1+m_u))  6 log2(1+n)  7 previous direction
+// Features of the frontier F_L (see the controller's documentation). All are
+// ratios of counts of the same graph, so that a network trained on smaller
+// graphs sees the same values for the same situation on a larger one:
+//  0 log2((1+n_f)/(1+n))   1 log2((1+m_f)/(1+nnz))
+//  2 log2((1+n_u)/(1+n))   3 log2((1+m_u)/(1+nnz))
+//  4 (id_max-id_min)/n     5 log2((1+m_f)/(1+m_u))
+//  6 log2((1+n)/(32 (1+m_f))): bitmap words a bottom-up step walks per
+//    frontier edge a top-down step expands   7 previous direction
 //  8..11 fraction of F_L in the degree buckets [0,32) [32,1024) [1024,32768) rest
+// (n: vertices of the searched graph, nnz: its directed entries)
 __device__ __forceinline__ void mlp_features_raw(long long nf, long long mf, long long nu,
                                                  long long mu, int id_min, int id_max, int32_t nb,
-                                                 int prev_dir, const long long* hist, float* f) {
+                                                 long long nnz, int prev_dir,
+                                                 const long long* hist, float* f) {
   const float fnf = (float)nf, fmf = (float)mf, fnu = (float)nu, fmu = (float)mu;
-  f[0] = log2f(1.f + fnf);
-  f[1] = log2f(1.f + fmf);
-  f[2] = log2f(1.f + fnu);
-  f[3] = log2f(1.f + fmu);
-  f[4] = (nf > 0 && nb > 0) ? (float)(id_max - id_min) / (float)nb : 0.f;
+  const float fn = (float)nb, fe = (float)nnz;
+  f[0] = log2f((1.f + fnf) / (1.f + fn));
+  f[1] = log2f((1.f + fmf) / (1.f + fe));
+  f[2] = log2f((1.f + fnu) / (1.f + fn));
+  f[3] = log2f((1.f + fmu) / (1.f + fe));
+  f[4] = (nf > 0 && nb > 0) ? (float)(id_max - id_min) / fn : 0.f;
   f[5] = log2f((1.f + fmf) / (1.f + fmu));
-  f[6] = log2f(1.f + (float)nb);  // graph size: the bottom-up scan cost grows with it
+  f[6] = log2f((1.f + fn) / (32.f * (1.f + fmf)));
   f[7] = (float)prev_dir;
   const float tot = nf > 0 ? fnf : 1.f;
   for (int k = 0; k < 4; ++k) f[8 + k] = (float)hist[k] / tot;

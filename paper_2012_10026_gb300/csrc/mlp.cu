@@ -159,10 +159,10 @@ struct FeatIn {
   int id_min, id_max, level, prev_dir;
 };
 
-__global__ void mlp_features_k(const FeatIn* in, int count, int32_t nb, float* x) {
+__global__ void mlp_features_k(const FeatIn* in, int count, int32_t nb, int64_t nnz, float* x) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < count; s += gridDim.x * blockDim.x) {
     const FeatIn& r = in[s];
-    mlp_features_raw(r.nf, r.mf, r.nu, r.mu, r.id_min, r.id_max, nb, r.prev_dir,
+    mlp_features_raw(r.nf, r.mf, r.nu, r.mu, r.id_min, r.id_max, nb, nnz, r.prev_dir,
                      r.hist, x + (size_t)s * MLP_IN);
   }
 }
@@ -207,8 +207,8 @@ extern "C" g3_status g3_mlp_train(float* params, const float* x, const float* y,
 }
 
 extern "C" g3_status g3_mlp_features(const g3_level_stats* stats, int32_t count, int32_t n_bfs,
-                                     float* x, void* stream) {
-  if (count < 0 || (count > 0 && (!stats || !x))) {
+                                     int64_t nnz, float* x, void* stream) {
+  if (count < 0 || nnz < 0 || (count > 0 && (!stats || !x))) {
     g3_set_error("g3_mlp_features: bad arguments");
     return G3_EINVAL;
   }
@@ -235,7 +235,7 @@ extern "C" g3_status g3_mlp_features(const g3_level_stats* stats, int32_t count,
     cudaError_t e = cudaMemcpyAsync(d, h, sizeof(FeatIn) * (size_t)count,
                                     cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
-      mlp_features_k<<<g3_grid_for(count, 256), 256, 0, s>>>(d, count, n_bfs, x);
+      mlp_features_k<<<g3_grid_for(count, 256), 256, 0, s>>>(d, count, n_bfs, nnz, x);
       g3_count_launch();
       e = cudaGetLastError();
     }

@@ -64,6 +64,7 @@ extern "C" g3_status g3_debug_inject(int32_t kind, int64_t value) {
     g_fail_at = value > 0 ? value : 0;
     return G3_OK;
   }
+  if (kind == G3_INJECT_STAGED_STALL) return g3_bfs_set_staged_stall(value > 0 ? (int)value : 0);
   if (kind == G3_INJECT_RCM_ROUNDS) {
     g_hook_cap = value > 0 ? (int)(value < (1 << 30) ? value : (1 << 30)) : 4096;
     return G3_OK;

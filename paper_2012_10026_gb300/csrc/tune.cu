@@ -275,7 +275,7 @@ extern "C" g3_status g3_autotune_bfs(g3_graph* g, const int32_t* roots, int32_t 
           o.t3 = bins[i][2];
         }
         if (c == 3) o.bu_reverse = i;
-        if (c == 4) o.bu_kernel = i;  // staged + word tiles, or word pairs
+        if (c == 4) o.bu_kernel = i;  // word pairs, or staged + word tiles
         if (!memcmp(&o, &best, sizeof(o))) continue;
         float ms = 0.f;
         G3_TRY(time_bfs(g, roots, nroots, o, parent, level, fl, ev, s, &ms));

@@ -46,7 +46,7 @@ def init_params(seed: int) -> np.ndarray:
 
 
 def collect(scale: int, seed: int, nroots: int, root_seed: int, device="cuda"):
-    """Recorded levels of nroots searches on one graph -> (rows, n_bfs)."""
+    """Recorded levels of nroots searches on one graph -> (rows, (n_bfs, nnz))."""
     import torch
     import graphgen
     n = 1 << scale
@@ -56,7 +56,7 @@ def collect(scale: int, seed: int, nroots: int, root_seed: int, device="cuda"):
     g = g3.g3_build_csr(src, dst, n)
     del src, dst
     g3.g3_rcm_relabel(g)
-    nb = g.info["n_bfs"]
+    nb = (g.info["n_bfs"], g.info["nnz"])
     parent = torch.empty(n, dtype=torch.int32, device=device)
     level = torch.empty(n, dtype=torch.int32, device=device)
     opts = g3.opts(record_both=1, timing=1)
@@ -69,12 +69,13 @@ def collect(scale: int, seed: int, nroots: int, root_seed: int, device="cuda"):
 
 
 def dataset(runs):
-    """(X, Y, meta) from [(rows_of_one_search, n_bfs)]: one sample per level >= 1."""
+    """(X, Y, meta) from [(rows_of_one_search, (n_bfs, nnz))]: one sample per
+    level >= 1."""
     xs, ys, meta = [], [], []
-    for st, nb in runs:
+    for st, (nb, nnz) in runs:
         if not st:
             continue
-        x = g3.g3_mlp_features(st, nb).cpu().numpy()
+        x = g3.g3_mlp_features(st, nb, nnz).cpu().numpy()
         for a, row in zip(st, x):
             if a["level"] == 0 or a["t_td_ms"] <= 0 or a["t_bu_ms"] <= 0:
                 continue
@@ -83,6 +84,22 @@ def dataset(runs):
                        math.log2(a["best_t2"]), math.log2(a["best_t3"])])
             meta.append((a["t_td_ms"], a["t_bu_ms"], a["dir"]))
     return (np.array(xs, np.float32), np.array(ys, np.float32), meta)
+
+
+def raw_rows(runs):
+    """Per sample of dataset(runs), the level record itself: n_f, m_f, n_u,
+    m_u, id_min, id_max, n_bfs, nnz, previous direction, level, hist[4],
+    t_TD, t_BU, the rule's direction and the best bins (for offline study)."""
+    out = []
+    for st, (nb, nnz) in runs:
+        for i, a in enumerate(st):
+            if a["level"] == 0 or a["t_td_ms"] <= 0 or a["t_bu_ms"] <= 0:
+                continue
+            prev = st[i - 1]["dir"] if i > 0 else 0
+            out.append([a["n_f"], a["m_f"], a["n_u"], a["m_u"], a["id_min"], a["id_max"], nb,
+                        nnz, prev, a["level"], *a["hist"], a["t_td_ms"], a["t_bu_ms"],
+                        a["dir"], a["best_t1"], a["best_t2"], a["best_t3"]])
+    return np.array(out, np.float64)
 
 
 def regret(meta, choice_bu):
@@ -132,32 +149,30 @@ def time_controllers(scale: int, seed: int, nroots: int, root_seed: int, configs
     return out
 
 
-DOMAIN_SLACK = 2 ** 0.5  # how far past the trained graph sizes the network is trusted
+FEATURES = "ratios"  # the feature set the controller's device code computes
 
 
 def controller_opts(path: str, n_bfs: int, device="cuda", **base):
-    """g3_bfs options for the trained controller in `path` on a graph of n_bfs
-    BFS vertices, on top of the options in `base`. Inside the graph sizes the
-    network was trained on (within a factor sqrt(2)) it runs with its margin
-    and bin choice; outside them the alpha/beta rule takes every decision and
-    the network is not run, since the per-level costs it learned do not carry
-    over (the bottom-up scan of the whole bitmap grows with n while
-    a small top-down frontier does not). Returns (opts, params tensor, note);
-    the tensor must outlive the searches."""
+    """g3_bfs options for the trained controller in `path`, on top of the
+    options in `base`: the network with its margin and bin choice. Its
+    features are ratios of the searched graph's own counts (frontier and
+    unvisited sizes over n and nnz, bitmap words per frontier edge), so the
+    same network serves every graph size. Returns (opts, params tensor,
+    note); the tensor must outlive the searches. Raises when the file was
+    trained on another feature set."""
     import torch
     with open(path) as f:
         mj = json.load(f)
+    if mj.get("features") != FEATURES:
+        raise ValueError(f"{path}: trained on feature set {mj.get('features')!r}, the "
+                         f"controller computes {FEATURES!r}; retrain it")
     params = torch.tensor(mj["params"], dtype=torch.float32, device=device)
-    lo, hi = mj.get("n_bfs_range", [0, 2 ** 31])
-    inside = lo / DOMAIN_SLACK <= n_bfs <= hi * DOMAIN_SLACK
-    kw = dict(base, controller=g3.G3_CTRL_LEARNED, mlp_params=params)
-    if inside:
-        kw.update(mlp_margin=int(mj.get("mlp_margin", 0)), mlp_bins=int(mj.get("mlp_bins", 1)))
-        note = "inside the trained graph sizes"
-    else:  # the rule decides every level; the network is not evaluated at all
-        kw.update(controller=g3.G3_CTRL_HEURISTIC, mlp_margin=0, mlp_bins=0)
-        note = (f"n_bfs {n_bfs} outside the trained sizes {lo}..{hi}: the alpha/beta rule "
-                f"decides every level")
+    kw = dict(base, controller=g3.G3_CTRL_LEARNED, mlp_params=params,
+              mlp_margin=int(mj.get("mlp_margin", 0)), mlp_bins=int(mj.get("mlp_bins", 1)))
+    lo, hi = mj.get("n_bfs_range", [0, 0])
+    where = "inside" if lo <= n_bfs <= hi else "outside"
+    note = (f"the network decides every level (n_bfs {n_bfs}, {where} the trained sizes "
+            f"{lo}..{hi}; size-free features)")
     return g3.opts(**kw), params, note
 
 
@@ -182,6 +197,10 @@ def main():
     ap.add_argument("--eval-scale", type=int, default=0,
                     help="held-out graph (seed 2) on which to compare the controllers")
     ap.add_argument("--eval-roots", type=int, default=8)
+    ap.add_argument("--dump", default="",
+                    help="also write the recorded samples (features, targets, per-level "
+                         "times and rule directions of the training, held-out and "
+                         "evaluation graphs) to this .npz file")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -199,9 +218,10 @@ def main():
     best_bu = np.array([tb < tt for (tt, tb, _) in meta])
     summary = {
         "params": [float(v) for v in p.cpu().numpy()],
+        "features": FEATURES,
         "layout": "W1[32][12], b1[32], W2[4][32], b2[4]",
         # graph sizes seen in training (BFS vertices); see controller_opts
-        "n_bfs_range": [min(nb for _, nb in runs), max(nb for _, nb in runs)],
+        "n_bfs_range": [min(nb[0] for _, nb in runs), max(nb[0] for _, nb in runs)],
         "scales": args.scales, "seeds": args.seeds, "roots_per_graph": args.roots,
         "samples": int(len(X)), "steps": args.steps, "lr": args.lr,
         "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
@@ -214,7 +234,8 @@ def main():
     # margin chosen on a held-out graph of the largest training scale (a new
     # seed and new roots), never on the evaluation scale
     rows, nb = collect(max(args.scales), 97, args.roots, 98)
-    Xh, _, mh = dataset([(st, nb) for st in rows])
+    hruns = [(st, nb) for st in rows]
+    Xh, _, mh = dataset(hruns)
     oh = g3.g3_mlp_forward(p, torch.from_numpy(Xh).cuda()).cpu().numpy()[:, 0]
     table = {str(m): regret(mh, gated(oh, mh, m)) for m in MARGINS}
     best_m = min(MARGINS, key=lambda m: (table[str(m)], m))
@@ -234,7 +255,8 @@ def main():
         # held-out graph: per-level times of both directions under the
         # heuristic's path; regret of each controller's choices on it
         rows, nb = collect(args.eval_scale, 1, args.eval_roots, 2)
-        Xe, Ye, me = dataset([(st, nb) for st in rows])
+        eruns = [(st, nb) for st in rows]
+        Xe, Ye, me = dataset(eruns)
         oe = g3.g3_mlp_forward(p, torch.from_numpy(Xe).cuda()).cpu().numpy()
         summary["eval"] = {
             "scale": args.eval_scale, "roots": args.eval_roots, "levels": int(len(Xe)),
@@ -243,6 +265,11 @@ def main():
             "regret_ms_heuristic": regret(me, [d == 1 for (_, _, d) in me]),
             "best_total_ms": float(sum(min(tt, tb) for (tt, tb, _) in me)),
         }
+    if args.dump:
+        arrays = {"train": raw_rows(runs), "holdout": raw_rows(hruns)}
+        if args.eval_scale:
+            arrays["eval"] = raw_rows(eruns)
+        np.savez(args.dump, **arrays)
     with open(args.out, "w") as f:
         json.dump(summary, f, indent=1)
     print(json.dumps({k: v for k, v in summary.items() if k != "params"}))

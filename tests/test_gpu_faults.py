@@ -2,7 +2,9 @@
 device allocation of a call made to fail in turn must give G3_ENOMEM, leave
 nothing of the call allocated and the graph as it was, and the same call
 must then succeed and agree with the oracle; an RCM relabel capped below the
-hooking rounds it needs must give G3_ETIMEOUT and leave the graph usable."""
+hooking rounds it needs must give G3_ETIMEOUT and leave the graph usable; a
+kernel's bounded wait that runs out (its data never arrives) must give
+G3_ETIMEOUT and leave the device usable."""
 import numpy as np
 import pytest
 
@@ -25,6 +27,7 @@ def _disarm():
     yield
     g3.g3_debug_inject(g3.G3_INJECT_ALLOC, 0)
     g3.g3_debug_inject(g3.G3_INJECT_RCM_ROUNDS, 0)
+    g3.g3_debug_inject(g3.G3_INJECT_STAGED_STALL, 0)
 
 
 def _each_allocation_fails(call, check_clean, limit=200):
@@ -186,3 +189,31 @@ def test_inject_rejects_unknown_kind():
     with pytest.raises(g3.G3Error) as e:
         g3.g3_debug_inject(99, 1)
     assert e.value.status == g3.G3_EINVAL
+
+
+def test_staged_kernel_wait_runs_out_and_the_device_stays_usable():
+    # the staged bottom-up kernel's first tile never arrives: its bounded
+    # wait ends, the search reports G3_ETIMEOUT, and the next search (hook
+    # off) is exact
+    scale, n = 14, 1 << 14
+    src, dst = graphgen.kronecker_edges(scale, 16, seed=13)
+    ref = oracle.pipeline(src, dst, n)
+    g = g3.g3_build_csr(_dev(src), _dev(dst), n)
+    g3.g3_rcm_relabel(g)
+    root = int(graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), 1, seed=14)[0])
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    o = g3.opts(controller=g3.G3_CTRL_BOTTOMUP, bu_kernel=1)
+    g3.g3_debug_inject(g3.G3_INJECT_STAGED_STALL, 1000)
+    for timing in (0, 1):  # the level-loop graph and the host-driven loop
+        with pytest.raises(g3.G3Error) as e:
+            g3.g3_bfs(g, root, parent, level, g3.opts(controller=g3.G3_CTRL_BOTTOMUP,
+                                                      bu_kernel=1, timing=timing))
+        assert e.value.status == g3.G3_ETIMEOUT
+    g3.g3_debug_inject(g3.G3_INJECT_STAGED_STALL, 0)
+    g3.g3_bfs(g, root, parent, level, o)
+    _, lref = oracle.bfs(ref["off"], ref["col"], root)
+    assert np.array_equal(level.cpu().numpy(), lref)
+    assert oracle.validate(ref["off"], ref["col"], root, parent.cpu().numpy(),
+                           level.cpu().numpy()) == 0
+    g.free()

@@ -31,15 +31,3 @@ def test_trained_controller_beats_the_rule_on_held_out_graph():
     assert r_learned < 0.5 * r_rule, (r_learned, r_rule)
     # with the margin past every output the rule decides every level
     assert tc.regret(mh, tc.gated(o0, mh, 1e9)) == pytest.approx(r_rule)
-
-
-def test_controller_opts_falls_back_outside_trained_sizes(tmp_path):
-    import json
-    from oracle import mlp
-    path = tmp_path / "c.json"
-    path.write_text(json.dumps({"params": mlp.init_params(1).tolist(), "mlp_margin": 250,
-                                "mlp_bins": 1, "n_bfs_range": [1 << 19, 1 << 23]}))
-    o, _, note = tc.controller_opts(str(path), 1 << 22, alpha=20)
-    assert (o.controller, o.mlp_margin, o.mlp_bins, o.alpha) == (g3.G3_CTRL_LEARNED, 250, 1, 20)
-    o, _, note = tc.controller_opts(str(path), 1 << 25)
-    assert o.controller == g3.G3_CTRL_HEURISTIC and "outside" in note

@@ -75,16 +75,16 @@ def test_features_match_oracle_on_real_levels():
     src, dst = graphgen.kronecker_edges(scale, 16, seed=2)
     g = g3.g3_build_csr(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
     g3.g3_rcm_relabel(g)
-    nb = g.info["n_bfs"]
+    nb, nnz = g.info["n_bfs"], g.info["nnz"]
     roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), 4, seed=3)
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
     level = torch.empty(n, dtype=torch.int32, device="cuda")
     for r in roots.tolist():
         st = g3.g3_bfs(g, r, parent, level, max_stats=64)
-        x = g3.g3_mlp_features(st, nb).cpu().numpy()
+        x = g3.g3_mlp_features(st, nb, nnz).cpu().numpy()
         for a, row in zip(st, x):
             prev = st[a["level"] - 1]["dir"] if a["level"] > 0 else 0
             ref = mlp.features(a["n_f"], a["m_f"], a["n_u"], a["m_u"], a["id_min"], a["id_max"],
-                               nb, a["level"], prev, a["hist"])
+                               nb, nnz, prev, a["hist"])
             assert np.allclose(row, ref, rtol=1e-5, atol=1e-5)
     g.free()

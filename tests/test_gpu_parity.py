@@ -118,10 +118,11 @@ def test_bfs_small_cases(case, relabel):
     g = gpu_pipeline(src, dst, n, relabel)
     rng = np.random.default_rng(n)
     roots = sorted(set([0, n - 1] + rng.integers(0, n, 6).tolist()))
-    # bottom-up in both kernels (word tiles, word pairs) and scan orders; the
-    # output pass in one pass and split over label halves
+    # bottom-up in every kernel set (word pairs, staged + word tiles, word
+    # tiles) and both scan orders; the output pass in one pass and split over
+    # label halves
     for ctrl, rev, kern, split in ((g3.G3_CTRL_HEURISTIC, 1, 0, 0),
-                                   (g3.G3_CTRL_HEURISTIC, 1, 0, 2),
+                                   (g3.G3_CTRL_HEURISTIC, 1, 1, 2),
                                    (g3.G3_CTRL_TOPDOWN, 1, 0, 1),
                                    (g3.G3_CTRL_BOTTOMUP, 1, 0, 0), (g3.G3_CTRL_BOTTOMUP, 0, 0, 0),
                                    (g3.G3_CTRL_BOTTOMUP, 1, 1, 0), (g3.G3_CTRL_BOTTOMUP, 0, 1, 2),
@@ -155,12 +156,12 @@ def _levels_new(ref, level_orig):
                                 dict(controller=g3.G3_CTRL_BOTTOMUP, bu_reverse=0),
                                 dict(t1=2, t2=4, t3=8), dict(alpha=64, beta=8),
                                 dict(bu_kernel=1),
-                                dict(controller=g3.G3_CTRL_BOTTOMUP, bu_kernel=1, bu_reverse=0),
+                                dict(controller=g3.G3_CTRL_BOTTOMUP, bu_kernel=1),
                                 dict(out_split=2), dict(out_split=1),
                                 dict(controller=g3.G3_CTRL_BOTTOMUP, bu_kernel=2)],
                          ids=["heuristic", "topdown", "bottomup", "forward_scan",
-                              "bottomup_forward", "tiny_bins", "alpha64_beta8", "word_pairs",
-                              "word_pairs_forward", "out_split", "out_one_pass",
+                              "bottomup_forward", "tiny_bins", "alpha64_beta8", "staged",
+                              "bottomup_staged", "out_split", "out_one_pass",
                               "bottomup_tiles"])
 def test_bfs_kron16_all_roots(kron16, kw):
     K = kron16
@@ -230,7 +231,8 @@ def test_learned_controller_random_params_stays_exact(kron16):
         assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
         for a in st[1:]:
             f = mlp.features(a["n_f"], a["m_f"], a["n_u"], a["m_u"], a["id_min"], a["id_max"],
-                             ref["n_plus"], a["level"], st[a["level"] - 1]["dir"], a["hist"])
+                             ref["n_plus"], len(ref["col_r"]), st[a["level"] - 1]["dir"],
+                             a["hist"])
             o = mlp.forward(mlp.init_params(5), f[None])[0]
             assert np.allclose(a["mlp_out"], o, rtol=1e-4, atol=1e-4)
             if abs(o[0]) > 1e-3:

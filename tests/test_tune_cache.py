@@ -68,21 +68,23 @@ def test_cache_errors(tmp_path):
         g3.tune_cache_lookup(None, g3.G3_TUNE_BFS, 1, 1)
 
 
-def test_learned_controller_domain_guard(tmp_path):
-    """The trained controller decides only for graph sizes near those it was
-    trained on; elsewhere the alpha/beta rule takes every decision."""
+def test_learned_controller_options_at_every_size(tmp_path):
+    """The trained controller (size-free features) decides at every graph
+    size with the margin and bin choice of its file; a file trained on
+    another feature set is refused."""
     import json
     pytest.importorskip("torch")
     from oracle import mlp
     from paper_2012_10026_gb300 import train_controller as tc
     path = tmp_path / "c.json"
     path.write_text(json.dumps({"params": mlp.init_params(1).tolist(), "mlp_margin": 250,
-                                "mlp_bins": 1, "n_bfs_range": [1 << 19, 1 << 23]}))
-    inside = [1 << 19, 1 << 21, 1 << 23, int((1 << 23) * 1.4)]
-    outside = [1 << 25, (1 << 19) // 2, int((1 << 23) * 1.5)]
-    for nb in inside:
+                                "mlp_bins": 1, "n_bfs_range": [1 << 19, 1 << 23],
+                                "features": tc.FEATURES}))
+    for nb in [1 << 19, 1 << 21, 1 << 25, (1 << 19) // 2]:
         o, _, note = tc.controller_opts(str(path), nb, device="cpu", alpha=20)
         assert (o.controller, o.mlp_margin, o.mlp_bins, o.alpha) == (g3.G3_CTRL_LEARNED, 250, 1, 20)
-    for nb in outside:
-        o, _, note = tc.controller_opts(str(path), nb, device="cpu")
-        assert o.controller == g3.G3_CTRL_HEURISTIC and "outside" in note
+        assert ("inside" in note) == ((1 << 19) <= nb <= (1 << 23))
+    old = tmp_path / "old.json"
+    old.write_text(json.dumps({"params": mlp.init_params(1).tolist()}))
+    with pytest.raises(ValueError):
+        tc.controller_opts(str(old), 1 << 20, device="cpu")
