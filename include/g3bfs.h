@@ -269,7 +269,10 @@ void g3_msbfs_opts_default(g3_msbfs_opts* o);
  *   n_levels : (nullable) number of levels run.
  *   ms       : (nullable) time of the call on the device, CUDA events.
  * The first call on a graph allocates its workspace (about 112 bytes per
- * BFS vertex). Synchronises `stream` once per level and before returning.
+ * BFS vertex). The level loop runs on the device as one CUDA graph (a WHILE
+ * node over a push/pull SWITCH, decided by a device-side control kernel;
+ * rebuilt when k's source mask or the options change); the call synchronises
+ * `stream` once, before returning.
  * Errors: G3_EINVAL, G3_ERANGE (a level above 126 does not fit int8),
  * G3_ENOMEM, G3_ECUDA. */
 g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k, const g3_msbfs_opts* opts,

@@ -9,10 +9,11 @@ Loss over a batch of B samples with per-output weights w_k:
     L = 1/(2B) * sum_b sum_k w_k (o_bk - y_bk)^2
 ReLU derivative is taken as 0 at z == 0.
 
-Features of a level (inputs), computed from the frontier statistics as
-ratios of counts of the same graph (n vertices, nnz directed entries):
+Features of a level (inputs), computed from the frontier statistics, all
+but feature 3 ratios of counts of the same graph (n vertices, nnz directed
+entries):
     0 log2((1+n_f)/(1+n))    1 log2((1+m_f)/(1+nnz))
-    2 log2((1+n_u)/(1+n))    3 log2((1+m_u)/(1+nnz))
+    2 log2((1+n_u)/(1+n))    3 n / 2^24 (the graph size, linear)
     4 (max_id - min_id) / n   (0 for an empty frontier)
     5 log2((1+m_f)/(1+m_u))  6 log2((1+n) / (32 (1+m_f)))
     7 previous direction (0 TD, 1 BU)
@@ -104,7 +105,7 @@ def features(n_f, m_f, n_u, m_u, id_min, id_max, n, nnz, prev_dir, hist4):
     tot = max(n_f, 1)
     return np.array([
         np.log2((1.0 + n_f) / (1.0 + n)), np.log2((1.0 + m_f) / (1.0 + nnz)),
-        np.log2((1.0 + n_u) / (1.0 + n)), np.log2((1.0 + m_u) / (1.0 + nnz)),
+        np.log2((1.0 + n_u) / (1.0 + n)), n / 2.0 ** 24,
         span, np.log2((1.0 + m_f) / (1.0 + m_u)), np.log2((1.0 + n) / (32.0 * (1.0 + m_f))),
         float(prev_dir),
         hist4[0] / tot, hist4[1] / tot, hist4[2] / tot, hist4[3] / tot,

@@ -23,6 +23,19 @@
 
 #define MS_CHUNK 2048  // row entries per warp work item
 
+// Device counters (ctr[]): per level [0] next queue length, [1] next sum of
+// degrees, [2] heavy / touched length, [3] chunk items, [4] pending heavy
+// vertices; per call [5] row entries read and [6] vertices scanned by pull
+// levels; the device-side level loop's state:
+#define MS_QCUR 7     // length of the queue being expanded
+#define MS_LEVEL 8    // levels expanded so far
+#define MS_PULLS 9    // pull levels
+#define MS_PUSHES 10  // push levels
+#define MS_PUSHED 11  // row entries pushed
+#define MS_ERANGE 12  // a level above 126 exists
+#define MS_LNEXT 13   // the level the current expansion writes
+#define MS_NCTR 32
+
 struct g3_ms_ws {
   int32_t nb;
   uint64_t *vis, *fa, *fb, *nx;
@@ -32,10 +45,11 @@ struct g3_ms_ws {
   int32_t* pend;     // pull: heavy vertices whose rows were split into chunks
   int2* items;       // (vertex, chunk index >= 1) of split rows
   int64_t items_cap;
-  // [0] next queue len, [1] next sum of degrees, [2] heavy len, [3] items,
-  // [4] pending heavy vertices (per level); [5] row entries read and [6]
-  // vertices scanned by the pull levels (per call)
-  unsigned long long* ctr;
+  unsigned long long* ctr;  // MS_NCTR counters, see above
+  // the level loop as one CUDA graph, and what it was built for
+  cudaGraphExec_t gexec;
+  uint64_t g_full;
+  g3_msbfs_opts g_opts;
   g3_msbfs_stats last;  // of the last call
   unsigned long long* h_ctr;
   int32_t* d_roots;
@@ -51,6 +65,7 @@ void g3_ms_ws_free(g3_ms_ws* w) {
   if (w->h_ctr) cudaFreeHost(w->h_ctr);
   for (int i = 0; i < 2; ++i)
     if (w->ev[i]) cudaEventDestroy(w->ev[i]);
+  if (w->gexec) cudaGraphExecDestroy(w->gexec);
   free(w);
 }
 
@@ -66,7 +81,7 @@ static g3_status ms_ws_create(g3_graph* g, g3_ms_ws** out) {
     size_t bytes;
   } req[] = {{(void**)&w->vis, nb1 * 8}, {(void**)&w->fa, nb1 * 8},   {(void**)&w->fb, nb1 * 8},
              {(void**)&w->nx, nb1 * 8},  {(void**)&w->lv, nb1 * 64},  {(void**)&w->qa, nb1 * 4},
-             {(void**)&w->qb, nb1 * 4},  {(void**)&w->heavy, nb1 * 4}, {(void**)&w->ctr, 64},
+             {(void**)&w->qb, nb1 * 4},  {(void**)&w->heavy, nb1 * 4}, {(void**)&w->ctr, MS_NCTR * 8},
              {(void**)&w->pend, nb1 * 4}, {(void**)&w->items, (size_t)w->items_cap * 8},
              {(void**)&w->d_roots, 64 * 4}};
   for (auto& r : req) {
@@ -79,7 +94,7 @@ static g3_status ms_ws_create(g3_graph* g, g3_ms_ws** out) {
       return G3_ENOMEM;
     }
   }
-  if (cudaMallocHost((void**)&w->h_ctr, 64) != cudaSuccess ||
+  if (cudaMallocHost((void**)&w->h_ctr, MS_NCTR * 8) != cudaSuccess ||
       cudaEventCreate(&w->ev[0]) != cudaSuccess || cudaEventCreate(&w->ev[1]) != cudaSuccess) {
     cudaGetLastError();
     g3_ms_ws_free(w);
@@ -144,13 +159,14 @@ __device__ __forceinline__ void ms_push_range(int64_t b, int64_t e, uint64_t fu,
 }
 
 // Push, one warp per frontier vertex (first chunk of long rows).
-__global__ void __launch_bounds__(256) ms_push(const int32_t* __restrict__ q, int64_t qlen,
+__global__ void __launch_bounds__(256) ms_push(const int32_t* __restrict__ q,
                                                const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
                                                const uint64_t* __restrict__ F,
                                                const uint64_t* __restrict__ vis, uint64_t* N,
                                                int32_t* touched, unsigned long long* ctr,
                                                int2* items) {
+  const int64_t qlen = (int64_t)ctr[MS_QCUR];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < qlen; i += nwarps) {
@@ -183,10 +199,11 @@ __global__ void __launch_bounds__(256) ms_push_chunks(const int2* __restrict__ i
 
 // Finalize after a push: keep N[w]'s bits not yet in vis[w] as the new
 // frontier word, record their levels, queue w when anything is new, clear N.
-__global__ void ms_push_finalize(const int32_t* __restrict__ touched, int64_t len,
-                                 uint64_t* N, uint64_t* vis, uint64_t* Fn, int8_t* lv,
-                                 int8_t lnext, int32_t* qn, const int64_t* __restrict__ off,
-                                 unsigned long long* ctr) {
+__global__ void ms_push_finalize(const int32_t* __restrict__ touched, uint64_t* N,
+                                 uint64_t* vis, uint64_t* Fn, int8_t* lv, int32_t* qn,
+                                 const int64_t* __restrict__ off, unsigned long long* ctr) {
+  const int64_t len = (int64_t)ctr[2];
+  const int8_t lnext = (int8_t)ctr[MS_LNEXT];
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < len;
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
@@ -233,10 +250,10 @@ __device__ __forceinline__ void ms_take(int32_t v, uint64_t nv, uint64_t* vis, u
 __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
                                                const uint64_t* __restrict__ F, uint64_t* vis,
-                                               uint64_t* Fn, int8_t* lv, int8_t lnext,
-                                               uint64_t full, int64_t heavy_deg,
-                                               int32_t* heavy, int32_t* qn,
+                                               uint64_t* Fn, int8_t* lv, uint64_t full,
+                                               int64_t heavy_deg, int32_t* heavy, int32_t* qn,
                                                unsigned long long* ctr) {
+  const int8_t lnext = (int8_t)ctr[MS_LNEXT];
   const bool col_al16 = ((uintptr_t)col & 15) == 0;
   unsigned long long rd_all = 0, sc_all = 0;  // work counts, added once per warp
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nb;
@@ -331,10 +348,11 @@ __global__ void __launch_bounds__(256) ms_pull_heavy(const int32_t* __restrict__
                                                      const int32_t* __restrict__ col,
                                                      const uint64_t* __restrict__ F,
                                                      uint64_t* vis, uint64_t* Fn, uint64_t* N,
-                                                     int8_t* lv, int8_t lnext, uint64_t full,
-                                                     int32_t* qn, int32_t* pend, int2* items,
+                                                     int8_t* lv, uint64_t full, int32_t* qn,
+                                                     int32_t* pend, int2* items,
                                                      unsigned long long* ctr) {
   const int64_t len = (int64_t)ctr[2];
+  const int8_t lnext = (int8_t)ctr[MS_LNEXT];
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int64_t read = 0, scanned = 0;  // work counts, added once per warp
@@ -384,9 +402,10 @@ __global__ void __launch_bounds__(256) ms_pull_chunks(const int2* __restrict__ i
 
 // Finishes the split heavy vertices: new sources = N[v] & ~vis[v]; N cleared.
 __global__ void ms_pull_pending(const int32_t* __restrict__ pend, const int64_t* __restrict__ off,
-                                uint64_t* vis, uint64_t* Fn, uint64_t* N, int8_t* lv,
-                                int8_t lnext, int32_t* qn, unsigned long long* ctr) {
+                                uint64_t* vis, uint64_t* Fn, uint64_t* N, int8_t* lv, int32_t* qn,
+                                unsigned long long* ctr) {
   const int64_t len = (int64_t)ctr[4];
+  const int8_t lnext = (int8_t)ctr[MS_LNEXT];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = pend[i];
@@ -464,6 +483,165 @@ __global__ void ms_roots_out(const int32_t* roots, int k, int32_t n, int8_t* lev
   if (s < k) level[(int64_t)s * n + roots[s]] = 0;
 }
 
+// ------------------------------------------------------ level loop graph
+// Before each level: reads the frontier produced by the previous one, ends
+// the loop when it is empty (or flags a level above 126), else chooses pull
+// (sum of frontier degrees * push_alpha > nnz) or push, keeps the per-call
+// counts, clears the per-level counters and selects the SWITCH branch.
+__global__ void ms_control(unsigned long long* ctr, int64_t nnz, int32_t push_alpha,
+                           cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_kind) {
+  const unsigned long long qlen = ctr[0], mf = ctr[1], L = ctr[MS_LEVEL];
+  if (qlen == 0 || L >= 127) {
+    if (qlen != 0) ctr[MS_ERANGE] = 1;  // expanding level 127 would write level 128
+    cudaGraphSetConditional(h_kind, 2u);  // no branch
+    cudaGraphSetConditional(h_loop, 0u);
+    return;
+  }
+  const bool pull = (long long)mf * (long long)push_alpha > nnz;
+  if (pull) {
+    ctr[MS_PULLS] += 1;
+  } else {
+    ctr[MS_PUSHES] += 1;
+    ctr[MS_PUSHED] += mf;  // every row entry of the frontier is pushed
+  }
+  ctr[MS_QCUR] = qlen;
+  ctr[MS_LNEXT] = L + 1;
+  ctr[MS_LEVEL] = L + 1;
+  for (int i = 0; i < 5; ++i) ctr[i] = 0;
+  cudaGraphSetConditional(h_kind, pull ? 0u : 1u);
+  cudaGraphSetConditional(h_loop, 1u);
+}
+
+// Push needs Fn zero outside the new frontier.
+__global__ void ms_clear(uint64_t* Fn, int32_t nb) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nb;
+       i += (int64_t)gridDim.x * blockDim.x)
+    Fn[i] = 0;
+}
+
+static g3_status ms_add_kernel(cudaGraph_t gr, cudaGraphNode_t* node, cudaGraphNode_t* dep,
+                               void* func, int grid, int block, void** args) {
+  cudaKernelNodeParams p;
+  memset(&p, 0, sizeof(p));
+  p.func = func;
+  p.gridDim = dim3(grid);
+  p.blockDim = dim3(block);
+  p.kernelParams = args;
+  G3_TRY_CUDA(cudaGraphAddKernelNode(node, gr, dep, dep ? 1 : 0, &p));
+  return G3_OK;
+}
+
+struct MsNodeParams {
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  MsNodeParams() { memset(raw, 0, sizeof(raw)); }
+  cudaGraphNodeParams& get() { return *reinterpret_cast<cudaGraphNodeParams*>(raw); }
+};
+
+// The level loop of one call as a CUDA graph: WHILE { control -> SWITCH
+// {pull, push} for a level from (fa, qa) into (fb, qb), then the same for a
+// level from (fb, qb) into (fa, qa) }. Kernel arguments are fixed; what
+// changes per level lives in ctr.
+static g3_status ms_build_graph(g3_graph* g, g3_ms_ws* w, uint64_t full, const g3_msbfs_opts& o) {
+  cudaGraph_t top = nullptr;
+  G3_TRY_CUDA(cudaGraphCreate(&top, 0));
+  g3_status st = G3_OK;
+  const int grid = G3_NUM_SMS * 8;
+  int32_t nb = w->nb;
+  int64_t nnz = g->nnz, heavy_deg = o.pull_warp_deg;
+  int32_t push_alpha = o.push_alpha;
+  const int64_t* off = g->off;
+  const int32_t* col = g->col;
+  uint64_t f = full;
+  cudaGraphConditionalHandle h_loop, h_kind[2];
+  // per half: the frontier buffers it reads and writes
+  uint64_t* Fs[2][2] = {{w->fa, w->fb}, {w->fb, w->fa}};
+  int32_t* Qs[2][2] = {{w->qa, w->qb}, {w->qb, w->qa}};
+  do {
+    if (cudaGraphConditionalHandleCreate(&h_loop, top, 1, cudaGraphCondAssignDefault) !=
+        cudaSuccess) { st = G3_ECUDA; break; }
+    MsNodeParams wb;
+    cudaGraphNodeParams& wp = wb.get();
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp) != cudaSuccess) {
+      st = G3_ECUDA;
+      break;
+    }
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    cudaGraphNode_t prev = nullptr;
+    for (int half = 0; half < 2 && st == G3_OK; ++half) {
+      if (cudaGraphConditionalHandleCreate(&h_kind[half], body, 0, 0) != cudaSuccess) {
+        st = G3_ECUDA;
+        break;
+      }
+    }
+    if (st != G3_OK) break;
+    // argument storage must outlive cudaGraphAddKernelNode only (copied in)
+    for (int half = 0; half < 2 && st == G3_OK; ++half) {
+      uint64_t *F = Fs[half][0], *Fn = Fs[half][1];
+      int32_t *q = Qs[half][0], *qn = Qs[half][1];
+      cudaGraphNode_t ctl, sw;
+      void* a_ctl[] = {&w->ctr, &nnz, &push_alpha, &h_loop, &h_kind[half]};
+      if ((st = ms_add_kernel(body, &ctl, half ? &prev : nullptr, (void*)ms_control, 1, 1,
+                              a_ctl)))
+        break;
+      MsNodeParams sb;
+      cudaGraphNodeParams& sp = sb.get();
+      sp.type = cudaGraphNodeTypeConditional;
+      sp.conditional.handle = h_kind[half];
+      sp.conditional.type = cudaGraphCondTypeSwitch;
+      sp.conditional.size = 2;
+      if (cudaGraphAddNode(&sw, body, &ctl, nullptr, 1, &sp) != cudaSuccess) {
+        st = G3_ECUDA;
+        break;
+      }
+      cudaGraph_t pull = sp.conditional.phGraph_out[0], push = sp.conditional.phGraph_out[1];
+      cudaGraphNode_t n0, n1, n2, n3;
+      void* a_pull[] = {&nb, &off, &col, &F, &w->vis, &Fn, &w->lv, &f, &heavy_deg, &w->heavy,
+                        &qn, &w->ctr};
+      void* a_heavy[] = {&w->heavy, &off, &col, &F, &w->vis, &Fn, &w->nx, &w->lv, &f, &qn,
+                         &w->pend, &w->items, &w->ctr};
+      void* a_chunks[] = {&w->items, &off, &col, &F, &w->vis, &w->nx, &f, &w->ctr};
+      void* a_pend[] = {&w->pend, &off, &w->vis, &Fn, &w->nx, &w->lv, &qn, &w->ctr};
+      if ((st = ms_add_kernel(pull, &n0, nullptr, (void*)ms_pull, grid, 256, a_pull))) break;
+      if ((st = ms_add_kernel(pull, &n1, &n0, (void*)ms_pull_heavy, grid, 256, a_heavy))) break;
+      if ((st = ms_add_kernel(pull, &n2, &n1, (void*)ms_pull_chunks, grid, 256, a_chunks)))
+        break;
+      if ((st = ms_add_kernel(pull, &n3, &n2, (void*)ms_pull_pending, G3_NUM_SMS, 256, a_pend)))
+        break;
+      void* a_clear[] = {&Fn, &nb};
+      void* a_push[] = {&q, &off, &col, &F, &w->vis, &w->nx, &w->heavy, &w->ctr, &w->items};
+      void* a_pchunks[] = {&w->items, &off, &col, &F, &w->vis, &w->nx, &w->heavy, &w->ctr};
+      void* a_fin[] = {&w->heavy, &w->nx, &w->vis, &Fn, &w->lv, &qn, &off, &w->ctr};
+      if ((st = ms_add_kernel(push, &n0, nullptr, (void*)ms_clear, grid, 256, a_clear))) break;
+      if ((st = ms_add_kernel(push, &n1, &n0, (void*)ms_push, grid, 256, a_push))) break;
+      if ((st = ms_add_kernel(push, &n2, &n1, (void*)ms_push_chunks, grid, 256, a_pchunks)))
+        break;
+      if ((st = ms_add_kernel(push, &n3, &n2, (void*)ms_push_finalize, grid, 256, a_fin))) break;
+      prev = sw;
+    }
+    if (st != G3_OK) break;
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, top, 0) != cudaSuccess) {
+      st = G3_ECUDA;
+      break;
+    }
+    if (w->gexec) cudaGraphExecDestroy(w->gexec);
+    w->gexec = ex;
+    w->g_full = full;
+    w->g_opts = o;
+  } while (0);
+  if (st != G3_OK) {
+    cudaError_t e = cudaGetLastError();
+    g3_set_error("g3_msbfs: building the level-loop graph failed: %s", cudaGetErrorString(e));
+  }
+  cudaGraphDestroy(top);
+  return st;
+}
+
 // ------------------------------------------------------------------ host
 extern "C" void g3_msbfs_opts_default(g3_msbfs_opts* o) {
   if (!o) return;
@@ -499,94 +677,43 @@ extern "C" g3_status g3_msbfs(g3_graph* g, const int32_t* roots, int32_t k,
   unsigned long long* h = w->h_ctr;
   const int grid = G3_NUM_SMS * 8;
 
+  if (w->items_cap < g->nnz / MS_CHUNK + 4) {
+    g3_set_error("g3_msbfs: workspace does not fit the graph");
+    return G3_ESTATE;
+  }
+  if (!w->gexec || w->g_full != full || w->g_opts.push_alpha != o.push_alpha ||
+      w->g_opts.pull_warp_deg != o.pull_warp_deg)
+    G3_TRY(ms_build_graph(g, w, full, o));
   G3_TRY_CUDA(cudaEventRecord(w->ev[0], s));
   G3_TRY_CUDA(cudaMemcpyAsync(w->d_roots, roots, (size_t)k * 4, cudaMemcpyHostToDevice, s));
   G3_TRY_CUDA(cudaMemsetAsync(w->vis, 0, (size_t)nb * 8 + 8, s));
   G3_TRY_CUDA(cudaMemsetAsync(w->fa, 0, (size_t)nb * 8 + 8, s));
   G3_TRY_CUDA(cudaMemsetAsync(w->nx, 0, (size_t)nb * 8 + 8, s));
-  G3_TRY_CUDA(cudaMemsetAsync(w->ctr, 0, 64, s));
-  if (w->items_cap < g->nnz / MS_CHUNK + 4) {
-    g3_set_error("g3_msbfs: workspace does not fit the graph");
-    return G3_ESTATE;
-  }
+  G3_TRY_CUDA(cudaMemsetAsync(w->ctr, 0, MS_NCTR * 8, s));
   ms_seed<<<1, 64, 0, s>>>(w->d_roots, k, n2o, nb, w->vis, w->fa, w->lv, w->qa, w->ctr, g->off);
   G3_CHECK_LAUNCH();
-  uint64_t *F = w->fa, *Fn = w->fb;
-  int32_t *q = w->qa, *qn = w->qb;
-  int32_t L = 0;
-  g3_msbfs_stats stats;
-  memset(&stats, 0, sizeof(stats));
-  for (;; ++L) {
-    G3_TRY_CUDA(cudaMemcpyAsync(h, w->ctr, 24, cudaMemcpyDeviceToHost, s));
-    G3_TRY_CUDA(cudaStreamSynchronize(s));
-    const int64_t qlen = (int64_t)h[0], mf = (int64_t)h[1];
-    if (qlen == 0) break;
-    // expanding level L writes L + 1 (127 still fits int8); a non-empty
-    // frontier at level 127 means a level above 126 exists
-    if (L >= 127) {
-      g3_set_error("g3_msbfs: a level exceeds 126, the int8 range of the output");
-      return G3_ERANGE;
-    }
-    G3_TRY_CUDA(cudaMemsetAsync(w->ctr, 0, 40, s));
-    const bool pull = mf * (int64_t)o.push_alpha > g->nnz;
-    if (pull) {
-      stats.pull_levels++;
-    } else {
-      stats.push_levels++;
-      stats.push_entries += mf;  // every row entry of the frontier is pushed
-    }
-    const int8_t lnext = (int8_t)(L + 1);
-    if (pull) {
-      ms_pull<<<grid, 256, 0, s>>>(nb, g->off, g->col, F, w->vis, Fn, w->lv, lnext, full,
-                                   o.pull_warp_deg, w->heavy, qn, w->ctr);
-      G3_CHECK_LAUNCH();
-      ms_pull_heavy<<<grid, 256, 0, s>>>(w->heavy, g->off, g->col, F, w->vis, Fn, w->nx, w->lv,
-                                         lnext, full, qn, w->pend, w->items, w->ctr);
-      G3_CHECK_LAUNCH();
-      ms_pull_chunks<<<grid, 256, 0, s>>>(w->items, g->off, g->col, F, w->vis, w->nx, full,
-                                          w->ctr);
-      G3_CHECK_LAUNCH();
-      ms_pull_pending<<<G3_NUM_SMS, 256, 0, s>>>(w->pend, g->off, w->vis, Fn, w->nx, w->lv,
-                                                 lnext, qn, w->ctr);
-      G3_CHECK_LAUNCH();
-    } else {
-      // Fn must be zero outside the new frontier: after a pull it is fully
-      // written, so clear it; after a push only the old frontier two levels
-      // back is set there, and clearing all of it is as cheap.
-      G3_TRY_CUDA(cudaMemsetAsync(Fn, 0, (size_t)nb * 8 + 8, s));
-      // touched vertices are collected in the heavy buffer
-      ms_push<<<g3_grid_for(qlen, 8, grid), 256, 0, s>>>(q, qlen, g->off, g->col, F, w->vis,
-                                                         w->nx, w->heavy, w->ctr, w->items);
-      G3_CHECK_LAUNCH();
-      ms_push_chunks<<<grid, 256, 0, s>>>(w->items, g->off, g->col, F, w->vis, w->nx, w->heavy,
-                                          w->ctr);
-      G3_CHECK_LAUNCH();
-      G3_TRY_CUDA(cudaMemcpyAsync(h + 2, w->ctr + 2, 8, cudaMemcpyDeviceToHost, s));
-      G3_TRY_CUDA(cudaStreamSynchronize(s));
-      const int64_t tl = (int64_t)h[2];
-      if (tl > 0) {
-        ms_push_finalize<<<g3_grid_for(tl, 256, grid), 256, 0, s>>>(
-            w->heavy, tl, w->nx, w->vis, Fn, w->lv, lnext, qn, g->off, w->ctr);
-        G3_CHECK_LAUNCH();
-      }
-    }
-    uint64_t* tf = F;
-    F = Fn;
-    Fn = tf;
-    int32_t* tq = q;
-    q = qn;
-    qn = tq;
-  }
-  if (n_levels) *n_levels = L;
-  stats.levels = L;
+  // the whole level loop: one graph launch, no host round trip per level
+  G3_TRY_CUDA(cudaGraphLaunch(w->gexec, s));
   ms_out<<<grid, 256, 0, s>>>(g->n, nb, k, n2o, w->vis, w->lv, level);
   G3_CHECK_LAUNCH();
   ms_roots_out<<<1, 64, 0, s>>>(w->d_roots, k, g->n, level);
   G3_CHECK_LAUNCH();
   G3_TRY_CUDA(cudaEventRecord(w->ev[1], s));
-  G3_TRY_CUDA(cudaMemcpyAsync(h + 5, w->ctr + 5, 16, cudaMemcpyDeviceToHost, s));
+  G3_TRY_CUDA(cudaMemcpyAsync(h, w->ctr, MS_NCTR * 8, cudaMemcpyDeviceToHost, s));
   G3_TRY_CUDA(cudaStreamSynchronize(s));
+  if (h[MS_ERANGE]) {
+    g3_set_error("g3_msbfs: a level exceeds 126, the int8 range of the output");
+    return G3_ERANGE;
+  }
+  const int32_t L = (int32_t)h[MS_LEVEL];
+  if (n_levels) *n_levels = L;
   if (ms) cudaEventElapsedTime(ms, w->ev[0], w->ev[1]);
+  g3_msbfs_stats stats;
+  memset(&stats, 0, sizeof(stats));
+  stats.levels = L;
+  stats.pull_levels = (int32_t)h[MS_PULLS];
+  stats.push_levels = (int32_t)h[MS_PUSHES];
+  stats.push_entries = (int64_t)h[MS_PUSHED];
   stats.pull_entries = (int64_t)h[5];
   stats.pull_vertices = (int64_t)h[6];
   w->last = stats;

@@ -149,17 +149,18 @@ def time_controllers(scale: int, seed: int, nroots: int, root_seed: int, configs
     return out
 
 
-FEATURES = "ratios"  # the feature set the controller's device code computes
+FEATURES = "ratios+size"  # the feature set the controller's device code computes
 
 
 def controller_opts(path: str, n_bfs: int, device="cuda", **base):
     """g3_bfs options for the trained controller in `path`, on top of the
-    options in `base`: the network with its margin and bin choice. Its
-    features are ratios of the searched graph's own counts (frontier and
-    unvisited sizes over n and nnz, bitmap words per frontier edge), so the
-    same network serves every graph size. Returns (opts, params tensor,
-    note); the tensor must outlive the searches. Raises when the file was
-    trained on another feature set."""
+    options in `base`: the network with its margin and bin choice, at every
+    graph size. Its features are ratios of the searched graph's own counts
+    (frontier and unvisited sizes over n and nnz, bitmap words per frontier
+    edge) plus the graph size itself, linear, which a bottom-up step's bitmap
+    walk grows with; trained at SCALE 20-24, the network extrapolates in that
+    one input. Returns (opts, params tensor, note); the tensor must outlive
+    the searches. Raises when the file was trained on another feature set."""
     import torch
     with open(path) as f:
         mj = json.load(f)
@@ -172,7 +173,7 @@ def controller_opts(path: str, n_bfs: int, device="cuda", **base):
     lo, hi = mj.get("n_bfs_range", [0, 0])
     where = "inside" if lo <= n_bfs <= hi else "outside"
     note = (f"the network decides every level (n_bfs {n_bfs}, {where} the trained sizes "
-            f"{lo}..{hi}; size-free features)")
+            f"{lo}..{hi})")
     return g3.opts(**kw), params, note
 
 
