@@ -9,16 +9,16 @@ Loss over a batch of B samples with per-output weights w_k:
     L = 1/(2B) * sum_b sum_k w_k (o_bk - y_bk)^2
 ReLU derivative is taken as 0 at z == 0.
 
-Features of a level (inputs), computed from the frontier statistics, all
-but feature 3 ratios of counts of the same graph (n vertices, nnz directed
-entries):
+Features of a level (inputs), from the frontier sizes and degree sums of the
+searched graph (n vertices, nnz directed entries):
     0 log2((1+n_f)/(1+n))    1 log2((1+m_f)/(1+nnz))
     2 log2((1+n_u)/(1+n))    3 n / 2^24 (the graph size, linear)
-    4 (max_id - min_id) / n   (0 for an empty frontier)
+    4 log2((1+m_f)/(1+n_f)) / 16 (mean frontier degree)
     5 log2((1+m_f)/(1+m_u))  6 log2((1+n) / (32 (1+m_f)))
     7 previous direction (0 TD, 1 BU)
-    8..11 fraction of frontier vertices with degree in
-          [0,32), [32,1024), [1024,32768), [32768, inf)
+    8 log2((1+m_u)/(1+n_u)) / 16 (mean unvisited degree)
+    9 log2((1+n_f)/(1+n_f of the previous level)) / 8 (frontier growth)
+   10 min(level, 32) / 32   11 1 - n_u / n (fraction visited)
 Outputs: o0 ~ ln(t_BU / t_TD) (bottom-up when o0 < 0), o1..o3 ~ log2 of the
 top-down bin thresholds T1 < T2 < T3.
 """
@@ -99,14 +99,14 @@ def train_adam(p, x, y, steps: int, lr: float = 1e-2, w=None, beta1: float = 0.9
     return p, np.array(losses)
 
 
-def features(n_f, m_f, n_u, m_u, id_min, id_max, n, nnz, prev_dir, hist4):
+def features(n_f, m_f, n_u, m_u, n, nnz, prev_dir, level, prev_nf):
     """Feature vector of one level (see the module docstring)."""
-    span = (id_max - id_min) / n if n_f > 0 and n > 0 else 0.0
-    tot = max(n_f, 1)
     return np.array([
         np.log2((1.0 + n_f) / (1.0 + n)), np.log2((1.0 + m_f) / (1.0 + nnz)),
         np.log2((1.0 + n_u) / (1.0 + n)), n / 2.0 ** 24,
-        span, np.log2((1.0 + m_f) / (1.0 + m_u)), np.log2((1.0 + n) / (32.0 * (1.0 + m_f))),
-        float(prev_dir),
-        hist4[0] / tot, hist4[1] / tot, hist4[2] / tot, hist4[3] / tot,
+        np.log2((1.0 + m_f) / (1.0 + n_f)) / 16.0, np.log2((1.0 + m_f) / (1.0 + m_u)),
+        np.log2((1.0 + n) / (32.0 * (1.0 + m_f))), float(prev_dir),
+        np.log2((1.0 + m_u) / (1.0 + n_u)) / 16.0,
+        np.log2((1.0 + n_f) / (1.0 + prev_nf)) / 8.0, min(level, 32) / 32.0,
+        (1.0 - n_u / n) if n > 0 else 0.0,
     ], dtype=np.float64)

@@ -179,8 +179,8 @@ __device__ __forceinline__ int deg_bucket(int64_t d) {
 // Per-thread statistics in 32-bit registers (a thread sees far fewer than
 // 2^32 vertices or edges per launch); reduced per block in 64 bits.
 // The degree histogram and the label range are kept only when the search
-// records its per-level statistics or the learned controller reads them
-// (Ctrl::full_stats); the direction rule needs only sizes and degree sums.
+// records its per-level statistics (Ctrl::full_stats); both controllers need
+// only sizes and degree sums.
 struct StatAcc {
   unsigned nf, mf, ex, h0, h1, h2, h3, mn, mx;
   bool full;
@@ -508,14 +508,21 @@ __device__ __forceinline__ void td_row_vec4(const TdArgs& a, WarpQueue& q, StatA
                                             int64_t nthr, int64_t steps) {
   const int64_t a0 = b & ~3ll;
   const int32_t vo = orig_of(a.o2n, v);
+  // the next step's entries are loaded before this step's claims, so the
+  // row read overlaps the visited probes and atomics instead of preceding them
+  int64_t j = a0 + 4 * t;
+  int4 x = make_int4(0, 0, 0, 0);
+  if (steps > 0 && j < e) x = *reinterpret_cast<const int4*>(a.col + j);
   for (int64_t s = 0; s < steps; ++s) {
-    const int64_t j = a0 + 4 * (t + s * nthr);
-    int4 x = make_int4(0, 0, 0, 0);
-    if (j < e) x = *reinterpret_cast<const int4*>(a.col + j);
+    const int64_t jn = j + 4 * nthr;
+    int4 xn = make_int4(0, 0, 0, 0);
+    if (s + 1 < steps && jn < e) xn = *reinterpret_cast<const int4*>(a.col + jn);
     const bool has[4] = {j >= b && j < e, j + 1 >= b && j + 1 < e, j + 2 >= b && j + 2 < e,
                          j + 3 >= b && j + 3 < e};
     const int32_t w[4] = {x.x, x.y, x.z, x.w};
     td_visit4(a, q, acc, has, w, vo);
+    j = jn;
+    x = xn;
   }
 }
 
@@ -1252,9 +1259,9 @@ __global__ void bitmap_to_q(Bufs B, int64_t nwords, Ctrl* c) {
 
 // ------------------------------------------------------------- controller
 // Learned controller: the 12-32-4 MLP of g3_mlp.cuh on the frontier record.
-__device__ void mlp_features(const Ctrl* c, int32_t nb, long long nnz, int prev_dir, float* f) {
-  mlp_features_raw(c->nf, c->mf, c->nu, c->mu, c->id_min, c->id_max, nb, nnz, prev_dir,
-                   c->hist, f);
+__device__ void mlp_features(const Ctrl* c, int32_t nb, long long nnz, int prev_dir,
+                             long long prev_nf, float* f) {
+  mlp_features_raw(c->nf, c->mf, c->nu, c->mu, nb, nnz, prev_dir, c->level, prev_nf, f);
 }
 
 __device__ __forceinline__ int clamp_thr(float lg, int lo, int hi) {
@@ -1325,7 +1332,7 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
       c->t2 = A.t2;
       c->t3 = A.t3;
       decide = d;
-      if (A.controller == G3_CTRL_LEARNED) mlp_features(c, A.nb, A.nnz, prev_dir, feat);
+      if (A.controller == G3_CTRL_LEARNED) mlp_features(c, A.nb, A.nnz, prev_dir, prev_nf, feat);
       reset_next(c);
     }
   }
@@ -2000,8 +2007,7 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
 
   G3_TRY_CUDA(cudaMemsetAsync(ws->visited, 0, (size_t)(ws->nwords + 1) * 4, s));
   const int cap = host_driven ? 0x7fffffff : GRAPH_LEVEL_CAP;
-  const int full_stats = o->controller == G3_CTRL_LEARNED || o->record_both ||
-                         (stats && max_stats > 0);
+  const int full_stats = o->record_both || (stats && max_stats > 0);
   if (mr) {
     bfs_roots_multi<<<1, 1024, 0, s>>>(mr->roots, mr->count, mr->lo,
                                        g->relabelled ? g->new_of_old : nullptr, nb, g->nnz,

@@ -14,36 +14,38 @@
 #define MLP_W2 (MLP_B1 + MLP_HID)
 #define MLP_B2 (MLP_W2 + MLP_OUT * MLP_HID)
 
-// Features of the frontier F_L (see the controller's documentation). All but
-// one are ratios of counts of the same graph, so that a network trained on
-// smaller graphs sees the same values for the same situation on a larger one:
+// Features of the frontier F_L (see the controller's documentation), all
+// from the frontier sizes and degree sums the expansion kernels count anyway
+// (n: vertices of the searched graph, nnz: its directed entries):
 //  0 log2((1+n_f)/(1+n))   1 log2((1+m_f)/(1+nnz))
 //  2 log2((1+n_u)/(1+n))   3 n / 2^24: the graph size, linear, because a
 //    bottom-up step's walk over the bitmap costs time in proportion to n
 //    while a small top-down step's cost does not grow with it
-//  4 (id_max-id_min)/n     5 log2((1+m_f)/(1+m_u))
+//  4 log2((1+m_f)/(1+n_f)) / 16: mean degree of the frontier
+//  5 log2((1+m_f)/(1+m_u))
 //  6 log2((1+n)/(32 (1+m_f))): bitmap words a bottom-up step walks per
 //    frontier edge a top-down step expands   7 previous direction
-//  8..11 fraction of F_L in the degree buckets [0,32) [32,1024) [1024,32768) rest
-// (n: vertices of the searched graph, nnz: its directed entries; the
-// unvisited edge fraction m_u/nnz is not an input, since features 1 and 5
-// determine it)
+//  8 log2((1+m_u)/(1+n_u)) / 16: mean degree of the unvisited vertices
+//  9 log2((1+n_f)/(1+n_f of the previous level)) / 8: frontier growth
+// 10 min(level, 32) / 32    11 1 - n_u / n: fraction of the graph visited
 __device__ __forceinline__ void mlp_features_raw(long long nf, long long mf, long long nu,
-                                                 long long mu, int id_min, int id_max, int32_t nb,
-                                                 long long nnz, int prev_dir,
-                                                 const long long* hist, float* f) {
+                                                 long long mu, int32_t nb, long long nnz,
+                                                 int prev_dir, int level, long long prev_nf,
+                                                 float* f) {
   const float fnf = (float)nf, fmf = (float)mf, fnu = (float)nu, fmu = (float)mu;
   const float fn = (float)nb, fe = (float)nnz;
   f[0] = log2f((1.f + fnf) / (1.f + fn));
   f[1] = log2f((1.f + fmf) / (1.f + fe));
   f[2] = log2f((1.f + fnu) / (1.f + fn));
   f[3] = fn * (1.f / 16777216.f);
-  f[4] = (nf > 0 && nb > 0) ? (float)(id_max - id_min) / fn : 0.f;
+  f[4] = log2f((1.f + fmf) / (1.f + fnf)) * (1.f / 16.f);
   f[5] = log2f((1.f + fmf) / (1.f + fmu));
   f[6] = log2f((1.f + fn) / (32.f * (1.f + fmf)));
   f[7] = (float)prev_dir;
-  const float tot = nf > 0 ? fnf : 1.f;
-  for (int k = 0; k < 4; ++k) f[8 + k] = (float)hist[k] / tot;
+  f[8] = log2f((1.f + fmu) / (1.f + fnu)) * (1.f / 16.f);
+  f[9] = log2f((1.f + fnf) / (1.f + (float)prev_nf)) * (1.f / 8.f);
+  f[10] = (float)(level < 32 ? level : 32) * (1.f / 32.f);
+  f[11] = nb > 0 ? 1.f - fnu / fn : 0.f;
 }
 
 // One warp evaluates the network for one feature vector: lane j is hidden

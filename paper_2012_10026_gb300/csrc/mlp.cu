@@ -154,16 +154,15 @@ __global__ void mlp_forward_k(const float* __restrict__ P, const float* __restri
 
 // Feature rows of logged levels, through the controller's own feature code.
 struct FeatIn {
-  long long nf, mf, nu, mu;
-  long long hist[4];
-  int id_min, id_max, level, prev_dir;
+  long long nf, mf, nu, mu, prev_nf;
+  int level, prev_dir;
 };
 
 __global__ void mlp_features_k(const FeatIn* in, int count, int32_t nb, int64_t nnz, float* x) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < count; s += gridDim.x * blockDim.x) {
     const FeatIn& r = in[s];
-    mlp_features_raw(r.nf, r.mf, r.nu, r.mu, r.id_min, r.id_max, nb, nnz, r.prev_dir,
-                     r.hist, x + (size_t)s * MLP_IN);
+    mlp_features_raw(r.nf, r.mf, r.nu, r.mu, nb, nnz, r.prev_dir, r.level, r.prev_nf,
+                     x + (size_t)s * MLP_IN);
   }
 }
 
@@ -222,12 +221,10 @@ extern "C" g3_status g3_mlp_features(const g3_level_stats* stats, int32_t count,
     h[i].mf = r.m_f;
     h[i].nu = r.n_u;
     h[i].mu = r.m_u;
-    for (int k = 0; k < 4; ++k) h[i].hist[k] = r.hist[k];
-    h[i].id_min = r.id_min;
-    h[i].id_max = r.id_max;
     h[i].level = r.level;
     // the previous level of the same search is the preceding record
     h[i].prev_dir = (r.level > 0 && i > 0) ? stats[i - 1].dir : 0;
+    h[i].prev_nf = (r.level > 0 && i > 0) ? stats[i - 1].n_f : 0;
   }
   FeatIn* d = nullptr;
   g3_status st = g3_alloc(&d, (size_t)count, s);

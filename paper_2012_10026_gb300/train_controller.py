@@ -117,9 +117,10 @@ def gated(o0, meta, margin):
 
 
 def time_controllers(scale: int, seed: int, nroots: int, root_seed: int, configs: dict,
-                     reps: int = 3, device="cuda"):
-    """Summed device ms of nroots searches per named g3_bfs_opts (the
-    minimum over reps for each root, 256 MB written between searches)."""
+                     reps: int = 3, device="cuda", tuned: bool = True):
+    """Summed device ms of nroots searches per named option set (dicts of
+    g3_bfs_opts fields, on top of the graph's autotuned options when tuned;
+    the minimum over reps for each root, 256 MB written between searches)."""
     import torch
     import graphgen
     n = 1 << scale
@@ -133,8 +134,15 @@ def time_controllers(scale: int, seed: int, nroots: int, root_seed: int, configs
     level = torch.empty(n, dtype=torch.int32, device=device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    base = {}
+    if tuned:  # tuning roots drawn apart from the timed ones, no cache
+        troots = graphgen.pick_roots(flags, 16, root_seed + 1000).tolist()
+        t, _ = g3.autotune_bfs(g, troots, parent, level, None, g3.opts())
+        base = dict(alpha=t.alpha, beta=t.beta, t1=t.t1, t2=t.t2, t3=t.t3,
+                    bu_reverse=t.bu_reverse, bu_kernel=t.bu_kernel)
     out = {}
-    for name, o in configs.items():
+    for name, kw in configs.items():
+        o = g3.opts(**dict(base, **kw))
         best = [float("inf")] * len(roots)
         for _ in range(reps + 1):  # the first round builds the level-loop graph
             for i, r in enumerate(roots):
@@ -149,17 +157,18 @@ def time_controllers(scale: int, seed: int, nroots: int, root_seed: int, configs
     return out
 
 
-FEATURES = "ratios+size"  # the feature set the controller's device code computes
+FEATURES = "sizes-and-sums"  # the feature set the controller's device code computes
 
 
 def controller_opts(path: str, n_bfs: int, device="cuda", **base):
     """g3_bfs options for the trained controller in `path`, on top of the
     options in `base`: the network with its margin and bin choice, at every
-    graph size. Its features are ratios of the searched graph's own counts
-    (frontier and unvisited sizes over n and nnz, bitmap words per frontier
-    edge) plus the graph size itself, linear, which a bottom-up step's bitmap
-    walk grows with; trained at SCALE 20-24, the network extrapolates in that
-    one input. Returns (opts, params tensor, note); the tensor must outlive
+    graph size. Its features come from the frontier sizes and degree sums
+    alone: ratios of the searched graph's own counts (frontier and unvisited
+    sizes over n and nnz, mean degrees, bitmap words per frontier edge,
+    frontier growth) plus the graph size itself, linear, which a bottom-up
+    step's bitmap walk grows with; trained at SCALE 20-24, the network
+    extrapolates in that one input. Returns (opts, params tensor, note); the tensor must outlive
     the searches. Raises when the file was trained on another feature set."""
     import torch
     with open(path) as f:
@@ -245,13 +254,15 @@ def main():
     summary["mlp_margin"] = int(round(min(best_m, 1e6) * 1000))
     # whether the network's bin thresholds beat the fixed ones: timed on the
     # same held-out graph, with the chosen margin
+    # (all three on the held-out graph's autotuned options)
     lo = dict(controller=g3.G3_CTRL_LEARNED, mlp_params=p, mlp_margin=summary["mlp_margin"])
     tt = time_controllers(max(args.scales), 97, args.roots, 98, {
-        "heuristic": g3.opts(),
-        "learned_bins": g3.opts(mlp_bins=1, **lo),
-        "learned_fixed_bins": g3.opts(mlp_bins=0, **lo)})
+        "heuristic": dict(controller=g3.G3_CTRL_HEURISTIC),
+        "learned_bins": dict(mlp_bins=1, **lo),
+        "learned_fixed_bins": dict(mlp_bins=0, **lo)})
     summary["holdout"]["ms"] = tt
-    summary["mlp_bins"] = 1 if tt["learned_bins"] < tt["learned_fixed_bins"] else 0
+    # the network's bins replace the tuned ones only when clearly faster
+    summary["mlp_bins"] = 1 if tt["learned_bins"] < 0.99 * tt["learned_fixed_bins"] else 0
     if args.eval_scale:
         # held-out graph: per-level times of both directions under the
         # heuristic's path; regret of each controller's choices on it

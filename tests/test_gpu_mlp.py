@@ -84,7 +84,8 @@ def test_features_match_oracle_on_real_levels():
         x = g3.g3_mlp_features(st, nb, nnz).cpu().numpy()
         for a, row in zip(st, x):
             prev = st[a["level"] - 1]["dir"] if a["level"] > 0 else 0
-            ref = mlp.features(a["n_f"], a["m_f"], a["n_u"], a["m_u"], a["id_min"], a["id_max"],
-                               nb, nnz, prev, a["hist"])
+            pnf = st[a["level"] - 1]["n_f"] if a["level"] > 0 else 0
+            ref = mlp.features(a["n_f"], a["m_f"], a["n_u"], a["m_u"], nb, nnz, prev,
+                               a["level"], pnf)
             assert np.allclose(row, ref, rtol=1e-5, atol=1e-5)
     g.free()

@@ -230,9 +230,9 @@ def test_learned_controller_random_params_stays_exact(kron16):
         assert np.array_equal(level, lref)
         assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
         for a in st[1:]:
-            f = mlp.features(a["n_f"], a["m_f"], a["n_u"], a["m_u"], a["id_min"], a["id_max"],
-                             ref["n_plus"], len(ref["col_r"]), st[a["level"] - 1]["dir"],
-                             a["hist"])
+            f = mlp.features(a["n_f"], a["m_f"], a["n_u"], a["m_u"], ref["n_plus"],
+                             len(ref["col_r"]), st[a["level"] - 1]["dir"], a["level"],
+                             st[a["level"] - 1]["n_f"])
             o = mlp.forward(mlp.init_params(5), f[None])[0]
             assert np.allclose(a["mlp_out"], o, rtol=1e-4, atol=1e-4)
             if abs(o[0]) > 1e-3:
