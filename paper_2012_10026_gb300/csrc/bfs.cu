@@ -456,6 +456,8 @@ __device__ __forceinline__ void wq_flush(WarpQueue& q, const TdArgs& a, StatAcc&
 // Appends up to four items per lane (want[k]); all 32 lanes call it together.
 __device__ __forceinline__ void wq_push4(WarpQueue& q, const bool want[4], const int32_t item[4],
                                          const TdArgs& a, StatAcc& acc) {
+  // most steps claim nothing (the visited probe already saw the bit set)
+  if (!__any_sync(0xffffffffu, want[0] | want[1] | want[2] | want[3])) return;
   const unsigned lt = g3_lanemask_lt();
   int at = q.cnt;
 #pragma unroll
@@ -517,8 +519,13 @@ __device__ __forceinline__ void td_row_vec4(const TdArgs& a, WarpQueue& q, StatA
     const int64_t jn = j + 4 * nthr;
     int4 xn = make_int4(0, 0, 0, 0);
     if (s + 1 < steps && jn < e) xn = *reinterpret_cast<const int4*>(a.col + jn);
-    const bool has[4] = {j >= b && j < e, j + 1 >= b && j + 1 < e, j + 2 >= b && j + 2 < e,
-                         j + 3 >= b && j + 3 < e};
+    bool has[4];
+    if (j >= b && j + 3 < e) {  // an interior step: all four entries
+      has[0] = has[1] = has[2] = has[3] = true;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) has[k] = j + k >= b && j + k < e;
+    }
     const int32_t w[4] = {x.x, x.y, x.z, x.w};
     td_visit4(a, q, acc, has, w, vo);
     j = jn;
