@@ -82,7 +82,8 @@ def parse_args():
                     help="bottom-up scans rows from the highest label (degree-aware order)")
     ap.add_argument("--bu-kernel", type=int, default=-1,
                     help="bottom-up kernels: 0 word pairs, 1 staged + word tiles, 2 word "
-                         "tiles (-1: the autotuner's choice, else the library default)")
+                         "tiles, 3 word pairs + word tiles (-1: the autotuner's choice, else "
+                         "the library default)")
     ap.add_argument("--out-split", type=int, default=-1,
                     help="output pass: 1 one pass, 2 two passes over label halves (-1: the "
                          "library default)")

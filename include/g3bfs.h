@@ -93,6 +93,10 @@ g3_status g3_build_csr(const int32_t* src, const int32_t* dst, int64_t m, int32_
  * neighbour in level k, then degree, then ID).
  * After the call the graph's CSR is the relabelled one over n_plus vertices
  * (rows ascending) and the permutation is kept for g3_bfs and g3_get_perm.
+ * Each component's vertices get consecutive labels (a component is finished
+ * before the next start is taken), and the label range of every vertex's
+ * component is kept too (8 bytes per vertex of V+): g3_bfs's output pass
+ * takes the reached set from its root's range instead of the visited bitmap.
  * Synchronises `stream`. Errors: G3_ESTATE (already relabelled), G3_ENOMEM,
  * G3_ECUDA. */
 g3_status g3_rcm_relabel(g3_graph* g, void* stream);
@@ -168,7 +172,11 @@ typedef struct {
                                array) when both outputs are device memory */
   int32_t bu_kernel;        /* bottom-up kernels: 0 (default) word pairs -- a
                                lane owns one vertex of each of two bitmap words
-                               -- on every level; 1 with bu_reverse, levels
+                               -- on levels with at least a quarter of the
+                               graph unvisited, and on the others a list of
+                               the unvisited vertices with a thread for each
+                               (Algorithm 6's shrinking active range); 1 with
+                               bu_reverse, levels
                                with at least a quarter of the graph unvisited
                                run the staged kernel (each CTA's next tile of
                                neighbors+ entries and visited words brought into
@@ -177,7 +185,9 @@ typedef struct {
                                kernel; without bu_reverse, word pairs; 2 word
                                tiles (a warp owns 32 words; dense tiles lane by
                                word, sparse ones as one compact list) on every
-                               level */
+                               level; 3 word pairs on the levels with at least
+                               a quarter of the graph unvisited, word tiles on
+                               the others */
   int32_t reserved[3];
 } g3_bfs_opts;
 
@@ -379,7 +389,7 @@ g3_status g3_tune_cache_store(const char* path, const g3_tune_entry* e);
  * in the caller's buffers. Synchronises.
  *   g3_autotune_bfs   : roots host (nroots original IDs), parent/level as for
  *                       g3_bfs; coordinate search, two passes, over alpha,
- *                       beta, (t1, t2, t3), bu_reverse and bu_kernel (0 or 1);
+ *                       beta, (t1, t2, t3), bu_reverse and bu_kernel (0, 1 or 3);
  *                       the controller stays.
  *   g3_autotune_msbfs : roots host (k <= 64), level as for g3_msbfs; full grid
  *                       over push_alpha x pull_warp_deg.

@@ -60,7 +60,7 @@ extern "C" void g3_graph_free(g3_graph* g) {
   cudaGetLastError();
   if (g->ws) g3_bfs_ws_free(g->ws);
   if (g->ms) g3_ms_ws_free(g->ms);
-  void* all[] = {g->off, g->col, g->old_of_new, g->new_of_old};
+  void* all[] = {g->off, g->col, g->old_of_new, g->new_of_old, g->comp_rng};
   for (void* p : all)
     if (p) cudaFreeAsync(p, 0);
   cudaStreamSynchronize(0);

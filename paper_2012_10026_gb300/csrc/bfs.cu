@@ -50,7 +50,13 @@
 #define LOG_MAX 4096           // per-level records kept on the device
 #define GRAPH_LEVEL_CAP 4096   // levels one graph launch may run
 
-enum { MODE_TD_Q = 0, MODE_TD_B = 1, MODE_BU_B = 2, MODE_BU_Q = 3, MODE_DONE = 4 };
+// Level kinds (the SWITCH branch a level runs): top-down from a queue or a
+// bitmap frontier, bottom-up from a bitmap or a queue frontier, the same on
+// a sparse level (vertex list, see bu_list_build), and the end.
+enum {
+  MODE_TD_Q = 0, MODE_TD_B = 1, MODE_BU_B = 2, MODE_BU_Q = 3, MODE_DONE = 4,
+  MODE_BU_BS = 5, MODE_BU_QS = 6, MODE_COUNT = 7
+};
 
 // Device-side controller record.
 struct Ctrl {
@@ -79,6 +85,11 @@ struct Ctrl {
   int cap;   // the controller ends the search at this level (graph launches)
   unsigned int err;  // a kernel's bounded wait ran out (the search stops; G3_ETIMEOUT)
   int full_stats;    // keep the degree histogram and label range of each frontier
+  // rng_ok: the search reaches exactly the labels [rng_lo, rng_hi), the root's
+  // component (known after a full RCM relabel); else the visited bitmap tells
+  int rng_ok, rng_lo, rng_hi;
+  int bu_sparse;                  // this bottom-up level runs over a vertex list
+  unsigned long long bl_len;      // that list's length
 };
 
 // Per-level record written by the controller (and bfs_root for level 0).
@@ -151,9 +162,11 @@ struct g3_bfs_ws {
   cudaEvent_t ev[6];
   // resident-grid sizes (SMs x blocks per SM) per kernel
   int grid_front, grid_bins, grid_bu, grid_tiles, grid_staged, grid_conv, grid_tr, grid_tr4;
+  int grid_lb, grid_lp;  // sparse bottom-up: list build, list pull
   // graph mode: instantiated level loop and the options it was built for
   cudaGraphExec_t gexec;
   g3_bfs_opts gopts;
+  int gfull;  // the statistics mode the cached graph's kernels were built for
 };
 
 void g3_bfs_ws_free(g3_bfs_ws* ws) {
@@ -180,20 +193,23 @@ __device__ __forceinline__ int deg_bucket(int64_t d) {
 // 2^32 vertices or edges per launch); reduced per block in 64 bits.
 // The degree histogram and the label range are kept only when the search
 // records its per-level statistics (Ctrl::full_stats); both controllers need
-// only sizes and degree sums.
-struct StatAcc {
+// only sizes and degree sums. MODE 0 keeps sizes and sums only, 1 everything,
+// 2 decides at run time from Ctrl::full_stats (a kernel instantiated for
+// MODE 0 or 1 is launched only when that matches).
+template <int MODE>
+struct StatAccT {
   unsigned nf, mf, ex, h0, h1, h2, h3, mn, mx;
   bool full;
   __device__ void init(const Ctrl* c) {
     nf = mf = ex = h0 = h1 = h2 = h3 = 0;
     mn = 0xFFFFFFFFu;
     mx = 0;
-    full = c->full_stats != 0;
+    full = MODE == 2 ? c->full_stats != 0 : MODE == 1;
   }
   __device__ void add_vertex(int32_t v, int64_t d) {
     nf++;
     mf += (unsigned)d;
-    if (!full) return;
+    if (MODE == 0 || !full) return;
     int b = deg_bucket(d);
     h0 += b == 0;
     h1 += b == 1;
@@ -206,17 +222,20 @@ struct StatAcc {
     __shared__ unsigned long long s[8][7];
     __shared__ unsigned int smn[8], smx[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nk = MODE == 0 ? 3 : 7;
     unsigned long long v[7] = {nf, mf, ex, h0, h1, h2, h3};
     unsigned a = mn, b = mx;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
 #pragma unroll
-      for (int k = 0; k < 7; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-      a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
-      b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+      for (int k = 0; k < nk; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+      if (MODE != 0) {
+        a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+      }
     }
     if (lane == 0) {
-      for (int k = 0; k < 7; ++k) s[warp][k] = v[k];
+      for (int k = 0; k < nk; ++k) s[warp][k] = v[k];
       smn[warp] = a;
       smx[warp] = b;
     }
@@ -225,13 +244,14 @@ struct StatAcc {
       unsigned long long t[7] = {0, 0, 0, 0, 0, 0, 0};
       unsigned tmn = 0xFFFFFFFFu, tmx = 0;
       for (int w = 0; w < nw; ++w) {
-        for (int k = 0; k < 7; ++k) t[k] += s[w][k];
+        for (int k = 0; k < nk; ++k) t[k] += s[w][k];
         tmn = min(tmn, smn[w]);
         tmx = max(tmx, smx[w]);
       }
       if (t[0]) atomicAdd(&c->nx_nf, t[0]);
       if (t[1]) atomicAdd(&c->nx_mf, t[1]);
       if (t[2]) atomicAdd(&c->nx_exam, t[2]);
+      if (MODE == 0) return;
       for (int k = 0; k < 4; ++k)
         if (t[3 + k]) atomicAdd(&c->nx_hist[k], t[3 + k]);
       if (t[0]) {
@@ -241,6 +261,7 @@ struct StatAcc {
     }
   }
 };
+using StatAcc = StatAccT<2>;
 
 __device__ __forceinline__ bool td_claim(uint32_t* visited, int32_t w) {
   const uint32_t bit = 1u << (w & 31);
@@ -262,12 +283,24 @@ __device__ __forceinline__ void reset_next(Ctrl* c) {
   c->nx_max = 0;
   c->g_pack = 0;
   c->conv_len = 0;
+  c->bl_len = 0;
 }
 
 __device__ __forceinline__ int mode_of(const Ctrl* c) {
   if (c->nf <= 0) return MODE_DONE;
   if (c->dir == G3_DIR_TD) return c->fmt_queue ? MODE_TD_Q : MODE_TD_B;
+  if (c->bu_sparse) return c->fmt_queue ? MODE_BU_QS : MODE_BU_BS;
   return c->fmt_queue ? MODE_BU_Q : MODE_BU_B;
+}
+
+// A bottom-up level with under 4 % of the graph unvisited runs over a list
+// of its unvisited vertices (bu_kernel 0); above that the word-pair kernel's
+// coalesced walk is the faster one (measured on Kronecker graphs).
+#ifndef BU_LIST_PM
+#define BU_LIST_PM 40
+#endif
+__host__ __device__ __forceinline__ bool bu_sparse_level(long long nu, int32_t nb) {
+  return nu * 1000 < (long long)nb * BU_LIST_PM;
 }
 
 __device__ __forceinline__ void log_frontier(LevelLog* log, const Ctrl* c) {
@@ -293,13 +326,21 @@ __device__ __forceinline__ void log_frontier(LevelLog* log, const Ctrl* c) {
 
 // ------------------------------------------------------------------- init
 // Sets up F_0 = {root} (root_new < 0 or >= nb: no BFS-graph vertex). The
-// visited bitmap has been cleared on the stream before.
-__global__ void bfs_root(const int32_t* new_of_old, int32_t root, int32_t nb, int64_t nnz,
-                         const int64_t* off, uint32_t* visited, PlOut plo, int32_t* q, Ctrl* c,
-                         LevelLog* log, int t1, int t2, int t3, int cap, int full_stats) {
+// visited bitmap has been cleared on the stream before. comp (nullable): the
+// label range of each label's component.
+__global__ void bfs_root(const int32_t* new_of_old, const int2* comp, int32_t root, int32_t nb,
+                         int64_t nnz, const int64_t* off, uint32_t* visited, PlOut plo,
+                         int32_t* q, Ctrl* c, LevelLog* log, int t1, int t2, int t3, int cap,
+                         int full_stats) {
   int32_t r = new_of_old ? new_of_old[root] : root;
   memset(c, 0, sizeof(Ctrl));
   reset_next(c);
+  if (comp) {  // an isolated root reaches no label: the empty range
+    const int2 cr = (r >= 0 && r < nb) ? comp[r] : make_int2(0, 0);
+    c->rng_ok = 1;
+    c->rng_lo = cr.x;
+    c->rng_hi = cr.y;
+  }
   c->full_stats = full_stats;
   c->t1 = t1;
   c->t2 = t2;
@@ -677,18 +718,57 @@ __device__ __forceinline__ int32_t bu_scan_rest(const int32_t* __restrict__ col,
   return -1;
 }
 
+// Rest of a row after a missed first probe, four entries per step: their
+// four column loads and then their four frontier probes are in flight
+// together, and the first hit in scan order wins, so k (entries examined, up
+// to and including the parent) is the same as for a one-at-a-time scan.
+// Entries past the row's end are never loaded.
 template <int REV>
+__device__ __forceinline__ int32_t bu_scan_rest4(const int32_t* __restrict__ col,
+                                                 const uint32_t* __restrict__ fcur, int64_t b,
+                                                 int64_t e, int64_t& k) {
+  const int64_t d = e - b;
+  while (k < d) {
+    int32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t kk = k + q;
+      w[q] = kk < d ? __ldg(&col[REV ? e - 1 - kk : b + kk]) : -1;
+    }
+    bool h[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[q] = w[q] >= 0 && in_frontier(fcur, w[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (h[q]) {
+        k += q + 1;
+        return w[q];
+      }
+    k = k + 4 < d ? k + 4 : d;
+  }
+  return -1;
+}
+
+// Bottom-up level over word pairs (Algorithms 5 and 6): a warp owns two
+// consecutive words of the visited bitmap per grid step and lane i the
+// vertex of bit i of each, so the neighbors+ loads of a warp are coalesced,
+// and two vertices per lane are in flight. FULL: the per-level histogram and
+// label range are kept too (a separate instantiation, so that the default
+// one carries only the counters the controllers read).
+template <int REV, int FULL>
 __global__ void __launch_bounds__(256, 6) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
                                                Bufs B, const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
                                                const int2* __restrict__ nplus, PlOut plo,
-                                               Ctrl* c) {
-  if (c->dir != G3_DIR_BU) return;
+                                               Ctrl* c, int sparse_to_tiles) {
+  // sparse_to_tiles: levels with under a quarter of the graph unvisited are
+  // left to the word-tile kernel launched beside this one
+  if (c->dir != G3_DIR_BU || (sparse_to_tiles && !bu_dense(c, nb))) return;
   const uint32_t* __restrict__ fcur = (c->fsel ? B.f[1] : B.f[0]);
   uint32_t* __restrict__ fnext = (c->fsel ? B.f[0] : B.f[1]);
   const int32_t lnext = c->level + 1;
   const int32_t* __restrict__ o2n = B.o2n;
-  StatAcc acc;
+  StatAccT<FULL> acc;
   acc.init(c);
   const int lane = threadIdx.x & 31;
   // word and vertex indices fit 32 bits (nb < 2^31); row offsets stay 64-bit
@@ -782,35 +862,114 @@ __global__ void __launch_bounds__(256, 6) bu_pull(int32_t nb, int64_t nwords, ui
   acc.flush(c);
 }
 
-// Rest of a row after a missed first probe, four entries per step: their
-// four column loads and then their four frontier probes are in flight
-// together, and the first hit in scan order wins, so k (entries examined, up
-// to and including the parent) is the same as for a one-at-a-time scan.
-// Entries past the row's end are never loaded.
-template <int REV>
-__device__ __forceinline__ int32_t bu_scan_rest4(const int32_t* __restrict__ col,
-                                                 const uint32_t* __restrict__ fcur, int64_t b,
-                                                 int64_t e, int64_t& k) {
-  const int64_t d = e - b;
-  while (k < d) {
-    int32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t kk = k + q;
-      w[q] = kk < d ? __ldg(&col[REV ? e - 1 - kk : b + kk]) : -1;
+// Bottom-up on a sparse level (Algorithm 6's shrinking of the active range,
+// taken down to single vertices). Walking the bitmap two words per warp step
+// costs a load latency per step even where every vertex is visited, which
+// dominates a level with a few thousand unvisited vertices in a million
+// words. Instead bu_list_build lists the unvisited vertices (a lane per
+// word, one atomic per warp to place its slice) and clears the next-frontier
+// words, and bu_list_pull gives every listed vertex its own thread, all in
+// flight at once; a found vertex sets its bits in the next frontier and the
+// visited bitmap with atomic ORs. The list goes into the queue that is not
+// the current frontier.
+__global__ void __launch_bounds__(256) bu_list_build(Bufs B, int64_t nwords, int32_t nb,
+                                                     const uint32_t* __restrict__ visited,
+                                                     Ctrl* c) {
+  if (c->dir != G3_DIR_BU) return;
+  uint32_t* __restrict__ fnext = (c->fsel ? B.f[0] : B.f[1]);
+  int32_t* __restrict__ list = (c->qsel ? B.q[0] : B.q[1]);
+  const int lane = threadIdx.x & 31;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  // the loop bound is uniform over the block, so whole warps iterate together
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nwords; base += nthr) {
+    const int64_t w = base + threadIdx.x;
+    uint32_t unv = 0u;
+    if (w < nwords) {
+      const int64_t left = (int64_t)nb - w * 32;  // vertices of this word in the graph
+      const uint32_t valid = left >= 32 ? 0xFFFFFFFFu : (left > 0 ? (1u << left) - 1u : 0u);
+      unv = ~visited[w] & valid;
+      fnext[w] = 0u;
     }
-    bool h[4];
+    const unsigned cnt = __popc(unv);
+    unsigned inc = cnt;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) h[q] = w[q] >= 0 && in_frontier(fcur, w[q]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (h[q]) {
-        k += q + 1;
-        return w[q];
-      }
-    k = k + 4 < d ? k + 4 : d;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, inc, 31);
+    unsigned long long at = 0;
+    if (lane == 31 && total) at = atomicAdd(&c->bl_len, (unsigned long long)total);
+    at = __shfl_sync(0xffffffffu, at, 31);
+    unsigned long long pos = at + inc - cnt;
+    while (unv) {
+      list[pos++] = (int32_t)(w * 32 + (__ffs(unv) - 1));
+      unv &= unv - 1u;
+    }
   }
-  return -1;
+}
+
+template <int REV>
+__global__ void __launch_bounds__(256) bu_list_pull(int32_t nb, int64_t nwords, uint32_t* visited,
+                                                    Bufs B, const int64_t* __restrict__ off,
+                                                    const int32_t* __restrict__ col,
+                                                    const int2* __restrict__ nplus, PlOut plo,
+                                                    Ctrl* c, int unused) {
+  if (c->dir != G3_DIR_BU) return;
+  const uint32_t* __restrict__ fcur = (c->fsel ? B.f[1] : B.f[0]);
+  uint32_t* fnext = (c->fsel ? B.f[0] : B.f[1]);
+  const int32_t* __restrict__ list = (c->qsel ? B.q[0] : B.q[1]);
+  const int32_t lnext = c->level + 1;
+  const int32_t* __restrict__ o2n = B.o2n;
+  StatAcc acc;
+  acc.init(c);
+  const int64_t len = (int64_t)c->bl_len;
+  const int lane = threadIdx.x & 31;
+  // whole warps iterate together (the bound is uniform over a warp), so the
+  // word grouping below may name all 32 lanes
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < len;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    const int32_t v = i < len ? list[i] : -1;
+    int32_t p = -1;
+    if (v >= 0) {
+      int64_t b = 0, e = 0;
+      int32_t x = -1, d = 0;
+      if (REV) {  // degree-aware order: the row's last entry first
+        const int2 t = nplus[v];
+        x = t.x;
+        d = t.y;
+      } else {
+        b = off[v];
+        e = off[v + 1];
+        d = (int32_t)(e - b);
+        if (d) x = col[b];
+      }
+      p = (x >= 0 && in_frontier(fcur, x)) ? x : -1;
+      int64_t k = d > 0 ? 1 : 0;
+      if (p < 0 && d > 1) {
+        if (REV) {
+          e = off[v + 1];
+          b = e - d;
+        }
+        p = bu_scan_rest<REV>(col, fcur, b, e, k);
+      }
+      acc.ex += (unsigned)k;
+      if (p >= 0) {
+        pl_put(plo, v, o2n ? __ldg(&o2n[p]) : p, lnext);
+        acc.add_vertex(v, d);
+      }
+    }
+    // the list ascends within each warp's slice, so neighbouring lanes often
+    // share a bitmap word: one atomic OR per distinct word and warp
+    const unsigned grp = __match_any_sync(0xffffffffu, v >= 0 ? (v >> 5) : -1);
+    const uint32_t bits = __reduce_or_sync(grp, p >= 0 ? 1u << (v & 31) : 0u);
+    if (bits && (__ffs(grp) - 1) == lane) {
+      atomicOr(&fnext[v >> 5], bits);
+      atomicOr(&visited[v >> 5], bits);
+    }
+  }
+  acc.flush(c);
 }
 
 // One round of the bottom-up search for up to U vertices per lane (v[u] < 0:
@@ -1287,6 +1446,7 @@ struct CtrlArgs {
   LevelLog* log;
   int graph_mode;
   cudaGraphConditionalHandle h_loop;
+  int bu_list;  // sparse bottom-up levels run over a vertex list
 };
 
 // After the expansion of level L: record where the produced frontier lives,
@@ -1297,6 +1457,8 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
   __shared__ float feat[12];
   __shared__ int decide, active;
   const int lane = threadIdx.x;
+  MlpLane W;  // the weights are on their way while lane 0 updates the record
+  if (A.controller == G3_CTRL_LEARNED) mlp_load_lane(A.mlp, W);
   if (lane == 0) {
     active = c->mode != MODE_DONE && c->nf > 0;
     if (active) {
@@ -1346,7 +1508,7 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
   __syncwarp();
   if (active && A.controller == G3_CTRL_LEARNED) {
     float out[4];
-    mlp_eval_warp(A.mlp, feat, out);
+    mlp_eval_lane(W, feat, out);
     if (lane == 0) {
       for (int k = 0; k < 4; ++k) c->mlp_out[k] = out[k];
       // inside the margin the alpha/beta rule's direction stands
@@ -1366,6 +1528,7 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
   if (lane == 0) {
     if (active) {
       c->dir = decide;
+      c->bu_sparse = decide == G3_DIR_BU && A.bu_list && bu_sparse_level(c->nu, A.nb);
       c->mode = c->err ? MODE_DONE : mode_of(c);
       if (c->mode != MODE_DONE) log_frontier(A.log, c);
     }
@@ -1382,15 +1545,35 @@ __global__ void bfs_select(const Ctrl* c, cudaGraphConditionalHandle h_mode) {
 }
 
 // --------------------------------------------------------- output mapping
+// Whether label x was reached. A search reaches exactly its root's connected
+// component, and after a full RCM relabel that component is one range of
+// labels, so the test is two compares instead of a probe of the visited
+// bitmap (a random 4-byte read per vertex, half of this pass's L2 requests).
+struct Reach {
+  const uint32_t* visited;
+  int32_t nb, lo, hi;
+  int ok;
+};
+
+__device__ __forceinline__ Reach reach_of(const Ctrl* c, const uint32_t* visited, int32_t nb) {
+  return Reach{visited, nb, c->rng_lo, c->rng_hi, c->rng_ok};
+}
+
+__device__ __forceinline__ bool reached(const Reach& R, int32_t x) {
+  if (R.ok) return x >= R.lo && x < R.hi;
+  return x < R.nb && ((__ldg(&R.visited[x >> 5]) >> (x & 31)) & 1u);
+}
+
 __global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
                               const int32_t* __restrict__ new_of_old,
-                              const uint32_t* __restrict__ visited, PlOut plo,
+                              const uint32_t* __restrict__ visited, const Ctrl* c, PlOut plo,
                               int32_t* parent, int32_t* level) {
+  const Reach R = reach_of(c, visited, nb);
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     int32_t p = -1, l = -1;
     const int32_t x = new_of_old ? new_of_old[v] : (int32_t)v;
-    if (x < nb && ((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u)) {
+    if (reached(R, x)) {
       const int2 t = pl_decode(plo, plo.pl[x], x);
       p = t.x;
       l = t.y;
@@ -1413,8 +1596,9 @@ __global__ void bfs_translate(int32_t n, int32_t nb, int32_t root,
 __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int32_t root,
                                                       const int32_t* __restrict__ new_of_old,
                                                       const uint32_t* __restrict__ visited,
-                                                      PlOut plo, int32_t* parent,
+                                                      const Ctrl* c, PlOut plo, int32_t* parent,
                                                       int32_t* level) {
+  const Reach R = reach_of(c, visited, nb);
   const int64_t n4 = n >> 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1432,8 +1616,7 @@ __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int
     }
     bool r[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      r[k] = x[k] < nb && ((__ldg(&visited[x[k] >> 5]) >> (x[k] & 31)) & 1u);
+    for (int k = 0; k < 4; ++k) r[k] = reached(R, x[k]);
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) w[k] = r[k] ? __ldg(&plo.pl[x[k]]) : 0u;
@@ -1456,7 +1639,7 @@ __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int
   if (v < n) {
     int32_t p = -1, l = -1;
     const int32_t xv = new_of_old ? new_of_old[v] : (int32_t)v;
-    if (xv < nb && ((__ldg(&visited[xv >> 5]) >> (xv & 31)) & 1u)) {
+    if (reached(R, xv)) {
       const int2 t = pl_decode(plo, plo.pl[xv], xv);
       p = t.x;
       l = t.y;
@@ -1485,11 +1668,9 @@ __global__ void __launch_bounds__(256) bfs_translate4(int32_t n, int32_t nb, int
 // levels, and those in the side table, are left pending for pass 2, which
 // decodes them from the packed word). Needs bits >= 4 and 16-byte aligned
 // outputs.
-__device__ __forceinline__ uint32_t tr_pass1_one(int32_t x, int32_t nb, int32_t split,
-                                                 const uint32_t* __restrict__ visited,
+__device__ __forceinline__ uint32_t tr_pass1_one(int32_t x, int32_t split, const Reach& R,
                                                  const PlOut& plo, uint32_t lmax) {
-  const bool reached = x < nb && ((__ldg(&visited[x >> 5]) >> (x & 31)) & 1u);
-  if (!reached) return lmax - 1u;
+  if (!reached(R, x)) return lmax - 1u;
   const uint32_t pend = ((uint32_t)x << plo.bits) | lmax;
   if (x >= split) return pend;
   const uint32_t w = __ldg(&plo.pl[x]);
@@ -1499,21 +1680,23 @@ __device__ __forceinline__ uint32_t tr_pass1_one(int32_t x, int32_t nb, int32_t 
 __global__ void __launch_bounds__(256) bfs_translate_p1(int32_t n, int32_t nb, int32_t split,
                                                         const int32_t* __restrict__ new_of_old,
                                                         const uint32_t* __restrict__ visited,
-                                                        PlOut plo, uint32_t* rec) {
+                                                        const Ctrl* c, PlOut plo,
+                                                        uint32_t* rec) {
+  const Reach R = reach_of(c, visited, nb);
   const uint32_t lmax = (1u << plo.bits) - 1u;
   const int64_t n4 = n >> 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int4 xs = __ldcs(reinterpret_cast<const int4*>(new_of_old) + i);
     uint4 r;
-    r.x = tr_pass1_one(xs.x, nb, split, visited, plo, lmax);
-    r.y = tr_pass1_one(xs.y, nb, split, visited, plo, lmax);
-    r.z = tr_pass1_one(xs.z, nb, split, visited, plo, lmax);
-    r.w = tr_pass1_one(xs.w, nb, split, visited, plo, lmax);
+    r.x = tr_pass1_one(xs.x, split, R, plo, lmax);
+    r.y = tr_pass1_one(xs.y, split, R, plo, lmax);
+    r.z = tr_pass1_one(xs.z, split, R, plo, lmax);
+    r.w = tr_pass1_one(xs.w, split, R, plo, lmax);
     __stcs(reinterpret_cast<uint4*>(rec) + i, r);
   }
   const int64_t v = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (v < n) rec[v] = tr_pass1_one(new_of_old[v], nb, split, visited, plo, lmax);
+  if (v < n) rec[v] = tr_pass1_one(new_of_old[v], split, R, plo, lmax);
 }
 
 __device__ __forceinline__ int2 tr_pass2_one(uint32_t r, const PlOut& plo, uint32_t lmax) {
@@ -1656,14 +1839,22 @@ static g3_status ws_create(g3_graph* g, g3_bfs_ws** out) {
   }
   ws->grid_front = resident_grid(td_front, 256);
   ws->grid_bins = resident_grid(td_bins, 256);
-  ws->grid_bu = resident_grid(bu_pull<1>, 256);
-  int g0 = resident_grid(bu_pull<0>, 256);
+  ws->grid_bu = resident_grid(bu_pull<1, 0>, 256);
+  int g0 = resident_grid(bu_pull<0, 0>, 256);
+  if (g0 < ws->grid_bu) ws->grid_bu = g0;
+  g0 = resident_grid(bu_pull<1, 1>, 256);
+  if (g0 < ws->grid_bu) ws->grid_bu = g0;
+  g0 = resident_grid(bu_pull<0, 1>, 256);
   if (g0 < ws->grid_bu) ws->grid_bu = g0;
   ws->grid_tiles = resident_grid(bu_tiles<1, 4>, 32 * BU_WARPS);
   g0 = resident_grid(bu_tiles<0, 4>, 32 * BU_WARPS);
   if (g0 < ws->grid_tiles) ws->grid_tiles = g0;
   ws->grid_staged = resident_grid(bu_staged, BS_THREADS);
   ws->grid_conv = resident_grid(bitmap_to_q, 256);
+  ws->grid_lb = resident_grid(bu_list_build, 256);
+  ws->grid_lp = resident_grid(bu_list_pull<1>, 256);
+  g0 = resident_grid(bu_list_pull<0>, 256);
+  if (g0 < ws->grid_lp) ws->grid_lp = g0;
   ws->grid_tr = resident_grid(bfs_translate, 256);
   ws->grid_tr4 = resident_grid(bfs_translate4, 256);
   *out = ws;
@@ -1704,24 +1895,41 @@ struct Launch {
   const g3_bfs_opts* o;
   Bufs B;
   int64_t nb1;
+  int full_stats;  // the kernels keep the per-level histogram and label range
 };
+
+// The word-pair bottom-up kernel for a scan order and statistics mode.
+static void* bu_pull_fn(int rev, int full) {
+  return rev ? (full ? (void*)bu_pull<1, 1> : (void*)bu_pull<1, 0>)
+             : (full ? (void*)bu_pull<0, 1> : (void*)bu_pull<0, 0>);
+}
+
+static bool bu_uses_list(const g3_bfs_opts& o) { return o.bu_kernel == 0; }
 
 static CtrlArgs ctrl_args(const Launch& S, int graph_mode, cudaGraphConditionalHandle h_loop) {
   return CtrlArgs{S.ws->nb,     S.g->nnz,        S.o->controller,
                   S.o->alpha,   S.o->beta,       S.o->mlp_params,
                   S.o->mlp_margin * 1e-3f,       S.o->mlp_bins,   S.o->t1,
                   S.o->t2,      S.o->t3,         S.ws->log,
-                  graph_mode,   h_loop};
+                  graph_mode,   h_loop,          bu_uses_list(*S.o)};
 }
 
 // Which bottom-up kernels the options select: bu_kernel 0 (default) word
-// pairs on every level; 1 the staged kernel on dense levels and the
+// pairs on dense levels and the vertex-list kernels on sparse ones; 1 the
+// staged kernel on dense levels and the
 // word-tile kernel on the others when rows are scanned in the degree-aware
-// order (word pairs in CSR order); 2 word tiles on every level.
+// order (word pairs in CSR order); 2 word tiles on every level; 3 word pairs
+// on dense levels and word tiles on the others. Where two kernels share a
+// level kind, each returns at once on the levels that are the other's.
 static bool bu_uses_staged(const g3_bfs_opts& o) { return o.bu_kernel == 1 && o.bu_reverse; }
 static bool bu_uses_tiles(const g3_bfs_opts& o) {
-  return o.bu_kernel == 2 || bu_uses_staged(o);
+  return o.bu_kernel == 2 || o.bu_kernel == 3 || bu_uses_staged(o);
 }
+static bool bu_uses_pairs(const g3_bfs_opts& o) {
+  return o.bu_kernel == 3 || !bu_uses_tiles(o);
+}
+// the flag both kernels of a split level kind get (skip_dense, sparse_to_tiles)
+static int bu_split(const g3_bfs_opts& o) { return bu_uses_staged(o) || o.bu_kernel == 3; }
 static int bu_tiles_grid(const g3_bfs_ws* ws) {
   return cap_grid((ws->nwords + 31) / 32, BU_WARPS, ws->grid_tiles);
 }
@@ -1740,7 +1948,7 @@ static g3_status launch_level(const Launch& S, int mode, int64_t nf, cudaEvent_t
   if (mode == MODE_TD_B) {
     bitmap_to_q<<<cap_grid(ws->nwords, 256, ws->grid_conv), 256, 0, s>>>(S.B, ws->nwords, c);
     G3_CHECK_LAUNCH();
-  } else if (mode == MODE_BU_Q) {
+  } else if (mode == MODE_BU_Q || mode == MODE_BU_QS) {
     bm_clear<<<g3_grid_for(ws->nwords, 256), 256, 0, s>>>(S.B, ws->nwords, c);
     G3_CHECK_LAUNCH();
     q_to_bitmap<<<g3_grid_for(nf, 256), 256, 0, s>>>(S.B, c);
@@ -1754,31 +1962,41 @@ static g3_status launch_level(const Launch& S, int mode, int64_t nf, cudaEvent_t
     td_bins<<<ws->grid_bins, 256, 0, s>>>(S.g->off, S.g->col, ws->visited, ws->plo, S.B,
                                           ws->bins, ws->goff, S.nb1, c);
     G3_CHECK_LAUNCH();
-  } else if (bu_uses_tiles(*S.o)) {
+  } else if (mode == MODE_BU_BS || mode == MODE_BU_QS) {
+    bu_list_build<<<cap_grid(ws->nwords, 256, ws->grid_lb), 256, 0, s>>>(S.B, ws->nwords, ws->nb,
+                                                                         ws->visited, c);
+    G3_CHECK_LAUNCH();
+    if (S.o->bu_reverse)
+      bu_list_pull<1><<<ws->grid_lp, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.B, S.g->off,
+                                                  S.g->col, ws->nplus, ws->plo, c, 0);
+    else
+      bu_list_pull<0><<<ws->grid_lp, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.B, S.g->off,
+                                                  S.g->col, ws->nplus, ws->plo, c, 0);
+    G3_CHECK_LAUNCH();
+  } else {
     int64_t nwords = ws->nwords;
     int32_t nb = ws->nb;
     const int64_t* off = S.g->off;
     const int32_t* col = S.g->col;
     Bufs B = S.B;
-    int skip = bu_uses_staged(*S.o);
-    void* args[] = {&nb, &nwords, &ws->visited, &B, &off, &col, &ws->nplus, &ws->plo, &c, &skip};
-    if (skip) {
+    int split = bu_split(*S.o);
+    void* args[] = {&nb, &nwords, &ws->visited, &B, &off, &col, &ws->nplus, &ws->plo, &c, &split};
+    if (bu_uses_staged(*S.o)) {
       G3_TRY_CUDA(cudaLaunchKernel((void*)bu_staged, dim3(bu_staged_grid(ws)), dim3(BS_THREADS),
                                    args, 0, s));
       g3_count_launch();
     }
-    G3_TRY_CUDA(cudaLaunchKernel(bu_tiles_fn(S.o->bu_reverse), dim3(bu_tiles_grid(ws)),
-                                 dim3(32 * BU_WARPS), args, 0, s));
-    g3_count_launch();
-  } else {
-    const int grid = cap_grid(ws->nwords, 16, ws->grid_bu);
-    if (S.o->bu_reverse)
-      bu_pull<1><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.B, S.g->off, S.g->col,
-                                      ws->nplus, ws->plo, c);
-    else
-      bu_pull<0><<<grid, 256, 0, s>>>(ws->nb, ws->nwords, ws->visited, S.B, S.g->off, S.g->col,
-                                      ws->nplus, ws->plo, c);
-    G3_CHECK_LAUNCH();
+    if (bu_uses_pairs(*S.o)) {
+      void* fn = bu_pull_fn(S.o->bu_reverse, S.full_stats);
+      G3_TRY_CUDA(cudaLaunchKernel(fn, dim3(cap_grid(ws->nwords, 16, ws->grid_bu)), dim3(256),
+                                   args, 0, s));
+      g3_count_launch();
+    }
+    if (bu_uses_tiles(*S.o)) {
+      G3_TRY_CUDA(cudaLaunchKernel(bu_tiles_fn(S.o->bu_reverse), dim3(bu_tiles_grid(ws)),
+                                   dim3(32 * BU_WARPS), args, 0, s));
+      g3_count_launch();
+    }
   }
   return G3_OK;
 }
@@ -1821,24 +2039,27 @@ static g3_status build_graph(Launch& S) {
   G3_TRY_CUDA(cudaGraphCreate(&top, 0));
   cudaGraphConditionalHandle h_loop, h_mode;
   cudaGraphNode_t wnode, sel, sw, ctl, n0, n1, n2;
-  cudaGraph_t body, br[4];
+  cudaGraph_t body, br[MODE_COUNT];
   Ctrl* c = ws->ctrl;
   int64_t nwords = ws->nwords;
   int32_t nb = ws->nb;
   int gconv = ws->grid_conv, gfront = ws->grid_front, gbins = ws->grid_bins;
   const bool tiles = bu_uses_tiles(*S.o), staged = bu_uses_staged(*S.o);
-  int gbu = tiles ? bu_tiles_grid(ws) : cap_grid(ws->nwords, 16, ws->grid_bu);
-  const int bbu = tiles ? 32 * BU_WARPS : 256;
+  const bool pairs = bu_uses_pairs(*S.o);
+  const int gtl = bu_tiles_grid(ws), gpr = cap_grid(ws->nwords, 16, ws->grid_bu);
   const int gst = bu_staged_grid(ws);
-  int skip = staged ? 1 : 0;
+  int skip = bu_split(*S.o);
   int gclear = g3_grid_for(ws->nwords, 256), gq2b = g3_grid_for(ws->nb, 256);
   const int64_t* off = S.g->off;
   const int32_t* col = S.g->col;
-  void* bu_fn = tiles ? bu_tiles_fn(S.o->bu_reverse)
-                      : (S.o->bu_reverse ? (void*)bu_pull<1> : (void*)bu_pull<0>);
+  void* tiles_fn = bu_tiles_fn(S.o->bu_reverse);
+  void* lp_fn = S.o->bu_reverse ? (void*)bu_list_pull<1> : (void*)bu_list_pull<0>;
+  const int glb = cap_grid(ws->nwords, 256, ws->grid_lb);
+  void* pairs_fn = bu_pull_fn(S.o->bu_reverse, S.full_stats);
   void* a_conv[] = {&S.B, &nwords, &c};
   void* a_clear[] = {&S.B, &nwords, &c};
   void* a_q2b[] = {&S.B, &c};
+  void* a_lb[] = {&S.B, &nwords, &nb, &ws->visited, &c};
   void* a_td[] = {&off, &col, &ws->visited, &ws->plo, &S.B, &ws->bins, &ws->goff, &S.nb1, &c};
   void* a_bu[] = {&nb, &nwords, &ws->visited, &S.B, &off, &col, &ws->nplus, &ws->plo, &c,
                   &skip};
@@ -1869,12 +2090,12 @@ static g3_status build_graph(Launch& S) {
     sp.type = cudaGraphNodeTypeConditional;
     sp.conditional.handle = h_mode;
     sp.conditional.type = cudaGraphCondTypeSwitch;
-    sp.conditional.size = 4;
+    sp.conditional.size = MODE_COUNT;  // branch MODE_DONE stays empty
     if (cudaGraphAddNode(&sw, body, &sel, nullptr, 1, &sp) != cudaSuccess) {
       st = G3_ECUDA;
       break;
     }
-    for (int k = 0; k < 4; ++k) br[k] = sp.conditional.phGraph_out[k];
+    for (int k = 0; k < MODE_COUNT; ++k) br[k] = sp.conditional.phGraph_out[k];
     // MODE_TD_Q
     if ((st = add_kernel(br[MODE_TD_Q], &n0, nullptr, (void*)td_front, gfront, 256, a_td))) break;
     if ((st = add_kernel(br[MODE_TD_Q], &n1, &n0, (void*)td_bins, gbins, 256, a_td))) break;
@@ -1883,27 +2104,40 @@ static g3_status build_graph(Launch& S) {
       break;
     if ((st = add_kernel(br[MODE_TD_B], &n1, &n0, (void*)td_front, gfront, 256, a_td))) break;
     if ((st = add_kernel(br[MODE_TD_B], &n2, &n1, (void*)td_bins, gbins, 256, a_td))) break;
-    // MODE_BU_B
-    if (staged) {
-      if ((st = add_kernel(br[MODE_BU_B], &n0, nullptr, (void*)bu_staged, gst, BS_THREADS,
-                           a_bu)))
-        break;
-      if ((st = add_kernel(br[MODE_BU_B], &n1, &n0, bu_fn, gbu, bbu, a_bu))) break;
-    } else if ((st = add_kernel(br[MODE_BU_B], &n0, nullptr, bu_fn, gbu, bbu, a_bu))) {
-      break;
-    }
-    // MODE_BU_Q
+    // MODE_BU_B and MODE_BU_Q (the latter after the queue -> bitmap
+    // conversion): the bottom-up kernels in a chain
     if ((st = add_kernel(br[MODE_BU_Q], &n0, nullptr, (void*)bm_clear, gclear, 256, a_clear)))
       break;
     if ((st = add_kernel(br[MODE_BU_Q], &n1, &n0, (void*)q_to_bitmap, gq2b, 256, a_q2b))) break;
-    if (staged) {
-      cudaGraphNode_t n3;
-      if ((st = add_kernel(br[MODE_BU_Q], &n2, &n1, (void*)bu_staged, gst, BS_THREADS, a_bu)))
-        break;
-      if ((st = add_kernel(br[MODE_BU_Q], &n3, &n2, bu_fn, gbu, bbu, a_bu))) break;
-    } else if ((st = add_kernel(br[MODE_BU_Q], &n2, &n1, bu_fn, gbu, bbu, a_bu))) {
-      break;
+    for (int q = 0; q < 2 && st == G3_OK; ++q) {
+      cudaGraph_t b = br[q ? MODE_BU_Q : MODE_BU_B];
+      cudaGraphNode_t prev = n1, cur;
+      cudaGraphNode_t* dep = q ? &prev : nullptr;
+      if (staged) {
+        if ((st = add_kernel(b, &cur, dep, (void*)bu_staged, gst, BS_THREADS, a_bu))) break;
+        prev = cur;
+        dep = &prev;
+      }
+      if (pairs) {
+        if ((st = add_kernel(b, &cur, dep, pairs_fn, gpr, 256, a_bu))) break;
+        prev = cur;
+        dep = &prev;
+      }
+      if (tiles) {
+        if ((st = add_kernel(b, &cur, dep, tiles_fn, gtl, 32 * BU_WARPS, a_bu))) break;
+      }
     }
+    if (st != G3_OK) break;
+    // MODE_BU_BS and MODE_BU_QS (sparse levels): list, then one thread per
+    // listed vertex
+    if ((st = add_kernel(br[MODE_BU_QS], &n0, nullptr, (void*)bm_clear, gclear, 256, a_clear)))
+      break;
+    if ((st = add_kernel(br[MODE_BU_QS], &n1, &n0, (void*)q_to_bitmap, gq2b, 256, a_q2b))) break;
+    if ((st = add_kernel(br[MODE_BU_QS], &n2, &n1, (void*)bu_list_build, glb, 256, a_lb))) break;
+    if ((st = add_kernel(br[MODE_BU_QS], &n0, &n2, lp_fn, ws->grid_lp, 256, a_bu))) break;
+    if ((st = add_kernel(br[MODE_BU_BS], &n0, nullptr, (void*)bu_list_build, glb, 256, a_lb)))
+      break;
+    if ((st = add_kernel(br[MODE_BU_BS], &n1, &n0, lp_fn, ws->grid_lp, 256, a_bu))) break;
     ca = ctrl_args(S, 1, h_loop);
     if ((st = add_kernel(body, &ctl, &sw, (void*)bfs_control, 1, 32, a_ctl))) break;
     cudaGraphExec_t ex = nullptr;
@@ -1914,6 +2148,7 @@ static g3_status build_graph(Launch& S) {
     if (ws->gexec) cudaGraphExecDestroy(ws->gexec);
     ws->gexec = ex;
     ws->gopts = *S.o;
+    ws->gfull = S.full_stats;
   } while (0);
   if (st != G3_OK) {
     cudaError_t e = cudaGetLastError();
@@ -1948,8 +2183,10 @@ static g3_status record_trials(const Launch& S, int64_t nf, g3_level_stats* r, c
       c.t2 = kSweep[k][1];
       c.t3 = kSweep[k][2];
     }
+    c.bu_sparse = !td && bu_uses_list(*S.o) && bu_sparse_level(c.nu, ws->nb);
     const int mode = td ? (c.fmt_queue ? MODE_TD_Q : MODE_TD_B)
-                        : (c.fmt_queue ? MODE_BU_Q : MODE_BU_B);
+                        : c.bu_sparse ? (c.fmt_queue ? MODE_BU_QS : MODE_BU_BS)
+                                      : (c.fmt_queue ? MODE_BU_Q : MODE_BU_B);
     G3_TRY_CUDA(cudaMemcpyAsync(ws->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     G3_TRY_CUDA(cudaEventRecord(ws->ev[4], s));
     G3_TRY(launch_level(S, mode, nf, nullptr, s));
@@ -2006,15 +2243,15 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   g3_bfs_ws* ws = g->ws;
   const int32_t nb = ws->nb;
   Ctrl* h = ws->h_ctrl;
+  const int full_stats = o->record_both || (stats && max_stats > 0);
   Launch S{g, ws, o,
            Bufs{{ws->qa, ws->qb}, {ws->fa, ws->fb}, g->relabelled ? g->old_of_new : nullptr},
-           (int64_t)ws->nb + 4};
+           (int64_t)ws->nb + 4, full_stats};
   const bool host_driven = o->timing || o->record_both;
   if (stats && max_stats > 0) memset(stats, 0, sizeof(g3_level_stats) * (size_t)max_stats);
 
   G3_TRY_CUDA(cudaMemsetAsync(ws->visited, 0, (size_t)(ws->nwords + 1) * 4, s));
   const int cap = host_driven ? 0x7fffffff : GRAPH_LEVEL_CAP;
-  const int full_stats = o->record_both || (stats && max_stats > 0);
   if (mr) {
     bfs_roots_multi<<<1, 1024, 0, s>>>(mr->roots, mr->count, mr->lo,
                                        g->relabelled ? g->new_of_old : nullptr, nb, g->nnz,
@@ -2022,7 +2259,8 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
                                        o->t1, o->t2, o->t3, cap, full_stats);
     root = -1;  // the output pass has no single root to patch
   } else {
-    bfs_root<<<1, 1, 0, s>>>(g->relabelled ? g->new_of_old : nullptr, root, nb, g->nnz, g->off,
+    bfs_root<<<1, 1, 0, s>>>(g->relabelled ? g->new_of_old : nullptr, g->comp_rng, root, nb,
+                             g->nnz, g->off,
                              ws->visited, ws->plo, ws->qa, ws->ctrl, ws->log, o->t1, o->t2,
                              o->t3, cap, full_stats);
   }
@@ -2044,24 +2282,25 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
     if (split) {
       const int grid = cap_grid((g->n + 3) / 4, 256, ws->grid_tr4);
       bfs_translate_p1<<<grid, 256, 0, ts>>>(g->n, nb, nb / 2, g->new_of_old, ws->visited,
-                                             ws->plo, (uint32_t*)op);
+                                             ws->ctrl, ws->plo, (uint32_t*)op);
       G3_CHECK_LAUNCH();
       bfs_translate_p2<<<grid, 256, 0, ts>>>(g->n, root, ws->plo, op, ol);
     } else if (aligned) {
       bfs_translate4<<<cap_grid((g->n + 3) / 4, 256, ws->grid_tr4), 256, 0, ts>>>(
-          g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op,
-          ol);
+          g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->ctrl,
+          ws->plo, op, ol);
     } else {  // outputs not 16-byte aligned
       bfs_translate<<<cap_grid(g->n, 256, ws->grid_tr), 256, 0, ts>>>(
-          g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->plo, op,
-          ol);
+          g->n, nb, root, g->relabelled ? g->new_of_old : nullptr, ws->visited, ws->ctrl,
+          ws->plo, op, ol);
     }
     G3_CHECK_LAUNCH();
     return G3_OK;
   };
   bool translated = false;
   if (!host_driven) {
-    if (!ws->gexec || !same_opts(ws->gopts, *o)) G3_TRY(build_graph(S));
+    if (!ws->gexec || !same_opts(ws->gopts, *o) || ws->gfull != full_stats)
+      G3_TRY(build_graph(S));
     G3_TRY_CUDA(cudaGraphLaunch(ws->gexec, s));
     // the output pass goes right behind the level loop, without waiting for
     // the host to read the controller; it is repeated below in the rare case
@@ -2152,7 +2391,7 @@ extern "C" g3_status g3_bfs(g3_graph* g, int32_t root, const g3_bfs_opts* opts, 
   if (opts) o = *opts; else g3_bfs_opts_default(&o);
   if (o.controller < 0 || o.controller > 3 || o.alpha <= 0 || o.beta <= 0 || o.t1 < 1 ||
       o.t2 <= o.t1 || o.t3 <= o.t2 || o.mlp_margin < 0 || o.out_split < 0 || o.out_split > 2 ||
-      o.bu_kernel < 0 || o.bu_kernel > 2) {
+      o.bu_kernel < 0 || o.bu_kernel > 3) {
     g3_set_error("g3_bfs: bad options");
     return G3_EINVAL;
   }

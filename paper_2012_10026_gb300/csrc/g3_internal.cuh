@@ -89,6 +89,10 @@ struct g3_graph {
   int32_t* col;         // [nnz]
   int32_t* old_of_new;  // [n] after relabel
   int32_t* new_of_old;  // [n] after relabel
+  // [n_plus] after a full RCM relabel, else NULL: the label range [x, y) of
+  // each label's connected component (Algorithm 3 numbers a component's
+  // vertices consecutively, so every component is one range of labels)
+  int2* comp_rng;
   g3_bfs_ws* ws;
   g3_ms_ws* ms;
 };

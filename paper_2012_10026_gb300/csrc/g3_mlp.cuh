@@ -48,20 +48,44 @@ __device__ __forceinline__ void mlp_features_raw(long long nf, long long mf, lon
   f[11] = nb > 0 ? 1.f - fnu / fn : 0.f;
 }
 
+// One lane's share of the weights: hidden unit j's input row and bias, and
+// its weight into each output. Loaded before the features are known, so that
+// their latency overlaps the work that produces the features.
+struct MlpLane {
+  float w1[MLP_IN], b1, w2[MLP_OUT], b2[MLP_OUT];
+};
+
+__device__ __forceinline__ void mlp_load_lane(const float* __restrict__ P, MlpLane& L) {
+  const int j = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < MLP_IN; ++i) L.w1[i] = P[j * MLP_IN + i];
+  L.b1 = P[MLP_B1 + j];
+#pragma unroll
+  for (int k = 0; k < MLP_OUT; ++k) {
+    L.w2[k] = P[MLP_W2 + k * MLP_HID + j];
+    L.b2[k] = P[MLP_B2 + k];
+  }
+}
+
 // One warp evaluates the network for one feature vector: lane j is hidden
 // unit j; the four outputs are warp reductions.
-__device__ __forceinline__ void mlp_eval_warp(const float* __restrict__ P, const float* f,
-                                              float* out) {
-  const int j = threadIdx.x & 31;
-  float z = P[MLP_B1 + j];
+__device__ __forceinline__ void mlp_eval_lane(const MlpLane& L, const float* f, float* out) {
+  float z = L.b1;
 #pragma unroll
-  for (int i = 0; i < MLP_IN; ++i) z = fmaf(P[j * MLP_IN + i], f[i], z);
+  for (int i = 0; i < MLP_IN; ++i) z = fmaf(L.w1[i], f[i], z);
   const float h = fmaxf(z, 0.f);
 #pragma unroll
   for (int k = 0; k < MLP_OUT; ++k) {
-    float s = P[MLP_W2 + k * MLP_HID + j] * h;
+    float s = L.w2[k] * h;
 #pragma unroll
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    out[k] = s + P[MLP_B2 + k];
+    out[k] = s + L.b2[k];
   }
+}
+
+__device__ __forceinline__ void mlp_eval_warp(const float* __restrict__ P, const float* f,
+                                              float* out) {
+  MlpLane L;
+  mlp_load_lane(P, L);
+  mlp_eval_lane(L, f, out);
 }

@@ -243,6 +243,24 @@ __global__ void rcm_labels(const int32_t* __restrict__ pos, int32_t n, int32_t k
   }
 }
 
+// Label range of each vertex's component (full relabelling). The component
+// started from rank c holds Cuthill-McKee positions [base[c], cursor[c])
+// once every level is placed, and the reversal turns position q into label
+// k - 1 - q, so its labels are [k - cursor[c], k - base[c]).
+__global__ void rcm_comp_ranges(const int32_t* __restrict__ rank, const int32_t* __restrict__ p,
+                                const int64_t* __restrict__ base,
+                                const int64_t* __restrict__ cursor,
+                                const int32_t* __restrict__ new_of_old, int32_t n, int32_t k,
+                                int2* rng) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rank[v];
+    if (r < 0) continue;  // isolated
+    const int32_t c = p[r];
+    rng[new_of_old[v]] = make_int2(k - (int32_t)cursor[c], k - (int32_t)base[c]);
+  }
+}
+
 // Partial RCM: the vertices of V+ below rank lo, labels k.. by ascending ID.
 struct IsUnordered {
   const int64_t* off;
@@ -328,7 +346,9 @@ static g3_status rcm_impl(g3_graph* g, int32_t p_permille, cudaStream_t s, RcmBu
   G3_TRY(g3_alloc(&B.kb, n, s));
   g3_free(g->new_of_old, s);
   g3_free(g->old_of_new, s);
+  g3_free(g->comp_rng, s);
   g->new_of_old = g->old_of_new = nullptr;
+  g->comp_rng = nullptr;
   G3_TRY(g3_alloc(&g->new_of_old, n, s));
   G3_TRY(g3_alloc(&g->old_of_new, n, s));
   G3_TRY(g3_alloc(&B.counters, 2, s));
@@ -429,6 +449,12 @@ static g3_status rcm_impl(g3_graph* g, int32_t p_permille, cudaStream_t s, RcmBu
   // 5. labels, inverse, relabelled CSR
   rcm_labels<<<g3_grid_for(n, 256), 256, 0, s>>>(B.pos, n, k, g->new_of_old);
   G3_CHECK_LAUNCH();
+  if (lo == 0 && n_plus > 0) {  // every component was ordered: keep their ranges
+    G3_TRY(g3_alloc(&g->comp_rng, n_plus, s));
+    rcm_comp_ranges<<<g3_grid_for(n, 256), 256, 0, s>>>(B.rank, B.p, B.base, B.cursor,
+                                                        g->new_of_old, n, k, g->comp_rng);
+    G3_CHECK_LAUNCH();
+  }
   if (lo > 0)
     G3_TRY(g3_compact((int64_t)n, IsUnordered{g->off, B.rank, lo},
                       EmitUnorderedLabel{k, g->new_of_old}, B.partial, s));
@@ -524,7 +550,9 @@ static g3_status relabel(g3_graph* g, int32_t p_permille, cudaStream_t s, const 
     // half-made permutation is dropped
     g3_free(g->new_of_old, s);
     g3_free(g->old_of_new, s);
+    g3_free(g->comp_rng, s);
     g->new_of_old = g->old_of_new = nullptr;
+    g->comp_rng = nullptr;
     cudaStreamSynchronize(s);
   }
   return st;

@@ -264,7 +264,7 @@ extern "C" g3_status g3_autotune_bfs(g3_graph* g, const int32_t* roots, int32_t 
                                     {32, 256, 8192},   {8, 256, 32768},   {32, 2048, 262144}};
   for (int pass = 0; pass < 2; ++pass) {
     for (int c = 0; c < 5; ++c) {
-      const int count = c == 0 ? 9 : c == 1 ? 6 : c == 2 ? 6 : 2;
+      const int count = c == 0 ? 9 : c == 1 ? 6 : c == 2 ? 6 : c == 3 ? 2 : 3;
       for (int i = 0; i < count; ++i) {
         g3_bfs_opts o = best;
         if (c == 0) o.alpha = alphas[i];
@@ -275,7 +275,8 @@ extern "C" g3_status g3_autotune_bfs(g3_graph* g, const int32_t* roots, int32_t 
           o.t3 = bins[i][2];
         }
         if (c == 3) o.bu_reverse = i;
-        if (c == 4) o.bu_kernel = i;  // word pairs, or staged + word tiles
+        // word pairs; staged + word tiles; word pairs + word tiles
+        if (c == 4) o.bu_kernel = i == 2 ? 3 : i;
         if (!memcmp(&o, &best, sizeof(o))) continue;
         float ms = 0.f;
         G3_TRY(time_bfs(g, roots, nroots, o, parent, level, fl, ev, s, &ms));

@@ -119,14 +119,15 @@ def test_bfs_small_cases(case, relabel):
     rng = np.random.default_rng(n)
     roots = sorted(set([0, n - 1] + rng.integers(0, n, 6).tolist()))
     # bottom-up in every kernel set (word pairs, staged + word tiles, word
-    # tiles) and both scan orders; the output pass in one pass and split over
+    # tiles, word pairs + word tiles) and both scan orders; the output pass in one pass and split over
     # label halves
     for ctrl, rev, kern, split in ((g3.G3_CTRL_HEURISTIC, 1, 0, 0),
                                    (g3.G3_CTRL_HEURISTIC, 1, 1, 2),
                                    (g3.G3_CTRL_TOPDOWN, 1, 0, 1),
                                    (g3.G3_CTRL_BOTTOMUP, 1, 0, 0), (g3.G3_CTRL_BOTTOMUP, 0, 0, 0),
                                    (g3.G3_CTRL_BOTTOMUP, 1, 1, 0), (g3.G3_CTRL_BOTTOMUP, 0, 1, 2),
-                                   (g3.G3_CTRL_BOTTOMUP, 1, 2, 0)):
+                                   (g3.G3_CTRL_BOTTOMUP, 1, 2, 0), (g3.G3_CTRL_BOTTOMUP, 1, 3, 0),
+                                   (g3.G3_CTRL_HEURISTIC, 0, 3, 0)):
         for root in roots:
             parent, level, _ = run_bfs(g, root, n, controller=ctrl, bu_reverse=rev,
                                        bu_kernel=kern, out_split=split)
@@ -158,11 +159,13 @@ def _levels_new(ref, level_orig):
                                 dict(bu_kernel=1),
                                 dict(controller=g3.G3_CTRL_BOTTOMUP, bu_kernel=1),
                                 dict(out_split=2), dict(out_split=1),
-                                dict(controller=g3.G3_CTRL_BOTTOMUP, bu_kernel=2)],
+                                dict(controller=g3.G3_CTRL_BOTTOMUP, bu_kernel=2),
+                                dict(bu_kernel=3),
+                                dict(controller=g3.G3_CTRL_BOTTOMUP, bu_kernel=3)],
                          ids=["heuristic", "topdown", "bottomup", "forward_scan",
                               "bottomup_forward", "tiny_bins", "alpha64_beta8", "staged",
                               "bottomup_staged", "out_split", "out_one_pass",
-                              "bottomup_tiles"])
+                              "bottomup_tiles", "pairs_tiles", "bottomup_pairs_tiles"])
 def test_bfs_kron16_all_roots(kron16, kw):
     K = kron16
     ref = K["ref"]
@@ -289,8 +292,8 @@ def test_kron22_permutation_and_levels():
     off_g, col_g = gpu_csr(g)
     assert np.array_equal(off_g, ref["off_r"]) and np.array_equal(col_g, ref["col_r"])
     roots = graphgen.pick_roots(graphgen.nonisolated_flags(src, dst, n), 64, seed=2)
-    for i, root in enumerate(roots[:4].tolist()):
-        parent, level, _ = run_bfs(g, root, n, out_split=1 + i % 2, bu_kernel=i // 2)
+    for i, root in enumerate(roots[:6].tolist()):
+        parent, level, _ = run_bfs(g, root, n, out_split=1 + i % 2, bu_kernel=(0, 1, 3)[i // 2])
         _, lref = oracle.bfs(ref["off"], ref["col"], root)
         assert np.array_equal(level, lref)
         assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
@@ -361,6 +364,44 @@ def test_levels_past_the_packed_word(relabel, split, ctrl):
     pw[ids] = ids[np.clip(np.where(pos > mid, pos - 1, pos + 1), 0, k - 1)]
     pw[ids[mid]] = ids[mid]
     assert np.array_equal(parent, pw)
+    g.free()
+
+
+def test_roots_in_every_component_after_stale_searches():
+    # after a full relabel each component is one label range, and the output
+    # pass takes "reached" from the root's range instead of the visited
+    # bitmap: search the largest component first, so that every packed
+    # (parent, level) word holds a stale value, then one root in each other
+    # component (sizes 2 to several hundred, isolated vertices in between);
+    # any vertex the range wrongly includes or leaves out shows up as a level
+    # that differs from the oracle's
+    rng = np.random.default_rng(31)
+    parts, base = [], 0
+    for k in [700, 2, 3, 5, 40, 2, 260, 9, 2, 120]:
+        if k == 2:
+            s, d = np.array([0], np.int32), np.array([1], np.int32)
+        elif k < 10:
+            s, d = path_graph(k)
+        else:  # a spanning path plus random chords: connected
+            ps, pd = path_graph(k)
+            cs, cd = random_graph(rng, k, 2 * k, allow_loops=False)
+            s, d = np.concatenate([ps, cs]), np.concatenate([pd, cd])
+        parts.append((s + base, d + base, base, k))
+        base += k + int(rng.integers(0, 4))  # isolated vertices between parts
+    n = base + 3
+    sigma = rng.permutation(n).astype(np.int32)  # scatter the original IDs
+    src = sigma[np.concatenate([p[0] for p in parts])]
+    dst = sigma[np.concatenate([p[1] for p in parts])]
+    off, col = oracle.build_csr(src, dst, n)
+    g = gpu_pipeline(src, dst, n)
+    roots = [int(sigma[b + int(rng.integers(0, k))]) for _, _, b, k in parts]
+    roots.append(int(sigma[n - 1]))  # an isolated root
+    for root in roots:
+        for ctrl in (g3.G3_CTRL_HEURISTIC, g3.G3_CTRL_BOTTOMUP):
+            parent, level, _ = run_bfs(g, root, n, controller=ctrl)
+            _, lref = oracle.bfs(off, col, root)
+            assert np.array_equal(level, lref), root
+            assert oracle.validate(off, col, root, parent, level) == 0, root
     g.free()
 
 

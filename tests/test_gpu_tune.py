@@ -40,7 +40,7 @@ def test_autotune_bfs_cache_and_parity(kron14, tmp_path):
     assert (rec.size_class, rec.deg_class) == g3.tune_key(g3.G3_TUNE_BFS, g.info["n_bfs"],
                                                           g.info["nnz"])
     assert list(rec.p) == [o.alpha, o.beta, o.t1, o.t2, o.t3, o.bu_reverse | (o.bu_kernel << 1)]
-    assert o.t1 < o.t2 < o.t3 and o.bu_reverse in (0, 1) and o.bu_kernel in (0, 1)
+    assert o.t1 < o.t2 < o.t3 and o.bu_reverse in (0, 1) and o.bu_kernel in (0, 1, 3)
     # second call: a cache hit, nothing launched
     l0 = g3.kernel_launches()
     o2, rec2 = g3.autotune_bfs(g, roots, parent, level, cache)
