@@ -12,7 +12,8 @@ ReLU derivative is taken as 0 at z == 0.
 Features of a level (inputs), from the frontier sizes and degree sums of the
 searched graph (n vertices, nnz directed entries):
     0 log2((1+n_f)/(1+n))    1 log2((1+m_f)/(1+nnz))
-    2 log2((1+n_u)/(1+n))    3 n / 2^24 (the graph size, linear)
+    2 log2((1+n_u)/(1+n))    3 log2((1+n_u)/(1+n_f)) / 8 (unvisited
+      vertices per frontier vertex)
     4 log2((1+m_f)/(1+n_f)) / 16 (mean frontier degree)
     5 log2((1+m_f)/(1+m_u))  6 log2((1+n) / (32 (1+m_f)))
     7 previous direction (0 TD, 1 BU)
@@ -103,7 +104,7 @@ def features(n_f, m_f, n_u, m_u, n, nnz, prev_dir, level, prev_nf):
     """Feature vector of one level (see the module docstring)."""
     return np.array([
         np.log2((1.0 + n_f) / (1.0 + n)), np.log2((1.0 + m_f) / (1.0 + nnz)),
-        np.log2((1.0 + n_u) / (1.0 + n)), n / 2.0 ** 24,
+        np.log2((1.0 + n_u) / (1.0 + n)), np.log2((1.0 + n_u) / (1.0 + n_f)) / 8.0,
         np.log2((1.0 + m_f) / (1.0 + n_f)) / 16.0, np.log2((1.0 + m_f) / (1.0 + m_u)),
         np.log2((1.0 + n) / (32.0 * (1.0 + m_f))), float(prev_dir),
         np.log2((1.0 + m_u) / (1.0 + n_u)) / 16.0,

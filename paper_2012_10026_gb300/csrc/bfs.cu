@@ -59,7 +59,7 @@ enum {
 };
 
 // Device-side controller record.
-struct Ctrl {
+struct __align__(16) Ctrl {
   // accumulators for the frontier being produced (reset by the controller)
   unsigned long long q_len;     // top-down: next queue length
   unsigned long long nx_nf;     // bottom-up: next frontier size
@@ -79,7 +79,8 @@ struct Ctrl {
   int t1, t2, t3;
   float mlp_out[4];
   long long n_visited, m_visited;
-  // where F_L lives: queue q[qsel] when fmt_queue, else bitmap f[fsel]
+  // where F_L lives: fmt_queue 0 bitmap f[fsel], 1 queue q[qsel], 2 both
+  // (a sparse bottom-up level writes its next frontier in both forms)
   int qsel, fsel, fmt_queue;
   int mode;  // MODE_* of the current level
   int cap;   // the controller ends the search at this level (graph launches)
@@ -289,8 +290,9 @@ __device__ __forceinline__ void reset_next(Ctrl* c) {
 __device__ __forceinline__ int mode_of(const Ctrl* c) {
   if (c->nf <= 0) return MODE_DONE;
   if (c->dir == G3_DIR_TD) return c->fmt_queue ? MODE_TD_Q : MODE_TD_B;
-  if (c->bu_sparse) return c->fmt_queue ? MODE_BU_QS : MODE_BU_BS;
-  return c->fmt_queue ? MODE_BU_Q : MODE_BU_B;
+  const bool only_queue = c->fmt_queue == 1;
+  if (c->bu_sparse) return only_queue ? MODE_BU_QS : MODE_BU_BS;
+  return only_queue ? MODE_BU_Q : MODE_BU_B;
 }
 
 // A bottom-up level with under 4 % of the graph unvisited runs over a list
@@ -870,8 +872,10 @@ __global__ void __launch_bounds__(256, 6) bu_pull(int32_t nb, int64_t nwords, ui
 // word, one atomic per warp to place its slice) and clears the next-frontier
 // words, and bu_list_pull gives every listed vertex its own thread, all in
 // flight at once; a found vertex sets its bits in the next frontier and the
-// visited bitmap with atomic ORs. The list goes into the queue that is not
-// the current frontier.
+// visited bitmap with atomic ORs and is also appended to a queue, so that a
+// top-down level after this one needs no bitmap -> queue pass. The list goes
+// into the queue that is not the current frontier, the found vertices into
+// the other one (whose frontier, if it had one, the bitmap already holds).
 __global__ void __launch_bounds__(256) bu_list_build(Bufs B, int64_t nwords, int32_t nb,
                                                      const uint32_t* __restrict__ visited,
                                                      Ctrl* c) {
@@ -919,6 +923,7 @@ __global__ void __launch_bounds__(256) bu_list_pull(int32_t nb, int64_t nwords, 
   const uint32_t* __restrict__ fcur = (c->fsel ? B.f[1] : B.f[0]);
   uint32_t* fnext = (c->fsel ? B.f[0] : B.f[1]);
   const int32_t* __restrict__ list = (c->qsel ? B.q[0] : B.q[1]);
+  int32_t* __restrict__ fq = (c->qsel ? B.q[1] : B.q[0]);
   const int32_t lnext = c->level + 1;
   const int32_t* __restrict__ o2n = B.o2n;
   StatAcc acc;
@@ -967,6 +972,13 @@ __global__ void __launch_bounds__(256) bu_list_pull(int32_t nb, int64_t nwords, 
     if (bits && (__ffs(grp) - 1) == lane) {
       atomicOr(&fnext[v >> 5], bits);
       atomicOr(&visited[v >> 5], bits);
+    }
+    const unsigned fb = __ballot_sync(0xffffffffu, p >= 0);
+    if (fb) {  // one queue reservation per warp step
+      unsigned long long at = 0;
+      if (lane == 0) at = atomicAdd(&c->q_len, (unsigned long long)__popc(fb));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (p >= 0) fq[at + __popc(fb & g3_lanemask_lt())] = v;
     }
   }
   acc.flush(c);
@@ -1372,7 +1384,7 @@ static void* bu_tiles_fn(int rev) {
 // queue -> bitmap before a bottom-up level that follows a top-down one:
 // clear f[fsel], then set the bit of every queued vertex.
 __global__ void bm_clear(Bufs B, int64_t nwords, const Ctrl* c) {
-  if (c->dir != G3_DIR_BU || !c->fmt_queue) return;
+  if (c->dir != G3_DIR_BU || c->fmt_queue != 1) return;
   uint32_t* f = (c->fsel ? B.f[1] : B.f[0]);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -1380,7 +1392,7 @@ __global__ void bm_clear(Bufs B, int64_t nwords, const Ctrl* c) {
 }
 
 __global__ void q_to_bitmap(Bufs B, const Ctrl* c) {
-  if (c->dir != G3_DIR_BU || !c->fmt_queue) return;
+  if (c->dir != G3_DIR_BU || c->fmt_queue != 1) return;
   const int32_t* __restrict__ q = (c->qsel ? B.q[1] : B.q[0]);
   uint32_t* bm = (c->fsel ? B.f[1] : B.f[0]);
   const int64_t len = c->nf;
@@ -1425,11 +1437,6 @@ __global__ void bitmap_to_q(Bufs B, int64_t nwords, Ctrl* c) {
 
 // ------------------------------------------------------------- controller
 // Learned controller: the 12-32-4 MLP of g3_mlp.cuh on the frontier record.
-__device__ void mlp_features(const Ctrl* c, int32_t nb, long long nnz, int prev_dir,
-                             long long prev_nf, float* f) {
-  mlp_features_raw(c->nf, c->mf, c->nu, c->mu, nb, nnz, prev_dir, c->level, prev_nf, f);
-}
-
 __device__ __forceinline__ int clamp_thr(float lg, int lo, int hi) {
   float x = fminf(fmaxf(rintf(lg), (float)lo), (float)hi);
   return 1 << (int)x;
@@ -1454,90 +1461,109 @@ struct CtrlArgs {
 // log it and clear the accumulators for the next expansion. In graph mode it
 // also ends the loop (done, or the launch's level cap reached).
 __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
-  __shared__ float feat[12];
-  __shared__ int decide, active;
+  // The record is brought into shared memory in 16-byte words, one per lane,
+  // worked on there by lane 0 and written back the same way: two round trips
+  // to L2 instead of one per field that lane 0 reads after writing.
+  __shared__ Ctrl sc;
+  __shared__ float feat[MLP_IN];
+  __shared__ long long s_prev_nf;
+  __shared__ int decide, active, s_dir;
   const int lane = threadIdx.x;
-  MlpLane W;  // the weights are on their way while lane 0 updates the record
+  MlpLane W;  // the weights are on their way while the record is updated
   if (A.controller == G3_CTRL_LEARNED) mlp_load_lane(A.mlp, W);
+  constexpr int kWords = (int)(sizeof(Ctrl) / 16);
+  int4* gw = reinterpret_cast<int4*>(c);
+  int4* sw = reinterpret_cast<int4*>(&sc);
+  for (int i = lane; i < kWords; i += 32) sw[i] = gw[i];
+  __syncwarp();
+  Ctrl* const r = &sc;
   if (lane == 0) {
-    active = c->mode != MODE_DONE && c->nf > 0;
+    active = r->mode != MODE_DONE && r->nf > 0;
     if (active) {
-      const int prev_dir = c->dir;
+      const int prev_dir = r->dir;
       const bool was_td = prev_dir == G3_DIR_TD;
-      const long long prev_nf = c->nf;
-      const long long nf = was_td ? (long long)c->q_len : (long long)c->nx_nf;
+      const long long prev_nf = r->nf;
+      const long long nf = was_td ? (long long)r->q_len : (long long)r->nx_nf;
       if (was_td) {
-        c->qsel ^= 1;
-        c->fmt_queue = 1;
+        r->qsel ^= 1;
+        r->fmt_queue = 1;
       } else {
-        c->fsel ^= 1;
-        c->fmt_queue = 0;
+        // a sparse level also left its next frontier in q[qsel]
+        r->fsel ^= 1;
+        r->fmt_queue = r->bu_sparse ? 2 : 0;
       }
-      if (c->level < LOG_MAX) {
-        A.log[c->level].n_next = nf;
-        if (!was_td) A.log[c->level].examined = (long long)c->nx_exam;
+      if (r->level < LOG_MAX) {
+        A.log[r->level].n_next = nf;
+        if (!was_td) A.log[r->level].examined = (long long)r->nx_exam;
       }
-      c->nf = nf;
-      c->mf = (long long)c->nx_mf;
-      for (int k = 0; k < 4; ++k) c->hist[k] = (long long)c->nx_hist[k];
-      c->id_min = nf ? (int)c->nx_min : 0;
-      c->id_max = nf ? (int)c->nx_max : 0;
-      c->n_visited += nf;
-      c->m_visited += c->mf;
-      c->nu = A.nb - c->n_visited;
-      c->mu = A.nnz - c->m_visited;
-      c->level += 1;
+      r->nf = nf;
+      r->mf = (long long)r->nx_mf;
+      for (int k = 0; k < 4; ++k) r->hist[k] = (long long)r->nx_hist[k];
+      r->id_min = nf ? (int)r->nx_min : 0;
+      r->id_max = nf ? (int)r->nx_max : 0;
+      r->n_visited += nf;
+      r->m_visited += r->mf;
+      r->nu = A.nb - r->n_visited;
+      r->mu = A.nnz - r->m_visited;
+      r->level += 1;
       int d;
       if (A.controller == G3_CTRL_TOPDOWN) {
         d = G3_DIR_TD;
       } else if (A.controller == G3_CTRL_BOTTOMUP) {
         d = G3_DIR_BU;
       } else if (prev_dir == G3_DIR_TD) {
-        d = (c->mf * (long long)A.alpha > c->mu) ? G3_DIR_BU : G3_DIR_TD;
+        d = (r->mf * (long long)A.alpha > r->mu) ? G3_DIR_BU : G3_DIR_TD;
       } else {
         d = (nf < prev_nf && nf * (long long)A.beta < (long long)A.nb) ? G3_DIR_TD : G3_DIR_BU;
       }
-      c->t1 = A.t1;
-      c->t2 = A.t2;
-      c->t3 = A.t3;
+      r->t1 = A.t1;
+      r->t2 = A.t2;
+      r->t3 = A.t3;
       decide = d;
-      if (A.controller == G3_CTRL_LEARNED) mlp_features(c, A.nb, A.nnz, prev_dir, prev_nf, feat);
-      reset_next(c);
+      s_prev_nf = prev_nf;
+      s_dir = prev_dir;
+      reset_next(r);
     }
   }
   __syncwarp();
   if (active && A.controller == G3_CTRL_LEARNED) {
+    // lane j computes feature j, all twelve at once
+    if (lane < MLP_IN)
+      feat[lane] = mlp_feature(lane, r->nf, r->mf, r->nu, r->mu, A.nb, A.nnz, s_dir, r->level,
+                               s_prev_nf);
+    __syncwarp();
     float out[4];
     mlp_eval_lane(W, feat, out);
     if (lane == 0) {
-      for (int k = 0; k < 4; ++k) c->mlp_out[k] = out[k];
+      for (int k = 0; k < 4; ++k) r->mlp_out[k] = out[k];
       // inside the margin the alpha/beta rule's direction stands
       if (fabsf(out[0]) > A.mlp_margin) decide = out[0] < 0.f ? G3_DIR_BU : G3_DIR_TD;
-      int a1 = clamp_thr(out[1], 2, 12), a2 = clamp_thr(out[2], 6, 18),
-          a3 = clamp_thr(out[3], 10, 26);
-      if (a2 <= a1) a2 = a1 * 2;
-      if (a3 <= a2) a3 = a2 * 2;
       if (A.mlp_bins) {
-        c->t1 = a1;
-        c->t2 = a2;
-        c->t3 = a3;
+        int a1 = clamp_thr(out[1], 2, 12), a2 = clamp_thr(out[2], 6, 18),
+            a3 = clamp_thr(out[3], 10, 26);
+        if (a2 <= a1) a2 = a1 * 2;
+        if (a3 <= a2) a3 = a2 * 2;
+        r->t1 = a1;
+        r->t2 = a2;
+        r->t3 = a3;
       }
     }
     __syncwarp();
   }
-  if (lane == 0) {
-    if (active) {
-      c->dir = decide;
-      c->bu_sparse = decide == G3_DIR_BU && A.bu_list && bu_sparse_level(c->nu, A.nb);
-      c->mode = c->err ? MODE_DONE : mode_of(c);
-      if (c->mode != MODE_DONE) log_frontier(A.log, c);
-    }
-    if (A.graph_mode) {
-      const bool go = c->mode != MODE_DONE && c->level < c->cap;
-      cudaGraphSetConditional(A.h_loop, go ? 1u : 0u);
-    }
+  if (lane == 0 && active) {
+    r->dir = decide;
+    r->bu_sparse = decide == G3_DIR_BU && A.bu_list && bu_sparse_level(r->nu, A.nb);
+    r->mode = r->err ? MODE_DONE : mode_of(r);
+    if (r->mode != MODE_DONE) log_frontier(A.log, r);
+  }
+  __syncwarp();
+  for (int i = lane; i < kWords; i += 32) gw[i] = sw[i];
+  if (lane == 0 && A.graph_mode) {
+    const bool go = r->mode != MODE_DONE && r->level < r->cap;
+    cudaGraphSetConditional(A.h_loop, go ? 1u : 0u);
   }
 }
+
 
 // Graph mode: picks the SWITCH body of the level about to run.
 __global__ void bfs_select(const Ctrl* c, cudaGraphConditionalHandle h_mode) {
@@ -2173,6 +2199,13 @@ static g3_status record_trials(const Launch& S, int64_t nf, g3_level_stats* r, c
   Ctrl save;
   G3_TRY_CUDA(cudaMemcpyAsync(&save, ws->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
   G3_TRY_CUDA(cudaStreamSynchronize(s));
+  // a sparse bottom-up trial writes its found vertices over q[qsel], which
+  // may hold the current frontier: it is kept in the output staging buffer
+  // (unused until the output pass) and put back after that trial
+  int32_t* qcur = S.B.q[save.qsel];
+  const size_t qbytes = save.fmt_queue && nf > 0 ? (size_t)nf * 4 : 0;
+  if (qbytes)
+    G3_TRY_CUDA(cudaMemcpyAsync(ws->out_level, qcur, qbytes, cudaMemcpyDeviceToDevice, s));
   float best = 1e30f;
   for (int k = 0; k < 6; ++k) {
     Ctrl c = save;
@@ -2184,14 +2217,17 @@ static g3_status record_trials(const Launch& S, int64_t nf, g3_level_stats* r, c
       c.t3 = kSweep[k][2];
     }
     c.bu_sparse = !td && bu_uses_list(*S.o) && bu_sparse_level(c.nu, ws->nb);
+    const bool only_queue = c.fmt_queue == 1;
     const int mode = td ? (c.fmt_queue ? MODE_TD_Q : MODE_TD_B)
-                        : c.bu_sparse ? (c.fmt_queue ? MODE_BU_QS : MODE_BU_BS)
-                                      : (c.fmt_queue ? MODE_BU_Q : MODE_BU_B);
+                        : c.bu_sparse ? (only_queue ? MODE_BU_QS : MODE_BU_BS)
+                                      : (only_queue ? MODE_BU_Q : MODE_BU_B);
     G3_TRY_CUDA(cudaMemcpyAsync(ws->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     G3_TRY_CUDA(cudaEventRecord(ws->ev[4], s));
     G3_TRY(launch_level(S, mode, nf, nullptr, s));
     G3_TRY_CUDA(cudaEventRecord(ws->ev[5], s));
     G3_TRY_CUDA(cudaMemcpyAsync(ws->visited, ws->vis_save, vbytes, cudaMemcpyDeviceToDevice, s));
+    if (!td && qbytes)
+      G3_TRY_CUDA(cudaMemcpyAsync(qcur, ws->out_level, qbytes, cudaMemcpyDeviceToDevice, s));
     G3_TRY_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ws->ev[4], ws->ev[5]);

@@ -16,11 +16,12 @@
 
 // Features of the frontier F_L (see the controller's documentation), all
 // from the frontier sizes and degree sums the expansion kernels count anyway
-// (n: vertices of the searched graph, nnz: its directed entries):
+// (n: vertices of the searched graph, nnz: its directed entries), and all
+// ratios of the graph's own counts, so that a level looks the same to the
+// network on a graph of any size:
 //  0 log2((1+n_f)/(1+n))   1 log2((1+m_f)/(1+nnz))
-//  2 log2((1+n_u)/(1+n))   3 n / 2^24: the graph size, linear, because a
-//    bottom-up step's walk over the bitmap costs time in proportion to n
-//    while a small top-down step's cost does not grow with it
+//  2 log2((1+n_u)/(1+n))   3 log2((1+n_u)/(1+n_f)) / 8: unvisited vertices per
+//    frontier vertex
 //  4 log2((1+m_f)/(1+n_f)) / 16: mean degree of the frontier
 //  5 log2((1+m_f)/(1+m_u))
 //  6 log2((1+n)/(32 (1+m_f))): bitmap words a bottom-up step walks per
@@ -28,24 +29,35 @@
 //  8 log2((1+m_u)/(1+n_u)) / 16: mean degree of the unvisited vertices
 //  9 log2((1+n_f)/(1+n_f of the previous level)) / 8: frontier growth
 // 10 min(level, 32) / 32    11 1 - n_u / n: fraction of the graph visited
+// Feature j alone, so that the lanes of a warp can compute them at once.
+// Nine of them are log2((1+a)/(1+b)) * scale + shift for a pair of counts;
+// the pair is selected per lane and every lane runs the same instructions
+// (one log2f per lane instead of the warp stepping through twelve cases).
+__device__ __forceinline__ float mlp_feature(int j, long long nf, long long mf, long long nu,
+                                             long long mu, int32_t nb, long long nnz,
+                                             int prev_dir, int level, long long prev_nf) {
+  const float fnf = (float)nf, fmf = (float)mf, fnu = (float)nu, fmu = (float)mu;
+  const float fn = (float)nb, fe = (float)nnz, fpn = (float)prev_nf;
+  // numerator and denominator counts of the log features
+  const float a = j == 0 ? fnf : j == 1 ? fmf : j == 2 ? fnu : j == 3 ? fnu : j == 4 ? fmf
+                : j == 5 ? fmf : j == 6 ? fn : j == 8 ? fmu : fnf;
+  const float b = j == 0 ? fn : j == 1 ? fe : j == 2 ? fn : j == 3 ? fnf : j == 4 ? fnf
+                : j == 5 ? fmu : j == 6 ? fmf : j == 8 ? fnu : fpn;
+  const float scale = j == 3 || j == 9 ? 1.f / 8.f : (j == 4 || j == 8 ? 1.f / 16.f : 1.f);
+  const float shift = j == 6 ? -5.f : 0.f;  // 6: per 32 (1 + m_f), a word per 32 vertices
+  const float lg = log2f((1.f + a) / (1.f + b)) * scale + shift;
+  const float lv = (float)(level < 32 ? level : 32) * (1.f / 32.f);
+  const float vis = nb > 0 ? 1.f - fnu / fn : 0.f;
+  return j == 7 ? (float)prev_dir : j == 10 ? lv : j == 11 ? vis : lg;
+}
+
 __device__ __forceinline__ void mlp_features_raw(long long nf, long long mf, long long nu,
                                                  long long mu, int32_t nb, long long nnz,
                                                  int prev_dir, int level, long long prev_nf,
                                                  float* f) {
-  const float fnf = (float)nf, fmf = (float)mf, fnu = (float)nu, fmu = (float)mu;
-  const float fn = (float)nb, fe = (float)nnz;
-  f[0] = log2f((1.f + fnf) / (1.f + fn));
-  f[1] = log2f((1.f + fmf) / (1.f + fe));
-  f[2] = log2f((1.f + fnu) / (1.f + fn));
-  f[3] = fn * (1.f / 16777216.f);
-  f[4] = log2f((1.f + fmf) / (1.f + fnf)) * (1.f / 16.f);
-  f[5] = log2f((1.f + fmf) / (1.f + fmu));
-  f[6] = log2f((1.f + fn) / (32.f * (1.f + fmf)));
-  f[7] = (float)prev_dir;
-  f[8] = log2f((1.f + fmu) / (1.f + fnu)) * (1.f / 16.f);
-  f[9] = log2f((1.f + fnf) / (1.f + (float)prev_nf)) * (1.f / 8.f);
-  f[10] = (float)(level < 32 ? level : 32) * (1.f / 32.f);
-  f[11] = nb > 0 ? 1.f - fnu / fn : 0.f;
+#pragma unroll
+  for (int j = 0; j < MLP_IN; ++j)
+    f[j] = mlp_feature(j, nf, mf, nu, mu, nb, nnz, prev_dir, level, prev_nf);
 }
 
 // One lane's share of the weights: hidden unit j's input row and bias, and

@@ -116,6 +116,17 @@ def gated(o0, meta, margin):
     return [(x < 0) if abs(x) > margin else (d == 1) for x, (_, _, d) in zip(o0, meta)]
 
 
+def pick_margin(table):
+    """The widest margin whose regret on a held-out graph is the smallest
+    any margin reaches (table: str(margin) -> regret): the rule stands
+    wherever the network is not clearly sure, which keeps its choices safe
+    on graphs larger than the training ones. 1e9 (the rule everywhere) when
+    no finite margin reaches that regret."""
+    low = min(table.values())
+    ok = [m for m in MARGINS if m < 1e9 and table[str(m)] <= low + 1e-9]
+    return max(ok) if ok else 1e9
+
+
 def time_controllers(scale: int, seed: int, nroots: int, root_seed: int, configs: dict,
                      reps: int = 3, device="cuda", tuned: bool = True):
     """Summed device ms of nroots searches per named option set (dicts of
@@ -157,19 +168,19 @@ def time_controllers(scale: int, seed: int, nroots: int, root_seed: int, configs
     return out
 
 
-FEATURES = "sizes-and-sums"  # the feature set the controller's device code computes
+FEATURES = "size-free counts"  # the feature set the controller's device code computes
 
 
 def controller_opts(path: str, n_bfs: int, device="cuda", **base):
     """g3_bfs options for the trained controller in `path`, on top of the
     options in `base`: the network with its margin and bin choice, at every
     graph size. Its features come from the frontier sizes and degree sums
-    alone: ratios of the searched graph's own counts (frontier and unvisited
-    sizes over n and nnz, mean degrees, bitmap words per frontier edge,
-    frontier growth) plus the graph size itself, linear, which a bottom-up
-    step's bitmap walk grows with; trained at SCALE 20-24, the network
-    extrapolates in that one input. Returns (opts, params tensor, note); the tensor must outlive
-    the searches. Raises when the file was trained on another feature set."""
+    alone and are all ratios of the searched graph's own counts (frontier and
+    unvisited sizes over n and nnz and over each other, mean degrees, bitmap
+    words per frontier edge, frontier growth), so a graph larger than the
+    training ones shows the network levels it has seen. Returns (opts,
+    params tensor, note); the tensor must outlive the searches. Raises when
+    the file was trained on another feature set."""
     import torch
     with open(path) as f:
         mj = json.load(f)
@@ -177,12 +188,18 @@ def controller_opts(path: str, n_bfs: int, device="cuda", **base):
         raise ValueError(f"{path}: trained on feature set {mj.get('features')!r}, the "
                          f"controller computes {FEATURES!r}; retrain it")
     params = torch.tensor(mj["params"], dtype=torch.float32, device=device)
-    kw = dict(base, controller=g3.G3_CTRL_LEARNED, mlp_params=params,
-              mlp_margin=int(mj.get("mlp_margin", 0)), mlp_bins=int(mj.get("mlp_bins", 1)))
     lo, hi = mj.get("n_bfs_range", [0, 0])
-    where = "inside" if lo <= n_bfs <= hi else "outside"
-    note = (f"the network decides every level (n_bfs {n_bfs}, {where} the trained sizes "
-            f"{lo}..{hi})")
+    inside = lo <= n_bfs <= hi
+    # the best bin thresholds follow the absolute degrees of the frontier,
+    # which grow with the graph: the network's thresholds are used only at
+    # the sizes it was trained on, the directions at every size
+    bins = int(mj.get("mlp_bins", 1)) if inside else 0
+    kw = dict(base, controller=g3.G3_CTRL_LEARNED, mlp_params=params,
+              mlp_margin=int(mj.get("mlp_margin", 0)), mlp_bins=bins)
+    where = "inside" if inside else "outside"
+    note = (f"the network decides every level's direction (n_bfs {n_bfs}, {where} the trained "
+            f"sizes {lo}..{hi}); bin thresholds "
+            + ("the network's" if bins else "autotuned"))
     return g3.opts(**kw), params, note
 
 
@@ -248,7 +265,7 @@ def main():
     Xh, _, mh = dataset(hruns)
     oh = g3.g3_mlp_forward(p, torch.from_numpy(Xh).cuda()).cpu().numpy()[:, 0]
     table = {str(m): regret(mh, gated(oh, mh, m)) for m in MARGINS}
-    best_m = min(MARGINS, key=lambda m: (table[str(m)], m))
+    best_m = pick_margin(table)
     summary["holdout"] = {"scale": max(args.scales), "levels": int(len(Xh)),
                           "regret_ms_by_margin": table}
     summary["mlp_margin"] = int(round(min(best_m, 1e6) * 1000))

@@ -132,20 +132,19 @@ def test_adam_fits_linear_target():
 
 
 def test_features_closed_form():
-    # 8/256, 16/1024, 128/256, 255/2^24, (16/8)/16, 16/512, 256/(32*16), 1,
+    # 8/256, 16/1024, 128/256, (128/8)/8, (16/8)/16, 16/512, 256/(32*16), 1,
     # (512/128)/16, (8/2)/8, 4/32, 128/255
     f = mlp.features(n_f=7, m_f=15, n_u=127, m_u=511, n=255, nnz=1023, prev_dir=1, level=4,
                      prev_nf=1)
-    assert np.allclose(f, [-5, -6, -1, 255 / 2 ** 24, 1 / 16, -5, -1, 1, 2 / 16, 2 / 8, 4 / 32,
+    assert np.allclose(f, [-5, -6, -1, 4 / 8, 1 / 16, -5, -1, 1, 2 / 16, 2 / 8, 4 / 32,
                            128 / 255])
-    # the same situation on a graph 64 times larger gives the same ratios;
-    # only the size feature grows, 64-fold
+    # the same situation on a graph 64 times larger gives the same features:
+    # every input is a ratio of the graph's own counts
     g = mlp.features(n_f=7 * 64 + 63, m_f=15 * 64 + 63, n_u=127 * 64 + 63, m_u=511 * 64 + 63,
                      n=255 * 64 + 63, nnz=1023 * 64 + 63, prev_dir=1, level=4,
                      prev_nf=1 * 64 + 63)
-    keep = [0, 1, 2, 4, 5, 6, 7, 8, 9, 10]
+    keep = [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10]
     assert np.allclose(f[keep], g[keep]) and abs(f[11] - g[11]) < 1e-2
-    assert g[3] == pytest.approx((255 * 64 + 63) / 2 ** 24)
     assert mlp.features(0, 0, 0, 0, 0, 0, 0, 40, 0)[10] == 1.0
 
 

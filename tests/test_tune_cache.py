@@ -69,9 +69,10 @@ def test_cache_errors(tmp_path):
 
 
 def test_learned_controller_options_at_every_size(tmp_path):
-    """The trained controller (size-free features) decides at every graph
-    size with the margin and bin choice of its file; a file trained on
-    another feature set is refused."""
+    """The trained controller (size-free features) decides the direction at
+    every graph size with the margin of its file, and its bin thresholds
+    only at the trained sizes; a file trained on another feature set is
+    refused."""
     import json
     pytest.importorskip("torch")
     from oracle import mlp
@@ -82,8 +83,10 @@ def test_learned_controller_options_at_every_size(tmp_path):
                                 "features": tc.FEATURES}))
     for nb in [1 << 19, 1 << 21, 1 << 25, (1 << 19) // 2]:
         o, _, note = tc.controller_opts(str(path), nb, device="cpu", alpha=20)
-        assert (o.controller, o.mlp_margin, o.mlp_bins, o.alpha) == (g3.G3_CTRL_LEARNED, 250, 1, 20)
-        assert ("inside" in note) == ((1 << 19) <= nb <= (1 << 23))
+        inside = (1 << 19) <= nb <= (1 << 23)
+        assert (o.controller, o.mlp_margin, o.alpha) == (g3.G3_CTRL_LEARNED, 250, 20)
+        assert o.mlp_bins == (1 if inside else 0)
+        assert ("inside" in note) == inside
     old = tmp_path / "old.json"
     old.write_text(json.dumps({"params": mlp.init_params(1).tolist()}))
     with pytest.raises(ValueError):
