@@ -1454,6 +1454,7 @@ struct CtrlArgs {
   int graph_mode;
   cudaGraphConditionalHandle h_loop;
   int bu_list;  // sparse bottom-up levels run over a vertex list
+  cudaGraphConditionalHandle h_mode;  // graph mode: the SWITCH of the next level
 };
 
 // After the expansion of level L: record where the produced frontier lives,
@@ -1559,16 +1560,16 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
   __syncwarp();
   for (int i = lane; i < kWords; i += 32) gw[i] = sw[i];
   if (lane == 0 && A.graph_mode) {
+    // the level just decided runs in this loop iteration, unless the search
+    // is done or has reached the launch's level cap (the host then goes on
+    // from this record)
     const bool go = r->mode != MODE_DONE && r->level < r->cap;
+    cudaGraphSetConditional(A.h_mode, go ? (unsigned)r->mode : (unsigned)MODE_DONE);
     cudaGraphSetConditional(A.h_loop, go ? 1u : 0u);
   }
 }
 
 
-// Graph mode: picks the SWITCH body of the level about to run.
-__global__ void bfs_select(const Ctrl* c, cudaGraphConditionalHandle h_mode) {
-  cudaGraphSetConditional(h_mode, (unsigned)c->mode);
-}
 
 // --------------------------------------------------------- output mapping
 // Whether label x was reached. A search reaches exactly its root's connected
@@ -1932,12 +1933,13 @@ static void* bu_pull_fn(int rev, int full) {
 
 static bool bu_uses_list(const g3_bfs_opts& o) { return o.bu_kernel == 0; }
 
-static CtrlArgs ctrl_args(const Launch& S, int graph_mode, cudaGraphConditionalHandle h_loop) {
+static CtrlArgs ctrl_args(const Launch& S, int graph_mode, cudaGraphConditionalHandle h_loop,
+                          cudaGraphConditionalHandle h_mode) {
   return CtrlArgs{S.ws->nb,     S.g->nnz,        S.o->controller,
                   S.o->alpha,   S.o->beta,       S.o->mlp_params,
                   S.o->mlp_margin * 1e-3f,       S.o->mlp_bins,   S.o->t1,
                   S.o->t2,      S.o->t3,         S.ws->log,
-                  graph_mode,   h_loop,          bu_uses_list(*S.o)};
+                  graph_mode,   h_loop,          bu_uses_list(*S.o), h_mode};
 }
 
 // Which bottom-up kernels the options select: bu_kernel 0 (default) word
@@ -2055,16 +2057,18 @@ static bool same_opts(const g3_bfs_opts& a, const g3_bfs_opts& b) {
          a.mlp_bins == b.mlp_bins && a.bu_kernel == b.bu_kernel;
 }
 
-// Builds the level loop: WHILE(h_loop) { bfs_select -> SWITCH(h_mode) {
-// TD_Q, TD_B, BU_B, BU_Q } -> bfs_control }. Kernel arguments are baked in;
-// everything that changes per search lives in the controller record.
+// Builds the level loop: level 0's top-down kernels, then WHILE(h_loop) {
+// bfs_control -> SWITCH(h_mode) { TD_Q, TD_B, BU_B, BU_Q, -, BU_BS, BU_QS } }:
+// the controller closes the level just expanded and sets both conditions for
+// the next one. Kernel arguments are baked in; everything that changes per
+// search lives in the controller record.
 static g3_status build_graph(Launch& S) {
   g3_bfs_ws* ws = S.ws;
   cudaGraph_t top = nullptr;
   g3_status st = G3_OK;
   G3_TRY_CUDA(cudaGraphCreate(&top, 0));
   cudaGraphConditionalHandle h_loop, h_mode;
-  cudaGraphNode_t wnode, sel, sw, ctl, n0, n1, n2;
+  cudaGraphNode_t wnode, sw, ctl, n0, n1, n2;
   cudaGraph_t body, br[MODE_COUNT];
   Ctrl* c = ws->ctrl;
   int64_t nwords = ws->nwords;
@@ -2091,8 +2095,14 @@ static g3_status build_graph(Launch& S) {
                   &skip};
   CtrlArgs ca;
   void* a_ctl[] = {&c, &ca};
-  void* a_sel[] = {&c, &h_mode};
   do {
+    // level 0 (top-down from the root, set up by bfs_root) runs before the
+    // loop; each loop iteration then runs the controller on the level just
+    // expanded, which picks the next level's SWITCH branch and whether the
+    // loop goes on, and that level's kernels
+    cudaGraphNode_t l0a, l0b;
+    if ((st = add_kernel(top, &l0a, nullptr, (void*)td_front, gfront, 256, a_td))) break;
+    if ((st = add_kernel(top, &l0b, &l0a, (void*)td_bins, gbins, 256, a_td))) break;
     if (cudaGraphConditionalHandleCreate(&h_loop, top, 1, cudaGraphCondAssignDefault) !=
         cudaSuccess) { st = G3_ECUDA; break; }
     NodeParams wbuf;
@@ -2101,23 +2111,25 @@ static g3_status build_graph(Launch& S) {
     wp.conditional.handle = h_loop;
     wp.conditional.type = cudaGraphCondTypeWhile;
     wp.conditional.size = 1;
-    if (cudaGraphAddNode(&wnode, top, nullptr, nullptr, 0, &wp) != cudaSuccess) {
+    if (cudaGraphAddNode(&wnode, top, &l0b, nullptr, 1, &wp) != cudaSuccess) {
       st = G3_ECUDA;
       break;
     }
     body = wp.conditional.phGraph_out[0];
-    if (cudaGraphConditionalHandleCreate(&h_mode, body, 0, 0) != cudaSuccess) {
+    // set by the controller before every SWITCH it precedes
+    if (cudaGraphConditionalHandleCreate(&h_mode, body, MODE_DONE, 0) != cudaSuccess) {
       st = G3_ECUDA;
       break;
     }
-    if ((st = add_kernel(body, &sel, nullptr, (void*)bfs_select, 1, 1, a_sel)) != G3_OK) break;
+    ca = ctrl_args(S, 1, h_loop, h_mode);
+    if ((st = add_kernel(body, &ctl, nullptr, (void*)bfs_control, 1, 32, a_ctl))) break;
     NodeParams sbuf;
     cudaGraphNodeParams& sp = sbuf.get();
     sp.type = cudaGraphNodeTypeConditional;
     sp.conditional.handle = h_mode;
     sp.conditional.type = cudaGraphCondTypeSwitch;
     sp.conditional.size = MODE_COUNT;  // branch MODE_DONE stays empty
-    if (cudaGraphAddNode(&sw, body, &sel, nullptr, 1, &sp) != cudaSuccess) {
+    if (cudaGraphAddNode(&sw, body, &ctl, nullptr, 1, &sp) != cudaSuccess) {
       st = G3_ECUDA;
       break;
     }
@@ -2164,8 +2176,6 @@ static g3_status build_graph(Launch& S) {
     if ((st = add_kernel(br[MODE_BU_BS], &n0, nullptr, (void*)bu_list_build, glb, 256, a_lb)))
       break;
     if ((st = add_kernel(br[MODE_BU_BS], &n1, &n0, lp_fn, ws->grid_lp, 256, a_bu))) break;
-    ca = ctrl_args(S, 1, h_loop);
-    if ((st = add_kernel(body, &ctl, &sw, (void*)bfs_control, 1, 32, a_ctl))) break;
     cudaGraphExec_t ex = nullptr;
     if (cudaGraphInstantiate(&ex, top, 0) != cudaSuccess) {
       st = G3_ECUDA;
@@ -2366,7 +2376,7 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
     if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[0], s));
     G3_TRY(launch_level(S, mode, h->nf, o->timing ? ws->ev[1] : nullptr, s));
     if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[2], s));
-    CtrlArgs ca = ctrl_args(S, 0, 0);
+    CtrlArgs ca = ctrl_args(S, 0, 0, 0);
     bfs_control<<<1, 32, 0, s>>>(ws->ctrl, ca);
     G3_CHECK_LAUNCH();
     if (o->timing) G3_TRY_CUDA(cudaEventRecord(ws->ev[3], s));
