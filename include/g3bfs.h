@@ -160,12 +160,16 @@ typedef struct {
   int32_t record_both;      /* training-data mode: every level is run both
                                top-down and bottom-up from the same state and
                                both are timed (stats t_td_ms, t_bu_ms) */
-  int32_t mlp_margin;       /* learned controller: the network overrides the
-                               alpha/beta rule's direction only when its
-                               predicted |ln(t_BU / t_TD)| exceeds
+  int32_t mlp_margin;       /* learned controller: the network is evaluated
+                               on the levels where the rule's own test is
+                               within a factor of 4 of its threshold
+                               (m_f*alpha against m_u, n_f*beta against
+                               n_bfs) and overrides the rule's direction there
+                               when its predicted |ln(t_BU / t_TD)| exceeds
                                mlp_margin / 1000 (0, the default: always) */
   int32_t mlp_bins;         /* learned controller: 1 (default) the network also
-                               picks the top-down bins; 0 t1..t3 stay */
+                               picks the top-down bins on the levels it is
+                               evaluated on; 0 t1..t3 stay */
   int32_t out_split;        /* output pass (original IDs): 0 (default) and 1
                                one pass; 2 two passes over label halves (each
                                gathers from half of the packed (parent, level)

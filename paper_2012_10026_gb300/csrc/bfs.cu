@@ -1468,7 +1468,7 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
   __shared__ Ctrl sc;
   __shared__ float feat[MLP_IN];
   __shared__ long long s_prev_nf;
-  __shared__ int decide, active, s_dir;
+  __shared__ int decide, active, s_dir, s_near;
   const int lane = threadIdx.x;
   MlpLane W;  // the weights are on their way while the record is updated
   if (A.controller == G3_CTRL_LEARNED) mlp_load_lane(A.mlp, W);
@@ -1523,11 +1523,19 @@ __global__ void bfs_control(Ctrl* c, CtrlArgs A) {
       decide = d;
       s_prev_nf = prev_nf;
       s_dir = prev_dir;
+      // the network is consulted where the rule's own test is within a
+      // factor of 4 of its threshold; elsewhere the rule's answer is clear
+      {
+        const long long lhs = was_td ? r->mf * (long long)A.alpha : nf * (long long)A.beta;
+        const long long rhs = was_td ? r->mu : (long long)A.nb;
+        s_near = 4 * lhs > rhs && lhs < 4 * rhs;
+      }
+      for (int k = 0; k < 4; ++k) r->mlp_out[k] = 0.f;  // (the network's, if consulted)
       reset_next(r);
     }
   }
   __syncwarp();
-  if (active && A.controller == G3_CTRL_LEARNED) {
+  if (active && A.controller == G3_CTRL_LEARNED && s_near) {
     // lane j computes feature j, all twelve at once
     if (lane < MLP_IN)
       feat[lane] = mlp_feature(lane, r->nf, r->mf, r->nu, r->mu, A.nb, A.nnz, s_dir, r->level,

@@ -68,21 +68,36 @@ def collect(scale: int, seed: int, nroots: int, root_seed: int, device="cuda"):
     return rows, nb
 
 
-def dataset(runs):
+def rule_near(prev_dir, n_f, m_f, m_u, nb, alpha=14, beta=24):
+    """Whether the alpha/beta rule's own test is within a factor of 4 of its
+    threshold (m_f alpha against m_u after a top-down level, n_f beta
+    against n after a bottom-up one): the levels on which the controller
+    consults the network; the same integer test as the device code."""
+    if prev_dir == 0:
+        lhs, rhs = m_f * alpha, m_u
+    else:
+        lhs, rhs = n_f * beta, nb
+    return 4 * lhs > rhs and lhs < 4 * rhs
+
+
+def dataset(runs, alpha=14, beta=24):
     """(X, Y, meta) from [(rows_of_one_search, (n_bfs, nnz))]: one sample per
-    level >= 1."""
+    level >= 1; meta = (t_TD, t_BU, the rule's direction, rule_near) per
+    sample (collect() records with the library's alpha 14, beta 24)."""
     xs, ys, meta = [], [], []
     for st, (nb, nnz) in runs:
         if not st:
             continue
         x = g3.g3_mlp_features(st, nb, nnz).cpu().numpy()
-        for a, row in zip(st, x):
+        for i, (a, row) in enumerate(zip(st, x)):
             if a["level"] == 0 or a["t_td_ms"] <= 0 or a["t_bu_ms"] <= 0:
                 continue
+            prev = st[i - 1]["dir"] if i > 0 else 0
             xs.append(row)
             ys.append([math.log(a["t_bu_ms"] / a["t_td_ms"]), math.log2(a["best_t1"]),
                        math.log2(a["best_t2"]), math.log2(a["best_t3"])])
-            meta.append((a["t_td_ms"], a["t_bu_ms"], a["dir"]))
+            meta.append((a["t_td_ms"], a["t_bu_ms"], a["dir"],
+                         rule_near(prev, a["n_f"], a["m_f"], a["m_u"], nb, alpha, beta)))
     return (np.array(xs, np.float32), np.array(ys, np.float32), meta)
 
 
@@ -104,16 +119,18 @@ def raw_rows(runs):
 
 def regret(meta, choice_bu):
     """sum over levels of t(chosen direction) - min(t_TD, t_BU), in ms."""
-    return float(sum((tb if c else tt) - min(tt, tb) for (tt, tb, _), c in zip(meta, choice_bu)))
+    return float(sum((m[1] if c else m[0]) - min(m[0], m[1]) for m, c in zip(meta, choice_bu)))
 
 
 MARGINS = [0.0, 0.05, 0.1, 0.15, 0.2, 0.3, 0.5, 0.75, 1.0, 1e9]
 
 
 def gated(o0, meta, margin):
-    """Direction choices when the network decides only outside the margin
-    (|predicted ln(t_BU/t_TD)| > margin) and the alpha/beta rule otherwise."""
-    return [(x < 0) if abs(x) > margin else (d == 1) for x, (_, _, d) in zip(o0, meta)]
+    """Direction choices of the controller: the network decides on the levels
+    where the rule is near its threshold (rule_near) and its prediction is
+    outside the margin (|predicted ln(t_BU/t_TD)| > margin), the alpha/beta
+    rule everywhere else."""
+    return [(x < 0) if (m[3] and abs(x) > margin) else (m[2] == 1) for x, m in zip(o0, meta)]
 
 
 def pick_margin(table):
@@ -241,8 +258,8 @@ def main():
     p, losses = train(X, Y, args.steps, args.lr)
     out = g3.g3_mlp_forward(p, torch.from_numpy(X).cuda()).cpu().numpy()
     learned_bu = out[:, 0] < 0
-    heur_bu = np.array([d == 1 for (_, _, d) in meta])
-    best_bu = np.array([tb < tt for (tt, tb, _) in meta])
+    heur_bu = np.array([m[2] == 1 for m in meta])
+    best_bu = np.array([m[1] < m[0] for m in meta])
     summary = {
         "params": [float(v) for v in p.cpu().numpy()],
         "features": FEATURES,
@@ -291,8 +308,8 @@ def main():
             "scale": args.eval_scale, "roots": args.eval_roots, "levels": int(len(Xe)),
             "regret_ms_learned": regret(me, oe[:, 0] < 0),
             "regret_ms_learned_gated": regret(me, gated(oe[:, 0], me, best_m)),
-            "regret_ms_heuristic": regret(me, [d == 1 for (_, _, d) in me]),
-            "best_total_ms": float(sum(min(tt, tb) for (tt, tb, _) in me)),
+            "regret_ms_heuristic": regret(me, [m[2] == 1 for m in me]),
+            "best_total_ms": float(sum(min(m[0], m[1]) for m in me)),
         }
     if args.dump:
         arrays = {"train": raw_rows(runs), "holdout": raw_rows(hruns)}

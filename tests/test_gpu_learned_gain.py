@@ -29,7 +29,7 @@ def test_trained_controller_beats_the_rule_on_held_out_graphs():
     assert len(X) > 50
     p, losses = tc.train(X, Y, steps=3000)
     assert losses[-1] < 0.1 * losses[0]
-    rule = lambda m: [d == 1 for (_, _, d) in m]  # noqa: E731
+    rule = lambda meta: [m[2] == 1 for m in meta]  # noqa: E731
     # on the graphs it was trained on, its own choices cut the rule's regret
     r_fit, r_rule_fit = tc.regret(meta, _out0(p, X) < 0), tc.regret(meta, rule(meta))
     assert r_rule_fit > 0 and r_fit < 0.5 * r_rule_fit, (r_fit, r_rule_fit)

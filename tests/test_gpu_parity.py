@@ -225,21 +225,32 @@ def test_learned_controller_random_params_stays_exact(kron16):
     from oracle import mlp
     K = kron16
     ref = K["ref"]
+    from paper_2012_10026_gb300 import train_controller as tc
     params = torch.from_numpy(mlp.init_params(5).astype(np.float32)).cuda()
+    seen = 0
     for root in K["roots"][:8].tolist():
         parent, level, st = run_bfs(K["g"], root, K["n"], max_stats=64,
                                     controller=g3.G3_CTRL_LEARNED, mlp_params=params)
         _, lref = oracle.bfs(ref["off"], ref["col"], root)
         assert np.array_equal(level, lref)
         assert oracle.validate(ref["off"], ref["col"], root, parent, level) == 0
+        consulted = 0
         for a in st[1:]:
+            prev = st[a["level"] - 1]
+            if not tc.rule_near(prev["dir"], a["n_f"], a["m_f"], a["m_u"], ref["n_plus"]):
+                # the rule's test is clear by a factor of 4: the network is
+                # not evaluated and the rule decides
+                assert list(a["mlp_out"]) == [0.0] * 4
+                continue
+            consulted += 1
             f = mlp.features(a["n_f"], a["m_f"], a["n_u"], a["m_u"], ref["n_plus"],
-                             len(ref["col_r"]), st[a["level"] - 1]["dir"], a["level"],
-                             st[a["level"] - 1]["n_f"])
+                             len(ref["col_r"]), prev["dir"], a["level"], prev["n_f"])
             o = mlp.forward(mlp.init_params(5), f[None])[0]
             assert np.allclose(a["mlp_out"], o, rtol=1e-4, atol=1e-4)
             if abs(o[0]) > 1e-3:
                 assert a["dir"] == (g3.G3_DIR_BU if o[0] < 0 else g3.G3_DIR_TD)
+        seen += consulted
+    assert seen > 0  # some levels were the network's to decide
 
 
 @pytest.mark.parametrize("margin", [0, 300, 2000, 10 ** 9])

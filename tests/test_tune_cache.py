@@ -91,3 +91,20 @@ def test_learned_controller_options_at_every_size(tmp_path):
     old.write_text(json.dumps({"params": mlp.init_params(1).tolist()}))
     with pytest.raises(ValueError):
         tc.controller_opts(str(old), 1 << 20, device="cpu")
+
+
+def test_rule_near_is_the_factor_four_band():
+    """The levels the controller consults the network on: the rule's test
+    strictly within a factor of 4 of its threshold, in integers."""
+    from paper_2012_10026_gb300 import train_controller as tc
+    # after a top-down level: m_f * 14 against m_u
+    assert tc.rule_near(0, 1, 10, 141, 10 ** 6)          # 140 vs 141
+    assert not tc.rule_near(0, 1, 10, 560, 10 ** 6)      # exactly 4x: clear
+    assert tc.rule_near(0, 1, 10, 559, 10 ** 6)
+    assert not tc.rule_near(0, 1, 40, 140, 10 ** 6)      # 560 vs 140: clear
+    assert tc.rule_near(0, 1, 40, 141, 10 ** 6)
+    # after a bottom-up level: n_f * 24 against n
+    assert tc.rule_near(1, 1000, 0, 0, 24000)
+    assert not tc.rule_near(1, 250, 0, 0, 24000)         # 6000 * 4 == 24000
+    assert not tc.rule_near(1, 4000, 0, 0, 24000)        # 96000 == 4 * 24000
+    assert tc.rule_near(1, 3999, 0, 0, 24000)
