@@ -706,16 +706,34 @@ __device__ __forceinline__ bool in_frontier(const uint32_t* __restrict__ f, int3
 }
 
 // Scans the rest of a row after a missed first probe; returns the parent or
-// -1 and advances k (edges examined).
+// -1 and advances k (edges examined, up to and including the parent, as a
+// one-at-a-time scan counts them). Four entries per step: their column
+// loads, then their frontier probes, are in flight together, so a row of a
+// few entries costs one dependent round trip instead of one per entry (on a
+// dense level most of the time goes into these scans). Entries past the
+// row's end are never loaded.
 template <int REV>
 __device__ __forceinline__ int32_t bu_scan_rest(const int32_t* __restrict__ col,
                                                 const uint32_t* __restrict__ fcur, int64_t b,
                                                 int64_t e, int64_t& k) {
   const int64_t d = e - b;
+  const int32_t* __restrict__ p = REV ? col + (e - 1) : col + b;  // entry k at p[+-k]
+  const int64_t step = REV ? -1 : 1;
   while (k < d) {
-    const int32_t w = col[REV ? e - 1 - k : b + k];
-    ++k;
-    if (in_frontier(fcur, w)) return w;
+    const int64_t left = d - k;
+    const int32_t w0 = __ldg(p + step * k);
+    const int32_t w1 = left > 1 ? __ldg(p + step * (k + 1)) : 0;
+    const int32_t w2 = left > 2 ? __ldg(p + step * (k + 2)) : 0;
+    const int32_t w3 = left > 3 ? __ldg(p + step * (k + 3)) : 0;
+    const bool f0 = in_frontier(fcur, w0);
+    const bool f1 = left > 1 && in_frontier(fcur, w1);
+    const bool f2 = left > 2 && in_frontier(fcur, w2);
+    const bool f3 = left > 3 && in_frontier(fcur, w3);
+    if (f0) { k += 1; return w0; }
+    if (f1) { k += 2; return w1; }
+    if (f2) { k += 3; return w2; }
+    if (f3) { k += 4; return w3; }
+    k += left < 4 ? left : 4;
   }
   return -1;
 }
@@ -825,20 +843,21 @@ __global__ void __launch_bounds__(256, 6) bu_pull(int32_t nb, int64_t nwords, ui
     int32_t p0 = (x0 >= 0 && in_frontier(fcur, x0)) ? x0 : -1;
     int32_t p1 = (x1 >= 0 && in_frontier(fcur, x1)) ? x1 : -1;
     int64_t k0 = d0 > 0 ? 1 : 0, k1 = d1 > 0 ? 1 : 0;
-    if (p0 < 0 && d0 > 1) {
-      if (REV) {
+    const bool m0 = p0 < 0 && d0 > 1, m1 = p1 < 0 && d1 > 1;
+    if (REV) {  // the first probe came from neighbors+: the row bounds now
+      if (m0) {
         e0 = off[v0 + 1];
         b0 = e0 - d0;
       }
-      p0 = bu_scan_rest<REV>(col, fcur, b0, e0, k0);
-    }
-    if (p1 < 0 && d1 > 1) {
-      if (REV) {
+      if (m1) {
         e1 = off[v1 + 1];
         b1 = e1 - d1;
       }
-      p1 = bu_scan_rest<REV>(col, fcur, b1, e1, k1);
     }
+    // (a warp-wide scan of the long rows was slower: under RCM the long rows
+    // come clustered, and one lane per row keeps them all in flight)
+    if (m0) p0 = bu_scan_rest<REV>(col, fcur, b0, e0, k0);
+    if (m1) p1 = bu_scan_rest<REV>(col, fcur, b1, e1, k1);
     acc.ex += (unsigned)(k0 + k1);
     const int32_t q0 = p0 >= 0 && o2n ? __ldg(&o2n[p0]) : p0;
     const int32_t q1 = p1 >= 0 && o2n ? __ldg(&o2n[p1]) : p1;
