@@ -776,7 +776,7 @@ __device__ __forceinline__ int32_t bu_scan_rest4(const int32_t* __restrict__ col
 // label range are kept too (a separate instantiation, so that the default
 // one carries only the counters the controllers read).
 template <int REV, int FULL>
-__global__ void __launch_bounds__(256, 6) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
+__global__ void __launch_bounds__(256, 8) bu_pull(int32_t nb, int64_t nwords, uint32_t* visited,
                                                Bufs B, const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ col,
                                                const int2* __restrict__ nplus, PlOut plo,
