@@ -55,8 +55,14 @@
 // a sparse level (vertex list, see bu_list_build), and the end.
 enum {
   MODE_TD_Q = 0, MODE_TD_B = 1, MODE_BU_B = 2, MODE_BU_Q = 3, MODE_DONE = 4,
-  MODE_BU_BS = 5, MODE_BU_QS = 6, MODE_COUNT = 7
+  MODE_BU_BS = 5, MODE_BU_QS = 6, MODE_TD_QS = 7, MODE_COUNT = 8
 };
+// A top-down level from a queue this small (frontier vertices, their edges)
+// runs the same kernels on TD_SMALL_GRID blocks: launching and retiring a
+// grid sized for the largest levels costs more than such a level's work.
+#define TD_SMALL_NF 16384
+#define TD_SMALL_MF 65536
+#define TD_SMALL_GRID 64
 
 // Device-side controller record.
 struct __align__(16) Ctrl {
@@ -289,7 +295,10 @@ __device__ __forceinline__ void reset_next(Ctrl* c) {
 
 __device__ __forceinline__ int mode_of(const Ctrl* c) {
   if (c->nf <= 0) return MODE_DONE;
-  if (c->dir == G3_DIR_TD) return c->fmt_queue ? MODE_TD_Q : MODE_TD_B;
+  if (c->dir == G3_DIR_TD) {
+    if (!c->fmt_queue) return MODE_TD_B;
+    return c->nf <= TD_SMALL_NF && c->mf <= TD_SMALL_MF ? MODE_TD_QS : MODE_TD_Q;
+  }
   const bool only_queue = c->fmt_queue == 1;
   if (c->bu_sparse) return only_queue ? MODE_BU_QS : MODE_BU_BS;
   return only_queue ? MODE_BU_Q : MODE_BU_B;
@@ -2010,12 +2019,13 @@ static g3_status launch_level(const Launch& S, int mode, int64_t nf, cudaEvent_t
     G3_CHECK_LAUNCH();
   }
   if (ev_mid) G3_TRY_CUDA(cudaEventRecord(ev_mid, s));
-  if (mode == MODE_TD_Q || mode == MODE_TD_B) {
-    td_front<<<cap_grid(nf, 256, ws->grid_front), 256, 0, s>>>(
+  if (mode == MODE_TD_Q || mode == MODE_TD_B || mode == MODE_TD_QS) {
+    const bool small = mode == MODE_TD_QS;
+    td_front<<<small ? TD_SMALL_GRID : cap_grid(nf, 256, ws->grid_front), 256, 0, s>>>(
         S.g->off, S.g->col, ws->visited, ws->plo, S.B, ws->bins, ws->goff, S.nb1, c);
     G3_CHECK_LAUNCH();
-    td_bins<<<ws->grid_bins, 256, 0, s>>>(S.g->off, S.g->col, ws->visited, ws->plo, S.B,
-                                          ws->bins, ws->goff, S.nb1, c);
+    td_bins<<<small ? TD_SMALL_GRID : ws->grid_bins, 256, 0, s>>>(
+        S.g->off, S.g->col, ws->visited, ws->plo, S.B, ws->bins, ws->goff, S.nb1, c);
     G3_CHECK_LAUNCH();
   } else if (mode == MODE_BU_BS || mode == MODE_BU_QS) {
     bu_list_build<<<cap_grid(ws->nwords, 256, ws->grid_lb), 256, 0, s>>>(S.B, ws->nwords, ws->nb,
@@ -2161,9 +2171,14 @@ static g3_status build_graph(Launch& S) {
       break;
     }
     for (int k = 0; k < MODE_COUNT; ++k) br[k] = sp.conditional.phGraph_out[k];
-    // MODE_TD_Q
+    // MODE_TD_Q, and MODE_TD_QS on a small grid
     if ((st = add_kernel(br[MODE_TD_Q], &n0, nullptr, (void*)td_front, gfront, 256, a_td))) break;
     if ((st = add_kernel(br[MODE_TD_Q], &n1, &n0, (void*)td_bins, gbins, 256, a_td))) break;
+    if ((st = add_kernel(br[MODE_TD_QS], &n0, nullptr, (void*)td_front, TD_SMALL_GRID, 256,
+                         a_td)))
+      break;
+    if ((st = add_kernel(br[MODE_TD_QS], &n1, &n0, (void*)td_bins, TD_SMALL_GRID, 256, a_td)))
+      break;
     // MODE_TD_B
     if ((st = add_kernel(br[MODE_TD_B], &n0, nullptr, (void*)bitmap_to_q, gconv, 256, a_conv)))
       break;
@@ -2255,7 +2270,8 @@ static g3_status record_trials(const Launch& S, int64_t nf, g3_level_stats* r, c
     }
     c.bu_sparse = !td && bu_uses_list(*S.o) && bu_sparse_level(c.nu, ws->nb);
     const bool only_queue = c.fmt_queue == 1;
-    const int mode = td ? (c.fmt_queue ? MODE_TD_Q : MODE_TD_B)
+    const bool small = c.nf <= TD_SMALL_NF && c.mf <= TD_SMALL_MF;
+    const int mode = td ? (c.fmt_queue ? (small ? MODE_TD_QS : MODE_TD_Q) : MODE_TD_B)
                         : c.bu_sparse ? (only_queue ? MODE_BU_QS : MODE_BU_BS)
                                       : (only_queue ? MODE_BU_Q : MODE_BU_B);
     G3_TRY_CUDA(cudaMemcpyAsync(ws->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
