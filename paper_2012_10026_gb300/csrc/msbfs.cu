@@ -234,15 +234,41 @@ __global__ void ms_push_finalize(const int32_t* __restrict__ touched, uint64_t* 
   }
 }
 
-// Records v's new source bits at level lnext.
+// The four level bytes of a 32-bit word whose sources are set in nib (bit i
+// -> byte i) become lnext (rep: lnext in every byte); the others stay.
+__device__ __forceinline__ uint32_t ms_merge4(uint32_t old, uint32_t nib, uint32_t rep) {
+  const uint32_t m = __vcmpne4((nib * 0x01010101u) & 0x08040201u, 0u);
+  return (old & ~m) | (rep & m);
+}
+
+// Records v's new source bits at level lnext: a few bits as single bytes;
+// more as 16-byte read-merge-writes of the 16-source quarters of v's 64-byte
+// row that have new bits (one store per quarter instead of one per source).
+// One thread owns v's row at a time (v is taken by one kernel of a level).
 __device__ __forceinline__ void ms_take(int32_t v, uint64_t nv, uint64_t* vis, uint64_t vv,
                                         int8_t* lv, int8_t lnext) {
   vis[v] = vv | nv;
-  uint64_t bits = nv;
-  while (bits) {
-    const int s = __ffsll((long long)bits) - 1;
-    lv[(int64_t)v * 64 + s] = lnext;
-    bits &= bits - 1;
+  if (__popcll((long long)nv) <= 4) {
+    uint64_t bits = nv;
+    while (bits) {
+      const int s = __ffsll((long long)bits) - 1;
+      lv[(int64_t)v * 64 + s] = lnext;
+      bits &= bits - 1;
+    }
+    return;
+  }
+  int4* row = reinterpret_cast<int4*>(lv + (int64_t)v * 64);
+  const uint32_t rep = 0x01010101u * (uint32_t)(uint8_t)lnext;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t b16 = (uint32_t)(nv >> (16 * q)) & 0xFFFFu;
+    if (!b16) continue;
+    int4 w = row[q];
+    w.x = (int)ms_merge4((uint32_t)w.x, b16 & 0xFu, rep);
+    w.y = (int)ms_merge4((uint32_t)w.y, (b16 >> 4) & 0xFu, rep);
+    w.z = (int)ms_merge4((uint32_t)w.z, (b16 >> 8) & 0xFu, rep);
+    w.w = (int)ms_merge4((uint32_t)w.w, (b16 >> 12) & 0xFu, rep);
+    row[q] = w;
   }
 }
 
