@@ -197,43 +197,6 @@ __global__ void __launch_bounds__(256) ms_push_chunks(const int2* __restrict__ i
   }
 }
 
-// Finalize after a push: keep N[w]'s bits not yet in vis[w] as the new
-// frontier word, record their levels, queue w when anything is new, clear N.
-__global__ void ms_push_finalize(const int32_t* __restrict__ touched, uint64_t* N,
-                                 uint64_t* vis, uint64_t* Fn, int8_t* lv, int32_t* qn,
-                                 const int64_t* __restrict__ off, unsigned long long* ctr) {
-  const int64_t len = (int64_t)ctr[2];
-  const int8_t lnext = (int8_t)ctr[MS_LNEXT];
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < len;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    bool want = false;
-    int32_t w = 0;
-    unsigned long long d = 0;
-    if (i < len) {
-      w = touched[i];
-      const uint64_t nw = N[w];
-      N[w] = 0;
-      const uint64_t nv = nw & ~vis[w];
-      Fn[w] = nv;
-      if (nv) {
-        vis[w] |= nv;
-        uint64_t bits = nv;
-        while (bits) {
-          const int s = __ffsll((long long)bits) - 1;
-          lv[(int64_t)w * 64 + s] = lnext;
-          bits &= bits - 1;
-        }
-        want = true;
-        d = (unsigned long long)(off[w + 1] - off[w]);
-      }
-    }
-    g3_warp_append(0xffffffffu, want, w, qn, &ctr[0]);
-    for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    if ((threadIdx.x & 31) == 0 && d) atomicAdd(&ctr[1], d);
-  }
-}
-
 // The four level bytes of a 32-bit word whose sources are set in nib (bit i
 // -> byte i) become lnext (rep: lnext in every byte); the others stay.
 __device__ __forceinline__ uint32_t ms_merge4(uint32_t old, uint32_t nib, uint32_t rep) {
@@ -269,6 +232,38 @@ __device__ __forceinline__ void ms_take(int32_t v, uint64_t nv, uint64_t* vis, u
     w.z = (int)ms_merge4((uint32_t)w.z, (b16 >> 8) & 0xFu, rep);
     w.w = (int)ms_merge4((uint32_t)w.w, (b16 >> 12) & 0xFu, rep);
     row[q] = w;
+  }
+}
+
+// Finalize after a push: keep N[w]'s bits not yet in vis[w] as the new
+// frontier word, record their levels, queue w when anything is new, clear N.
+__global__ void ms_push_finalize(const int32_t* __restrict__ touched, uint64_t* N,
+                                 uint64_t* vis, uint64_t* Fn, int8_t* lv, int32_t* qn,
+                                 const int64_t* __restrict__ off, unsigned long long* ctr) {
+  const int64_t len = (int64_t)ctr[2];
+  const int8_t lnext = (int8_t)ctr[MS_LNEXT];
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < len;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool want = false;
+    int32_t w = 0;
+    unsigned long long d = 0;
+    if (i < len) {
+      w = touched[i];
+      const uint64_t nw = N[w];
+      N[w] = 0;
+      const uint64_t vw = vis[w];
+      const uint64_t nv = nw & ~vw;
+      Fn[w] = nv;
+      if (nv) {
+        ms_take(w, nv, vis, vw, lv, lnext);
+        want = true;
+        d = (unsigned long long)(off[w + 1] - off[w]);
+      }
+    }
+    g3_warp_append(0xffffffffu, want, w, qn, &ctr[0]);
+    for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if ((threadIdx.x & 31) == 0 && d) atomicAdd(&ctr[1], d);
   }
 }
 
