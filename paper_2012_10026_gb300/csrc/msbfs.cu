@@ -291,13 +291,20 @@ __global__ void __launch_bounds__(256) ms_pull(int32_t nb, const int64_t* __rest
           big = true;
         } else {
           sc_all += 1;
-          // up to the next multiple of 4 one entry at a time, then one
-          // 128-bit column load and four independent gathers per step; the
+          // up to the next multiple of 4 one entry at a time, then two
+          // 128-bit column loads and eight independent gathers per step
+          // (four near the row's end); the
           // exit test runs per step (vector loads only on a 16-byte aligned
           // col, which the allocator gives)
           uint64_t acc = 0;
           int64_t j = b;
           for (; j < e && (j & 3) && (acc | vv) != full; ++j) acc |= __ldg(&F[col[j]]);
+          for (; col_al16 && j + 8 <= e && (acc | vv) != full; j += 8) {
+            const int4 c4 = __ldg(reinterpret_cast<const int4*>(col + j));
+            const int4 c5 = __ldg(reinterpret_cast<const int4*>(col + j + 4));
+            acc |= ((__ldg(&F[c4.x]) | __ldg(&F[c4.y])) | (__ldg(&F[c4.z]) | __ldg(&F[c4.w]))) |
+                   ((__ldg(&F[c5.x]) | __ldg(&F[c5.y])) | (__ldg(&F[c5.z]) | __ldg(&F[c5.w])));
+          }
           for (; col_al16 && j + 4 <= e && (acc | vv) != full; j += 4) {
             const int4 c4 = __ldg(reinterpret_cast<const int4*>(col + j));
             acc |= (__ldg(&F[c4.x]) | __ldg(&F[c4.y])) | (__ldg(&F[c4.z]) | __ldg(&F[c4.w]));
