@@ -809,7 +809,9 @@ def gpu_arm(args, rank, world):
     if args.host_loop:  # profiling: every level's kernels as separate stream launches
         kw["timing"] = 1
     opts = g3.opts(**kw)  # default path: the level loop runs as one CUDA graph
-    opts_timed = g3.opts(**dict(kw, timing=1))  # host-driven, events around each level
+    # host-driven, events around each level; the counts the byte model needs,
+    # without the histogram, so the kernels timed are the ones searches run
+    opts_timed = g3.opts(**dict(kw, timing=1, stats_counts_only=1))
     # the plain method: the alpha/beta rule on the same tuned options, and
     # with the library defaults
     plain_opts = g3.opts(controller=g3.G3_CTRL_HEURISTIC, **base)

@@ -192,7 +192,12 @@ typedef struct {
                                level; 3 word pairs on the levels with at least
                                a quarter of the graph unvisited, word tiles on
                                the others */
-  int32_t reserved[3];
+  int32_t stats_counts_only; /* 1: per-level statistics (stats, max_stats)
+                               carry the counts but not the degree histogram
+                               and label range (zero), so the expansion
+                               kernels run as they do without statistics;
+                               0 (default): everything */
+  int32_t reserved[2];
 } g3_bfs_opts;
 
 /* Fills the defaults listed above. */

@@ -44,7 +44,8 @@ class g3_bfs_opts(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
                 ("record_both", ctypes.c_int32), ("mlp_margin", ctypes.c_int32),
                 ("mlp_bins", ctypes.c_int32), ("out_split", ctypes.c_int32),
-                ("bu_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("bu_kernel", ctypes.c_int32), ("stats_counts_only", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class g3_level_stats(ctypes.Structure):

@@ -2332,7 +2332,7 @@ static g3_status bfs_impl(g3_graph* g, int32_t root, const g3_bfs_opts* o, int32
   g3_bfs_ws* ws = g->ws;
   const int32_t nb = ws->nb;
   Ctrl* h = ws->h_ctrl;
-  const int full_stats = o->record_both || (stats && max_stats > 0);
+  const int full_stats = o->record_both || (stats && max_stats > 0 && !o->stats_counts_only);
   Launch S{g, ws, o,
            Bufs{{ws->qa, ws->qb}, {ws->fa, ws->fb}, g->relabelled ? g->old_of_new : nullptr},
            (int64_t)ws->nb + 4, full_stats};

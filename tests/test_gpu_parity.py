@@ -325,6 +325,23 @@ def test_record_both_mode_keeps_results_exact(kron16):
         assert all((a["best_t1"], a["best_t2"], a["best_t3"]) in sweep for a in st)
 
 
+def test_counts_only_statistics_equal_the_full_ones(kron16):
+    # stats_counts_only: the same counts per level as the full statistics,
+    # the histogram and label range left at zero, the same results
+    K = kron16
+    for root in K["roots"][:4].tolist():
+        for timing in (0, 1):
+            p_f, l_f, st_f = run_bfs(K["g"], root, K["n"], max_stats=64, timing=timing)
+            p_c, l_c, st_c = run_bfs(K["g"], root, K["n"], max_stats=64, timing=timing,
+                                     stats_counts_only=1)
+            assert np.array_equal(l_f, l_c) and len(st_f) == len(st_c)
+            for a, b in zip(st_f, st_c):
+                for key in ("level", "dir", "n_f", "m_f", "n_u", "m_u", "examined", "n_next"):
+                    assert a[key] == b[key], (root, key)
+                if b["level"] > 0:
+                    assert list(b["hist"]) == [0, 0, 0, 0]
+
+
 def test_graph_mode_equals_host_driven_mode(kron16):
     # default searches run the level loop as one CUDA graph; per-level timing
     # switches to the host-driven loop. Both must give the same levels, the
