@@ -477,13 +477,13 @@ __global__ void __launch_bounds__(256) ms_out(int32_t n, int32_t nb, int k,
       const int32_t x = xs[r];
       int4 val = make_int4(-1, -1, -1, -1);
       if (x >= 0) val = *reinterpret_cast<const int4*>(lv + (int64_t)x * 64 + qd * 16);
-      const int8_t* vb = reinterpret_cast<const int8_t*>(&val);
-      const uint64_t m = vm[r];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int sidx = qd * 16 + j;
-        tile[r][sidx] = ((m >> sidx) & 1ull) ? vb[j] : (int8_t)-1;
-      }
+      // bytes of sources not reached become -1, four at a time
+      const uint32_t nb16 = ~(uint32_t)(vm[r] >> (qd * 16)) & 0xFFFFu;
+      uint32_t* trow = reinterpret_cast<uint32_t*>(&tile[r][qd * 16]);
+      trow[0] = ms_merge4((uint32_t)val.x, nb16 & 0xFu, 0xFFFFFFFFu);
+      trow[1] = ms_merge4((uint32_t)val.y, (nb16 >> 4) & 0xFu, 0xFFFFFFFFu);
+      trow[2] = ms_merge4((uint32_t)val.z, (nb16 >> 8) & 0xFu, 0xFFFFFFFFu);
+      trow[3] = ms_merge4((uint32_t)val.w, (nb16 >> 12) & 0xFu, 0xFFFFFFFFu);
     }
     __syncthreads();
     constexpr int WPT = MS_OUT_TILE / 4;  // 32-bit words per source per tile
