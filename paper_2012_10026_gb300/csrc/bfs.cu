@@ -538,7 +538,9 @@ __device__ __forceinline__ void td_visit4(const TdArgs& a, WarpQueue& q, StatAcc
   uint32_t word[4];
   bool cand[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) word[k] = has[k] ? __ldcg(&a.visited[w[k] >> 5]) : ~0u;
+  // the probes may hit L1: during a level bits only turn from 0 to 1, so a
+  // stale word can only say "unvisited", and the atomicOr then tells the truth
+  for (int k = 0; k < 4; ++k) word[k] = has[k] ? __ldca(&a.visited[w[k] >> 5]) : ~0u;
 #pragma unroll
   for (int k = 0; k < 4; ++k) cand[k] = has[k] && !((word[k] >> (w[k] & 31)) & 1u);
   uint32_t old[4];
