@@ -270,13 +270,6 @@ struct StatAccT {
 };
 using StatAcc = StatAccT<2>;
 
-__device__ __forceinline__ bool td_claim(uint32_t* visited, int32_t w) {
-  const uint32_t bit = 1u << (w & 31);
-  uint32_t* word = &visited[w >> 5];
-  if (__ldcg(word) & bit) return false;
-  return !(atomicOr(word, bit) & bit);
-}
-
 __device__ __forceinline__ void reset_next(Ctrl* c) {
   c->q_len = 0;
   c->nx_nf = 0;
