@@ -698,9 +698,11 @@ __global__ void __launch_bounds__(256, 4) td_bins(const int64_t* __restrict__ of
 }
 
 // -------------------------------------------------------------- bottom-up
-// Bottom-up levels where at least a quarter of the graph is unvisited run
-// bu_staged (in the degree-aware scan order); the others run the word-tile
-// kernel. Both kernels of a level's pair check the same condition.
+// Where two bottom-up kernels share a level kind (bu_kernel 1: staged and
+// word tiles; 3: word pairs and word tiles), levels with at least a quarter
+// of the graph unvisited are the first kernel's and the others the word-tile
+// kernel's; both check this same condition. (bu_kernel 0 splits the levels
+// by bu_sparse_level instead, in the controller.)
 __device__ __forceinline__ bool bu_dense(const Ctrl* c, int32_t nb) {
   return c->nu * 4 >= (long long)nb;
 }
