@@ -108,3 +108,20 @@ def test_rule_near_is_the_factor_four_band():
     assert not tc.rule_near(1, 250, 0, 0, 24000)         # 6000 * 4 == 24000
     assert not tc.rule_near(1, 4000, 0, 0, 24000)        # 96000 == 4 * 24000
     assert tc.rule_near(1, 3999, 0, 0, 24000)
+
+
+def test_pick_margin_is_the_widest_with_the_least_regret():
+    """The controller's margin: the widest candidate whose held-out regret is
+    the smallest reached (ties go to the wider margin, so the rule stands
+    where the network is unsure); the rule everywhere when only the infinite
+    margin reaches it."""
+    from paper_2012_10026_gb300 import train_controller as tc
+    ms = tc.MARGINS
+    table = {str(m): 0.5 for m in ms}
+    table[str(0.1)] = table[str(0.2)] = table[str(0.3)] = 0.1
+    assert tc.pick_margin(table) == 0.3
+    table = {str(m): 0.2 for m in ms}
+    assert tc.pick_margin(table) == max(m for m in ms if m < 1e9)
+    table = {str(m): 0.3 for m in ms}
+    table[str(1e9)] = 0.1
+    assert tc.pick_margin(table) == 1e9
