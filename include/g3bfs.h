@@ -233,7 +233,10 @@ typedef struct {
  * (Algorithm 2): each level expanded top-down from a frontier queue
  * (degree-binned thread / warp / CTA / grid work, Algorithms 1 and 4) or
  * bottom-up over the unvisited vertices with bitmaps and an early exit on
- * the first parent found (Algorithm 5), as the controller decides.
+ * the first parent found (Algorithm 5; on levels with under 4 % of the graph
+ * unvisited, over a list of those vertices, Algorithm 6's shrinking active
+ * range), as the controller decides. After a full RCM relabel the output
+ * pass takes the reached set from the root's component range.
  *   parent, level : n int32 entries each (original IDs); device OR host
  *                   pointers. Page-locked host memory is written directly
  *                   by the output kernel; pageable host memory is filled
@@ -243,7 +246,8 @@ typedef struct {
  *                   valid: only the root is reached.
  *   opts          : NULL = defaults.
  *   stats         : host array of max_stats entries or NULL; receives one
- *                   record per level while room remains. *n_levels (may be
+ *                   record per level while room remains (degree histogram
+ *                   and label range included unless opts.stats_counts_only). *n_levels (may be
  *                   NULL) receives the number of non-empty frontiers.
  * The first call on a graph allocates its BFS workspace (about 52 bytes per
  * BFS vertex plus 8 per vertex of the input); later calls allocate nothing. By default the level loop runs on
