@@ -77,3 +77,29 @@ def test_parity_leg_rejects_other_roots():
 def test_oracle_threads_bounds():
     assert 1 <= bench.oracle_threads(1 << 26, 64) <= max(1, bench.host_cores() - 1)
     assert bench.oracle_threads(1 << 10, 1) == 1
+
+
+def test_level_kinds_and_graph_kernel_count():
+    """Roofline split and the level-loop kernel count: dense bottom-up levels
+    (at least 4 % of the graph unvisited) are the word-pair kernel's, sparse
+    ones the vertex-list kernels'; the count follows the loop's structure."""
+    nb = 100000
+
+    def lv(level, d, n_u, ms=0.1):
+        return {"level": level, "dir": d, "n_u": n_u, "n_f": 10, "m_f": 100,
+                "examined": 50, "n_next": 5, "ms_expand": ms}
+    # TD (level 0), TD, BU dense, BU dense, BU sparse, TD, TD
+    st = [lv(0, 0, nb - 1), lv(1, 0, nb - 50), lv(2, 1, 90000), lv(3, 1, 5000),
+          lv(4, 1, 3999), lv(5, 0, 100), lv(6, 0, 90)]
+    kinds = [bench.level_kind(s, nb) for s in st]
+    assert kinds == ["td", "td", "bu", "bu", "bu_list", "td", "td"]
+    agg = bench.roofline_levels([st], nb)
+    assert agg["bu"][2] == 2 and agg["bu_list"][2] == 1 and agg["td"][2] == 4
+    assert agg["bu"][0] == bench.level_bytes(st[2], nb) + bench.level_bytes(st[3], nb)
+    # level 0: 2; level 1: 1 + 2; level 2: 1 + 1 + 2 (queue -> bitmap);
+    # level 3: 1 + 1; level 4: 1 + 2; level 5 after the list level: 1 + 2;
+    # level 6: 1 + 2; the final controller: 1
+    assert bench.graph_kernel_count([st], nb) == 2 + 3 + 4 + 2 + 3 + 3 + 3 + 1
+    # a top-down level after a word-pair bottom-up level converts the bitmap
+    st2 = [lv(0, 0, nb - 1), lv(1, 1, 90000), lv(2, 0, 100)]
+    assert bench.graph_kernel_count([st2], nb) == 2 + (1 + 1 + 2) + (1 + 2 + 1) + 1
