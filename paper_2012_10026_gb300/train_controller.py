@@ -14,6 +14,14 @@ with t_TD the fastest top-down time over the candidates and t*'s its bin
 thresholds. The 12-32-4 network is trained by g3_mlp_train (full-batch Adam,
 one kernel), and the parameters are written as JSON.
 
+How the controller uses it: on a level where the alpha/beta rule's own test
+is within a factor of 4 of its threshold (rule_near), the network's sign of
+ln(t_BU / t_TD) decides the direction when its magnitude exceeds the margin;
+everywhere else the rule decides. The margin is the widest candidate that
+loses nothing on a held-out graph of the largest trained size (pick_margin);
+the network's bin thresholds are used only when they time at least 1 %
+faster there, and only at trained graph sizes (controller_opts).
+
 Usage:
   python -m paper_2012_10026_gb300.train_controller --scales 20 21 22 23 24 \\
       --seeds 11 12 13 14 15 --roots 12 --out paper_2012_10026_gb300/mlp_params.json
